@@ -1,0 +1,95 @@
+"""Data model of a composed collective (paper Sec. 3, Listing 1).
+
+A program holds named per-rank buffers and a sequence of epochs.  Each epoch
+is a set of primitives registered between two fences; all primitives of an
+epoch run concurrently (Sec. 3.2) and a fence orders the epochs (Sec. 3.3).
+
+* ``Multicast(root i, leaves j, count d)``: the root's source range is
+  replicated into every leaf's destination range (Sec. 3.1, M(i, j, d)).
+* ``Reduction(leaves i, root j, count d)``: the leaves' source ranges are
+  summed into the root's destination range (Sec. 3.1, R(i, j, d, op)); the op
+  is sum.
+
+A location is a ``Ref(key, off)``: an element offset into a named buffer.  The
+keys of user buffers are tuples such as ``("send", r)``; the factorizer's
+relay buffers use ``("scratch", k)``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+DTYPES = {
+    "f32": np.dtype(np.float32),
+    "i32": np.dtype(np.int32),
+    "bf16": np.dtype(np.uint16),     # bit patterns; see lowprec
+    "fp8": np.dtype(np.uint8),       # e4m3 bit patterns; see lowprec
+}
+
+# elements per 16-byte quantum; FP8 pieces also align to its 128-element scale blocks
+QUANTUM = {"f32": 4, "i32": 4, "bf16": 8, "fp8": 128}
+
+
+@dataclass(frozen=True)
+class Ref:
+    key: tuple
+    off: int
+
+    def shift(self, k: int) -> "Ref":
+        return Ref(self.key, self.off + k)
+
+
+@dataclass
+class Multicast:
+    root: int
+    leaves: tuple
+    count: int
+    src: Ref                      # the root's source range
+    dsts: dict                    # leaf rank -> Ref of its destination range
+
+    kind = "multicast"
+
+
+@dataclass
+class Reduction:
+    leaves: tuple
+    root: int
+    count: int
+    srcs: dict                    # leaf rank -> Ref of its source range
+    dst: Ref                      # the root's destination range
+
+    kind = "reduction"
+
+
+@dataclass
+class Program:
+    P: int
+    dtype: str = "f32"
+    buffers: dict = field(default_factory=dict)     # key -> length (elements)
+    epochs: list = field(default_factory=lambda: [[]])
+
+    # -- registration (Listing 1) ------------------------------------------
+    def buffer(self, key, length: int) -> Ref:
+        self.buffers[key] = int(length)
+        return Ref(key, 0)
+
+    def multicast(self, root: int, leaves, count: int, src: Ref, dsts: dict) -> None:
+        self.epochs[-1].append(Multicast(int(root), tuple(sorted(int(j) for j in leaves)),
+                                         int(count), src, dict(dsts)))
+
+    def reduction(self, leaves, root: int, count: int, srcs: dict, dst: Ref) -> None:
+        self.epochs[-1].append(Reduction(tuple(sorted(int(i) for i in leaves)), int(root),
+                                         int(count), dict(srcs), dst))
+
+    def fence(self) -> None:
+        self.epochs.append([])
+
+    @property
+    def primitives(self):
+        return [p for ep in self.epochs for p in ep]
+
+    def allocate(self, fill=None) -> dict:
+        """Zero-filled NumPy arrays for every user buffer."""
+        dt = DTYPES[self.dtype]
+        return {k: np.zeros(n, dtype=dt) for k, n in self.buffers.items()}

@@ -1,0 +1,204 @@
+"""Plain semantics of primitives and collectives (paper Sec. 3.1-3.3, Table 2).
+
+Readings (the paper is silent on these; each is stated once here):
+
+* Sum order.  A reduction's result is the *hierarchical nested fold*: a rank
+  contributes its own values; a level-l group contributes the left fold, in
+  the payload's arithmetic (FP32 round-to-nearest-even, no fused
+  multiply-add; int32 wraps), of the contributions of its non-empty
+  subgroups in ascending index order.  It depends only on the hierarchy and
+  the leaf set -- not on the root, striping, pipeline depth or
+  representatives -- so a factorized schedule must reproduce it exactly.
+* Races.  Two primitives of one epoch that write overlapping ranges, or where
+  one writes what another reads, race (Sec. 3.2: the result is undefined).
+  ``find_race`` reports them; the library rejects such programs.
+* A multicast whose root is also a leaf delivers to the root's own
+  destination (nothing to do when source and destination coincide, the
+  "dashed edges" of Fig. 4).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .hierarchy import check, group_sizes
+from .model import Multicast, Program, Reduction
+
+
+# ---------------------------------------------------------------------------
+# the fixed-order sum
+# ---------------------------------------------------------------------------
+
+def nested_fold(values: dict, hierarchy, add=None) -> np.ndarray:
+    """Hierarchical nested fold of ``values`` (rank -> array) over ``hierarchy``.
+
+    S(rank r) = values[r]; S(group) = left fold over the S(subgroup) of the
+    subgroups that hold at least one contributing rank, in ascending order.
+    ``add`` combines two partials (default: NumPy's elementwise add in the
+    arrays' own dtype, i.e. IEEE RNE for float32 and wrapping for int32).
+    """
+    if not values:
+        raise ValueError("empty leaf set")
+    h = list(hierarchy)
+    G = group_sizes(h)
+    ranks = sorted(values)
+    add = add or (lambda a, b: a + b)
+
+    def S(level: int, base: int, members: list):
+        if level == len(h):
+            return values[base]
+        sub = G[level + 1]
+        acc = None
+        for q in range(h[level]):
+            lo = base + q * sub
+            inside = [r for r in members if lo <= r < lo + sub]
+            if not inside:
+                continue
+            part = S(level + 1, lo, inside)
+            acc = part.copy() if acc is None else add(acc, part)
+        return acc
+
+    return S(0, 0, ranks)
+
+
+def fsum64(values: list) -> np.ndarray:
+    """Elementwise FP64 sum (the error reference of the reduced-precision payloads)."""
+    acc = np.zeros_like(np.asarray(values[0], dtype=np.float64))
+    for v in values:
+        acc = acc + np.asarray(v, dtype=np.float64)
+    return acc
+
+
+# ---------------------------------------------------------------------------
+# primitives and programs
+# ---------------------------------------------------------------------------
+
+def _view(mem: dict, ref, n: int) -> np.ndarray:
+    return mem[ref.key][ref.off:ref.off + n]
+
+
+def apply_multicast(p: Multicast, mem: dict) -> None:
+    """M(i, j, d): every leaf's destination receives the root's d elements (Sec. 3.1)."""
+    src = _view(mem, p.src, p.count).copy()
+    for j in p.leaves:
+        _view(mem, p.dsts[j], p.count)[...] = src
+
+
+def apply_reduction(p: Reduction, mem: dict, hierarchy, add=None) -> None:
+    """R(i, j, d, sum): the root's destination receives the fixed-order sum of
+    the leaves' d elements (Sec. 3.1)."""
+    if p.count == 0:
+        return
+    vals = {i: _view(mem, p.srcs[i], p.count).copy() for i in p.leaves}
+    _view(mem, p.dst, p.count)[...] = nested_fold(vals, hierarchy, add)
+
+
+def run_program(prog: Program, mem: dict, hierarchy, add=None) -> dict:
+    """Execute the program's epochs in order; inside an epoch the (race-free)
+    primitives are applied in registration order, which Sec. 3.2 makes
+    irrelevant."""
+    check(hierarchy, prog.P)
+    for epoch in prog.epochs:
+        for p in epoch:
+            if isinstance(p, Multicast):
+                apply_multicast(p, mem)
+            else:
+                apply_reduction(p, mem, hierarchy, add)
+    return mem
+
+
+# ---------------------------------------------------------------------------
+# races (Sec. 3.2)
+# ---------------------------------------------------------------------------
+
+def accesses(p) -> tuple[list, list]:
+    """(reads, writes) of a primitive as (key, lo, hi) element ranges."""
+    if isinstance(p, Multicast):
+        reads = [(p.src.key, p.src.off, p.src.off + p.count)]
+        writes = []
+        for j in p.leaves:
+            d = p.dsts[j]
+            if j == p.root and d == p.src:
+                continue                      # in-place root: nothing written
+            writes.append((d.key, d.off, d.off + p.count))
+        return (reads if p.count else []), (writes if p.count else [])
+    reads = [(p.srcs[i].key, p.srcs[i].off, p.srcs[i].off + p.count) for i in p.leaves]
+    writes = [(p.dst.key, p.dst.off, p.dst.off + p.count)]
+    return (reads if p.count else []), (writes if p.count else [])
+
+
+def _overlap(a, b) -> bool:
+    return a[0] == b[0] and a[1] < b[2] and b[1] < a[2]
+
+
+def find_race(prog: Program):
+    """First pair of primitives of one epoch that race, or None.  A primitive
+    whose own writes overlap each other (two leaves sharing a destination) or
+    overlap its own source is reported as racing with itself."""
+    for e, epoch in enumerate(prog.epochs):
+        acc = [accesses(p) for p in epoch]
+        for a in range(len(epoch)):
+            ra, wa = acc[a]
+            for x in range(len(wa)):
+                for y in range(x + 1, len(wa)):
+                    if _overlap(wa[x], wa[y]):
+                        return (e, a, a)
+                for r in ra:
+                    if _overlap(wa[x], r):
+                        return (e, a, a)
+            for b in range(a + 1, len(epoch)):
+                rb, wb = acc[b]
+                if any(_overlap(w, v) for w in wa for v in wb + rb) or \
+                        any(_overlap(w, v) for w in wb for v in ra):
+                    return (e, a, b)
+    return None
+
+
+# ---------------------------------------------------------------------------
+# direct definitions of the collectives (Table 2, Sec. 3.2), without primitives
+# x[r] is rank r's send buffer, the result y[r] its receive buffer.
+# ---------------------------------------------------------------------------
+
+def _chunks(v: np.ndarray, P: int):
+    d = v.shape[0] // P
+    return [v[k * d:(k + 1) * d] for k in range(P)]
+
+
+def def_broadcast(x, root):
+    return [x[root].copy() for _ in range(len(x))]
+
+
+def def_reduce(x, root, hierarchy):
+    """Only the root's result is defined; other ranks' y are untouched (None)."""
+    y = [None] * len(x)
+    y[root] = nested_fold({r: x[r] for r in range(len(x))}, hierarchy)
+    return y
+
+
+def def_allgather(x):
+    return [np.concatenate(x) for _ in range(len(x))]
+
+
+def def_reducescatter(x, hierarchy):
+    P = len(x)
+    return [nested_fold({r: _chunks(x[r], P)[j] for r in range(P)}, hierarchy) for j in range(P)]
+
+
+def def_allreduce(x, hierarchy):
+    s = nested_fold({r: x[r] for r in range(len(x))}, hierarchy)
+    return [s.copy() for _ in range(len(x))]
+
+
+def def_scatter(x, root):
+    return [c.copy() for c in _chunks(x[root], len(x))]
+
+
+def def_gather(x, root):
+    y = [None] * len(x)
+    y[root] = np.concatenate(x)
+    return y
+
+
+def def_alltoall(x):
+    P = len(x)
+    ch = [_chunks(x[i], P) for i in range(P)]
+    return [np.concatenate([ch[i][j] for i in range(P)]) for j in range(P)]

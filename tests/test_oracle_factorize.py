@@ -1,0 +1,311 @@
+"""Pins of the oracle's factorizer and schedule simulator (paper Sec. 4):
+the worked examples of Sec. 4.3 and Fig. 1, closed-form per-level volumes,
+the volumes implied by Table 3, stage counts, and brute-force agreement of
+the simulated schedule with the plain semantics over every hierarchy of up to
+eight ranks, random roots, leaf subsets, stripe counts and pipeline depths,
+executed in random dependency-respecting orders."""
+import os
+from math import prod
+
+import numpy as np
+import pytest
+
+from oracle import programs as PR
+from oracle import semantics as S
+from oracle.factorize import factorize, piece_bounds
+from oracle.hierarchy import all_factorizations, group_sizes, level_of
+from oracle.model import Program
+from oracle.simulate import simulate
+from synth import int_ranks, random_leaf_set, uniform_ranks
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def _hops(plan):
+    out = set()
+    for op in plan.ops:
+        if op.kind != "copy" or op.level is None:
+            continue
+        a = op.srcs[0][0]
+        for b, _ in op.dsts:
+            out.add((op.level, a, b))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# worked examples
+# ---------------------------------------------------------------------------
+
+def test_golden_broadcast_2_2_3():
+    rows = _read_golden("bcast_2_2_3.txt")
+    hops = {(int(r[1]), int(r[2]), int(r[3])) for r in rows if r[0] == "hop"}
+    stages = {int(r[1]): int(r[2]) for r in rows if r[0] == "stages"}
+    prog = PR.broadcast(12, 6, root=0)
+    plan = factorize(prog, [2, 2, 3])
+    assert _hops(plan) == hops
+    for s, n in stages.items():
+        assert factorize(prog, [2, 2, 3], stripe=s).stages() == n
+
+
+def test_golden_fig1_direct_vs_hierarchical():
+    node = [2, 3]                                  # two nodes of three GPUs
+    for h, crossing in _read_golden("fig1_direct_vs_hier.txt"):
+        h = [int(v) for v in h.split(",")]
+        plan = factorize(PR.broadcast(6, 2, root=0), h)
+        n = sum(1 for lv, a, b in _hops(plan) if level_of(a, b, node) == 0)
+        assert n == int(crossing)
+
+
+def test_striped_tree_is_multi_rail():
+    """Sec. 4.3: with stripe(3) on {2,2,3} every GPU of the root node sends one
+    piece across the top level (g0, g1, g2 -> g6, g7, g8)."""
+    plan = factorize(PR.broadcast(12, 6, root=0), [2, 2, 3], stripe=3)
+    top = {(a, b) for lv, a, b in _hops(plan) if lv == 0}
+    assert top == {(0, 6), (1, 7), (2, 8)}
+
+
+# ---------------------------------------------------------------------------
+# closed-form volumes
+# ---------------------------------------------------------------------------
+
+HIERS = [[8], [2, 4], [4, 2], [2, 2, 2], [2, 2, 3], [4, 4, 4], [3, 1, 2], [1, 6]]
+
+
+@pytest.mark.parametrize("h", HIERS)
+@pytest.mark.parametrize("s,m", [(1, 1), (2, 3), (3, 1), (4, 2)])
+def test_full_leaf_level_volumes(h, s, m):
+    """A multicast (or reduction) of b bytes over all P ranks crosses level l
+    prod_{k<l} f_k * (f_l - 1) times: one copy into each sibling subgroup of
+    every level-l group, (P-1) copies in all.  Pipelining leaves this
+    unchanged.  Striping inside one bottom-level group only re-routes the
+    same transfers (Sec. 4.3), except that a root holding a separate
+    destination also exchanges the pieces of the branches b > 0 with k_b
+    (the branches deliver to "all GPUs but" k_b, the root included)."""
+    P = prod(h)
+    if s > P:
+        pytest.skip("stripe larger than P")
+    d = 8
+    b = d * P * 4
+    L = len(h)
+    expect = [prod(h[:l]) * (h[l] - 1) * b for l in range(L)]
+    G = group_sizes(h)
+    ls = max(l for l in range(L + 1) if G[l] >= s)
+    striped = s > 1 and G[ls] < P
+    bounds = piece_bounds(d * P, s * m, 4)
+    extra = (d * P - bounds[m]) * 4 if striped else 0
+    for root in {0, P - 1, P // 2}:
+        bc = factorize(PR.broadcast(P, d, root=root), h, s, m).level_bytes()
+        rd = factorize(PR.reduce(P, d, root=root), h, s, m).level_bytes()
+        inplace = PR.broadcast(P, d, root=root)
+        p0 = inplace.primitives[0]
+        p0.dsts[root] = p0.src
+        ip = factorize(inplace, h, s, m).level_bytes()
+        assert sum(ip) == (P - 1) * b
+        assert sum(bc) == (P - 1) * b + extra
+        assert sum(rd) == (P - 1) * b + extra
+        if not striped or ls == L - 1:
+            assert ip == expect
+            want = list(expect)
+            want[L - 1] += extra
+            assert bc == want and rd == want, (bc, rd, want)
+
+
+@pytest.mark.parametrize("n,g", [(2, 2), (2, 4), (4, 4), (3, 2)])
+@pytest.mark.parametrize("s", [1, 2])
+def test_table3_top_level_volumes(n, g, s):
+    """Table 3's bounds divide the per-node top-level volume by the node
+    bandwidth kf.  With h = {n, g}, p = n*g and chunk d, the volumes entering
+    each node are: All-gather and Reduce-scatter (p-g)d, All-reduce 2(p-g)d,
+    All-to-all g(p-g)d, Broadcast dp (every non-root node), Gather (p-g)d
+    into the root node; Scatter sends (p-g)d out of the root node."""
+    p = n * g
+    d = 16
+    e = 4
+
+    def per_node_in(plan):
+        vol = [0] * n
+        for op in plan.ops:
+            pairs = ([(op.srcs[0][0], b) for b, _ in op.dsts] if op.kind == "copy"
+                     else [(a, op.dsts[0][0]) for a, _ in op.srcs])
+            for a, b in pairs:
+                if a // g != b // g:
+                    vol[b // g] += op.n * e
+        return vol
+
+    def per_node_out(plan):
+        vol = [0] * n
+        for op in plan.ops:
+            pairs = ([(op.srcs[0][0], b) for b, _ in op.dsts] if op.kind == "copy"
+                     else [(a, op.dsts[0][0]) for a, _ in op.srcs])
+            for a, b in pairs:
+                if a // g != b // g:
+                    vol[a // g] += op.n * e
+        return vol
+
+    h = [n, g]
+    if s > g:
+        pytest.skip()
+    assert per_node_in(factorize(PR.allgather(p, d), h, s)) == [(p - g) * d * e] * n
+    assert per_node_in(factorize(PR.reducescatter(p, d), h, s)) == [(p - g) * d * e] * n
+    assert per_node_in(factorize(PR.allreduce(p, d), h, s)) == [2 * (p - g) * d * e] * n
+    assert per_node_in(factorize(PR.alltoall(p, d), h, s)) == [g * (p - g) * d * e] * n
+    vin = per_node_in(factorize(PR.broadcast(p, d, root=0), h, s))
+    assert vin == [0] + [d * p * e] * (n - 1)
+    assert per_node_in(factorize(PR.gather(p, d, root=0), h, s))[0] == (p - g) * d * e
+    assert per_node_out(factorize(PR.scatter(p, d, root=0), h, s))[0] == (p - g) * d * e
+
+
+def test_hierarchical_vs_direct_top_volume():
+    """Sec. 2.2: hierarchical factorization minimises top-level traffic; for a
+    Broadcast on {n, g} the top level carries (n-1) copies instead of p-g."""
+    for n, g in [(2, 3), (4, 4), (2, 8)]:
+        p = n * g
+        node = [n, g]
+        flat = factorize(PR.broadcast(p, 4, root=0), [p])
+        hier = factorize(PR.broadcast(p, 4, root=0), node)
+        cross = lambda plan: sum(1 for lv, a, b in _hops(plan) if level_of(a, b, node) == 0)
+        assert cross(flat) == p - g
+        assert cross(hier) == n - 1
+
+
+# ---------------------------------------------------------------------------
+# stages and fences
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("h", [[2, 2, 3], [4, 4, 4], [2, 4], [8]])
+def test_stage_counts(h):
+    """Without striping a full broadcast has one dependent stage per level;
+    striping adds stage 0; pipelining does not change the chain length of a
+    channel (Sec. 4.5)."""
+    P = prod(h)
+    L = sum(1 for f in h if f > 1)
+    prog = PR.broadcast(P, 64, root=0)
+    assert factorize(prog, h).stages() == L
+    assert factorize(prog, h, 1, 4).stages() == L
+    g = group_sizes(h)[-2]
+    if len(h) > 1:
+        assert factorize(prog, h, g).stages() == L + 1
+
+
+def test_fence_is_dependency_not_barrier():
+    """Sec. 3.3 / Fig. 4: in the All-reduce program, multicast M_i depends on
+    reduction R_i only (per pipeline channel), not on the other R_j."""
+    P, d = 8, 16
+    plan = factorize(PR.allreduce(P, d), [2, 4], 1, 2)
+    for op in plan.ops:
+        if op.epoch != 1:
+            continue
+        for j in op.deps:
+            dep = plan.ops[j]
+            if dep.epoch == 0:
+                assert dep.prim == op.prim - P          # M_i -> R_i
+                assert dep.channel == op.channel
+
+
+def test_piece_bounds_properties():
+    for count in [0, 1, 3, 4, 17, 1000, 4097]:
+        for parts in [1, 2, 3, 8, 32]:
+            for q in [4, 8, 128]:
+                b = piece_bounds(count, parts, q)
+                assert b[0] == 0 and b[-1] == count
+                assert all(b[i] <= b[i + 1] for i in range(parts))
+                assert all(v % q == 0 for v in b[:-1] if v != count)
+
+
+# ---------------------------------------------------------------------------
+# simulator == semantics, brute force over small configurations
+# ---------------------------------------------------------------------------
+
+def _random_program(P, seed, dtype):
+    """Two epochs of multicasts and reductions on disjoint ranges with random
+    roots and sparse leaf sets; the second epoch reads what the first wrote."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    prog = Program(P, dtype)
+    n = int(g.integers(1, 40))
+    k = 3
+    send = [prog.buffer(("send", r), n * k) for r in range(P)]
+    recv = [prog.buffer(("recv", r), n * k) for r in range(P)]
+    for c in range(k):
+        leaves = random_leaf_set(P, seed * 31 + c)
+        root = int(g.integers(0, P))
+        if g.integers(0, 2):
+            prog.multicast(root, leaves, n, send[root].shift(c * n),
+                           {j: recv[j].shift(c * n) for j in leaves})
+        else:
+            prog.reduction(leaves, root, n, {i: send[i].shift(c * n) for i in leaves},
+                           recv[root].shift(c * n))
+    prog.fence()
+    for c in range(k):
+        root = int(g.integers(0, P))
+        leaves = [j for j in random_leaf_set(P, seed * 97 + c) if j != root] or [(root + 1) % P]
+        leaves = [j for j in leaves if j != root]
+        if not leaves:
+            continue
+        # in place: forward what the root holds in recv chunk c
+        prog.multicast(root, leaves, n, recv[root].shift(c * n),
+                       {j: recv[j].shift(c * n) for j in leaves})
+    return prog
+
+
+def _init(prog, seed):
+    mem = prog.allocate()
+    g = np.random.Generator(np.random.PCG64(seed))
+    for k, v in mem.items():
+        if v.dtype == np.float32:
+            v[...] = g.uniform(-1, 1, size=v.shape).astype(np.float32)
+        else:
+            v[...] = g.integers(-2**31, 2**31 - 1, size=v.shape, endpoint=True, dtype=np.int64)
+    return mem
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 6, 8])
+def test_simulator_matches_semantics(P):
+    cases = 0
+    for h in all_factorizations(P):
+        for s in sorted({1, 2, P} & set(range(1, P + 1))):
+            for m in (1, 3):
+                for dtype in ("f32", "i32"):
+                    seed = hash((P, tuple(h), s, m, dtype)) % 100000
+                    prog = _random_program(P, seed, dtype)
+                    if S.find_race(prog) is not None:
+                        continue
+                    mem0 = _init(prog, seed)
+                    ref = {k: v.copy() for k, v in mem0.items()}
+                    S.run_program(prog, ref, h)
+                    plan = factorize(prog, h, s, m)
+                    got = {k: v.copy() for k, v in mem0.items()}
+                    simulate(plan, got, order_seed=seed)
+                    for k in ref:
+                        assert np.array_equal(ref[k], got[k]), (h, s, m, dtype, k)
+                    cases += 1
+    assert cases > 0
+
+
+@pytest.mark.parametrize("name", PR.SEVEN + ("reduce", "allreduce_single"))
+@pytest.mark.parametrize("P,h,s,m", [(8, [2, 4], 1, 1), (8, [2, 4], 4, 3), (12, [2, 2, 3], 3, 2),
+                                     (16, [4, 4], 4, 2), (8, [2, 2, 2], 2, 4)])
+def test_collectives_simulated(name, P, h, s, m):
+    d = 13
+    prog = PR.BUILDERS[name](P, d)
+    x = uniform_ranks(P, d * P, seed=2)
+    mem0 = prog.allocate()
+    for r in range(P):
+        mem0[("send", r)][...] = x[r][:mem0[("send", r)].shape[0]]
+        mem0[("recv", r)][...] = np.float32(-7.0)              # guard value
+    ref = {k: v.copy() for k, v in mem0.items()}
+    S.run_program(prog, ref, h)
+    plan = factorize(prog, h, s, m)
+    got = {k: v.copy() for k, v in mem0.items()}
+    simulate(plan, got, order_seed=P + s + m)
+    for k in ref:
+        assert np.array_equal(ref[k], got[k]), (name, k)
