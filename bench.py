@@ -1,0 +1,410 @@
+"""Benchmark of the hierarchical collective path on GB300.
+
+Workload (one "step"): the seven standard collectives -- Broadcast, Scatter,
+Gather, All-gather, Reduce-scatter, All-reduce (Listing 2) and All-to-all --
+over P = 64 virtual ranks with hierarchy {4,4,4}, 4 MiB of fp32 per rank
+(uniform[-1, 1], seed 0), stripe 4, pipeline 8; each collective is one start
+of its own persistent communicator, all seven enqueued back to back.
+
+Metric: device-memory GB/s of the schedule (each copy reads its bytes once
+and writes them once per destination; an f-input reduce reads f times and
+writes once), summed over the seven collectives and divided by their summed
+kernel time, with the fraction of the measured HBM bandwidth; per-collective
+GB/s and the paper-style d*p/t are reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica on its own GPU
+("replicas only": the virtual-rank path does not shard across devices).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HBM GB/s (% of GB300 peak) per collective; p50/p99 latency of served requests"
+KINDS = ("broadcast", "scatter", "gather", "allgather", "reducescatter", "allreduce", "alltoall")
+P, HIER, STRIPE, PIPE = 64, [4, 4, 4], 4, 8
+BYTES_PER_RANK = 4 << 20
+STRIDE = 1          # oracle sample: every STRIDE-th primitive of each collective
+KERNEL_SRC = os.path.join(ROOT, "paper_2408_05962_gb300", "csrc", "hiccl_runtime.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "executor_traffic_seven_p64.txt")
+
+
+def workload_config(extra=None):
+    cfg = {"workload": "seven collectives, P=64 virtual ranks, hierarchy {4,4,4}, 4 MiB fp32 per rank, "
+                       "stripe 4, pipeline 8",
+           "ranks": P, "hierarchy": HIER, "stripe": STRIPE, "pipeline": PIPE,
+           "bytes_per_rank": BYTES_PER_RANK, "collectives": list(KINDS),
+           "l2": "working set of one step ~3.5 GB > 129 MB L2; no flush between steps"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------------------
+# multi-rank plumbing (replicas): barrier and max over ranks
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    world, rank, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend, rank=rank, world_size=world)
+    return world, rank
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def aggregate(local_bytes: float, local_seconds: float, device=None):
+    """Whole-job (sum of bytes over ranks, max of time over ranks)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return local_bytes, local_seconds
+    dev = device if (device is not None and dist.get_backend() == "nccl") else torch.device("cpu")
+    b = torch.tensor([local_bytes], dtype=torch.float64, device=dev)
+    t = torch.tensor([local_seconds], dtype=torch.float64, device=dev)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(b.item()), float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        loaded = [v for v in sm if mx and v > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("hiccl_runtime.cu", "hiccl_internal.h"):
+        with open(os.path.join(ROOT, "paper_2408_05962_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current executor source (else None)."""
+    try:
+        vals = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.split("=", 1)
+                    vals[k.strip()] = v.strip()
+        if vals.get("kernel_sha") != kernel_hash():
+            return None
+        return float(vals["dram_bytes_per_step"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# the oracle as a CPU baseline / reference arm (bounded sample)
+# ---------------------------------------------------------------------------
+
+_ORACLE_CACHE = {}
+
+
+def _oracle_plans(seed: int = 0):
+    """The oracle's factorized schedules of the workload and their buffers
+    (built once; factorization is initialization, not part of a step)."""
+    if seed in _ORACLE_CACHE:
+        return _ORACLE_CACHE[seed]
+    import numpy as np
+
+    from oracle import programs as PR
+    from oracle.factorize import factorize
+    from oracle.model import Program
+    from synth import uniform_ranks
+
+    d = BYTES_PER_RANK // 4 // P
+    x = uniform_ranks(P, d * P, seed=seed)
+    out = []
+    for kind in KINDS:
+        full = PR.BUILDERS[kind](P, d)
+        prog = Program(P, full.dtype, dict(full.buffers), [ep[::STRIDE] for ep in full.epochs])
+        plan = factorize(prog, HIER, STRIPE, PIPE)
+        mem = prog.allocate()
+        for r in range(P):
+            mem[("send", r)][...] = x[r][:mem[("send", r)].shape[0]]
+        for k, n in plan.scratch.items():
+            mem[k] = np.zeros(n, dtype=np.float32)
+        out.append((kind, plan, mem))
+    _ORACLE_CACHE[seed] = out
+    return out
+
+
+def oracle_sample(budget_s: float, seed: int = 0):
+    """Simulate the oracle's factorized schedule of the workload (all seven
+    collectives) for at most ``budget_s`` seconds in all.
+    Returns (schedule bytes simulated, seconds, description)."""
+    from oracle.simulate import execute_op
+
+    total_b, total_t = 0, 0.0
+    per = budget_s / len(KINDS)
+    for kind, plan, mem in _oracle_plans(seed):
+        t0 = time.perf_counter()
+        for op in plan.ops:
+            execute_op(op, mem)
+            total_b += op.n * 4 * (1 + len(op.dsts) if op.kind == "copy" else len(op.srcs) + 1)
+            if time.perf_counter() - t0 > per:
+                break
+        total_t += time.perf_counter() - t0
+    kept = "every primitive" if STRIDE == 1 else f"every {STRIDE}-th primitive"
+    return total_b, total_t, (f"oracle schedule simulator (NumPy, 1 thread) on {kept} of each of the seven "
+                              f"collectives, at most {per:.1f} s of simulation each (factorization untimed)")
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if world > 1:
+        dist_init("gloo")
+        if rank != 0:
+            return
+    for _ in range(args.warmup):
+        oracle_sample(0.5)
+    bs, ts = 0, 0.0
+    for _ in range(args.steps):
+        b, t, desc = oracle_sample(args.ref_budget)
+        bs += b
+        ts += t
+    gbs = bs / ts / 1e9
+    line = {"metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ts / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(), "impl": "reference",
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the CUDA path
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        dist_init("nccl")
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2408_05962_gb300 import collectives as C
+    from paper_2408_05962_gb300 import hiccl as H
+    from synth import uniform_ranks
+
+    d = BYTES_PER_RANK // 4 // P
+    x = torch.from_numpy(uniform_ranks(P, d * P, seed=0))
+    comms, bufs, nbytes, pbytes = {}, {}, {}, {}
+    for kind in KINDS:
+        b = C.Buffers(kind, P, d, torch.float32, device)
+        b.send.copy_(x[:, :b.ls].to(device))
+        b.recv.zero_()
+        comm = H.Comm(P, "f32")
+        C.compose(comm, kind, d, b.send_ptrs(), b.recv_ptrs())
+        comm.init(HIER, STRIPE, PIPE)
+        rd, wr = comm.hbm_bytes()
+        comms[kind], bufs[kind], nbytes[kind] = comm, b, rd + wr
+        pbytes[kind] = d * 4 * P                       # the paper's d*p per collective
+    stream = torch.cuda.current_stream(device)
+    step_bytes = sum(nbytes.values())
+
+    def one_step(evs=None):
+        for i, kind in enumerate(KINDS):
+            if evs is not None:
+                evs[i].record(stream)
+            comms[kind].start(stream)
+        if evs is not None:
+            evs[len(KINDS)].record(stream)
+        for kind in KINDS:
+            comms[kind].wait()
+
+    for _ in range(max(args.warmup, 3)):
+        one_step()
+    torch.cuda.synchronize(device)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    all_evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(KINDS) + 1)] for _ in range(args.steps)]
+    barrier(device)
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        one_step(all_evs[k])
+    torch.cuda.synchronize(device)
+    wall = time.perf_counter() - t0
+    barrier(device)
+    clk = clocks.stop()
+
+    per_kind = {kind: [] for kind in KINDS}
+    step_ms = []
+    for evs in all_evs:
+        for i, kind in enumerate(KINDS):
+            per_kind[kind].append(evs[i].elapsed_time(evs[i + 1]))
+        step_ms.append(evs[0].elapsed_time(evs[len(KINDS)]))
+    dev_s = sum(step_ms) / 1e3
+    tot_bytes, tot_s = aggregate(step_bytes * args.steps, dev_s, device)
+    gbs = tot_bytes / tot_s / 1e9
+    peak, peak_kind = measured_peak()
+
+    # end to end through the public API with host buffers (pinned)
+    h_send = {k: torch.empty(bufs[k].send.shape, dtype=torch.float32, pin_memory=True) for k in KINDS}
+    h_recv = {k: torch.empty(bufs[k].recv.shape, dtype=torch.float32, pin_memory=True) for k in KINDS}
+    for k in KINDS:
+        h_send[k].copy_(x[:, :bufs[k].ls])
+    h2d = sum(t.numel() * 4 for t in h_send.values())
+    d2h = sum(t.numel() * 4 for t in h_recv.values())
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier(device)
+    torch.cuda.synchronize(device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        for k in KINDS:
+            bufs[k].send.copy_(h_send[k], non_blocking=True)
+        one_step()
+        for k in KINDS:
+            h_recv[k].copy_(bufs[k].recv, non_blocking=True)
+        torch.cuda.synchronize(device)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    eb, es = aggregate(step_bytes * e2e_steps, e2e_s, device)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        b, t, desc = oracle_sample(args.cpu_budget)
+        cpu = {"value": b / t / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+    coll = {}
+    for kind in KINDS:
+        med = statistics.median(per_kind[kind])
+        coll[kind] = {"ms": med, "gbs": nbytes[kind] / med / 1e6, "frac": nbytes[kind] / med / 1e6 / peak,
+                      "dp_over_t_gbs": pbytes[kind] / med / 1e6, "schedule_bytes": nbytes[kind],
+                      "level_bytes": comms[kind].level_bytes(), "steps": comms[kind].plan_info()["steps"]}
+    traffic = recorded_traffic()
+    line = {
+        "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": statistics.mean(step_ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload_config({"parallelism": f"replicas{world}"}),
+        "roofline": {"bound": "hbm", "achieved": gbs / world, "peak": peak, "unit": "GB/s",
+                     "frac": gbs / world / peak, "peak_source": peak_kind,
+                     "traffic": traffic, "kernel": "hiccl_exec_kernel"},
+        "clocks": clk, "gpu_launches": len(KINDS) * args.steps * world,
+        "e2e": {"value": eb / es / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "collectives": coll, "wall_ms_per_step": wall / args.steps * 1e3,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for c in comms.values():
+        c.destroy()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=14.0)
+    ap.add_argument("--ref-budget", type=float, default=7.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * hiccl.h -- C ABI of the GB300 hierarchical collective engine.
+ *
+ * A collective is composed from multicast, reduction and fence primitives
+ * (HiCCL, arXiv 2408.05962, Sec. 3, Listing 1), factorized for a stated
+ * hierarchy into per-level point-to-point copy and sum-reduce steps with
+ * striping and pipelining (Sec. 4), and executed by one persistent CUDA
+ * kernel per start (Sec. 5.2).  The P ranks are virtual: each rank is a set
+ * of disjoint buffers in one GPU's memory, so every step is a copy or a
+ * reduce between device buffers; per-level byte volumes are counted, not
+ * measured on links.
+ *
+ * Conventions for every function below:
+ *   - A status is returned; nothing aborts.  On failure the communicator's
+ *     state is unchanged and hiccl_last_error() holds a message.
+ *   - "device pointer" means a pointer into memory of the current CUDA
+ *     device (cudaMalloc / PyTorch allocations); host pointers there are a
+ *     caller error the library cannot detect before the kernel runs.
+ *   - Counts are in elements of the communicator's dtype.
+ *   - A communicator is not thread-safe; calls on one communicator must be
+ *     serialized by the caller.  Different communicators are independent.
+ */
+#ifndef HICCL_H
+#define HICCL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hiccl_comm *hiccl_comm_t;
+
+/* Payload element types.  F32 and I32 reductions are exact functions of the
+ * hierarchy (see hiccl_add_reduction); BF16 and FP8E4M3 are reduced with FP32
+ * accumulation. */
+typedef enum {
+  HICCL_F32 = 0,
+  HICCL_I32 = 1,
+  HICCL_BF16 = 2,
+  HICCL_FP8E4M3 = 3
+} hiccl_dtype_t;
+
+/* Reduction operator (Sec. 3.1 lists sum, max, logical or; sum is provided). */
+typedef enum { HICCL_SUM = 0 } hiccl_op_t;
+
+typedef enum {
+  HICCL_OK = 0,
+  HICCL_ERR_INVALID = 1,     /* bad argument, rank, hierarchy, stripe or pipeline */
+  HICCL_ERR_STATE = 2,       /* call not allowed in the communicator's state      */
+  HICCL_ERR_RACE = 3,        /* primitives of one epoch overlap (Sec. 3.2)         */
+  HICCL_ERR_NOMEM = 4,       /* host or device allocation failed                   */
+  HICCL_ERR_CUDA = 5,        /* a CUDA runtime call failed                         */
+  HICCL_ERR_TIMEOUT = 6,     /* a dependency wait in the executor ran out          */
+  HICCL_ERR_UNSUPPORTED = 7  /* valid request this build does not implement        */
+} hiccl_status_t;
+
+/* ---- composition (Sec. 3, Listing 1) ---------------------------------------- */
+
+/* Create a communicator over `nranks` (>= 1) virtual ranks whose payload is
+ * `dtype`.  *out receives the handle (NULL on failure).  The handle owns all
+ * library memory; release it with hiccl_destroy. */
+hiccl_status_t hiccl_create(int nranks, hiccl_dtype_t dtype, hiccl_comm_t *out);
+
+/* Register M(root, leaves, count) (Sec. 3.1): after execution every leaf j's
+ * range recv[j][0, count) holds the root's send[root][0, count).
+ *   send, recv : arrays of nranks device pointers, one per virtual rank, as
+ *                each rank would pass its own buffer in the paper's SPMD API.
+ *                Only send[root] and recv[j] for j in leaves are read; other
+ *                entries may be NULL.  A root that is also a leaf with
+ *                recv[root] == send[root] is in place (nothing to copy).
+ *   leaves     : nleaves (>= 1) distinct ranks in [0, nranks).
+ * The caller keeps every buffer valid and unmoved until hiccl_destroy.
+ * Only allowed before hiccl_init / hiccl_plan (HICCL_ERR_STATE otherwise). */
+hiccl_status_t hiccl_add_multicast(hiccl_comm_t comm, const void *const *send,
+                                   void *const *recv, size_t count, int root,
+                                   const int *leaves, int nleaves);
+
+/* Register R(leaves, root, count, op) (Sec. 3.1): after execution the root's
+ * range recv[root][0, count) holds the sum over the leaves i of
+ * send[i][0, count).  Only send[i] for i in leaves and recv[root] are read.
+ * Sum order (fixed, independent of root, stripe and pipeline): a rank
+ * contributes its values; a group of the hierarchy contributes the left fold
+ * of its non-empty subgroups' contributions in ascending subgroup order, in
+ * the payload's arithmetic (F32: IEEE round-to-nearest-even adds, no fused
+ * multiply-add; I32: wrapping adds; BF16/FP8: FP32 adds, rounded to the
+ * payload at each hierarchy level).  Ownership and state as for multicast. */
+hiccl_status_t hiccl_add_reduction(hiccl_comm_t comm, const void *const *send,
+                                   void *const *recv, size_t count,
+                                   const int *leaves, int nleaves, int root,
+                                   hiccl_op_t op);
+
+/* Register a fence (Sec. 3.3): primitives added after it depend on the
+ * earlier ones whose buffer ranges they overlap (read-after-write,
+ * write-after-read, write-after-write).  It is not a barrier. */
+hiccl_status_t hiccl_add_fence(hiccl_comm_t comm);
+
+/* ---- optimization (Sec. 4) -------------------------------------------------- */
+
+/* Factorize the registered program and upload it to the current device
+ * (Sec. 4, Sec. 5.2 "memoizing").
+ *   hierarchy : nlevels (>= 1) factors >= 1, top level first, whose product
+ *               is nranks; ranks of a level-l group are contiguous (Sec. 4.2).
+ *   stripe    : s in [1, nranks], branches per primitive (Sec. 4.3).
+ *   pipeline  : m >= 1, channels per branch (Sec. 4.5).
+ * Errors: HICCL_ERR_INVALID (arguments), HICCL_ERR_RACE (overlapping
+ * primitives within an epoch), HICCL_ERR_NOMEM / HICCL_ERR_CUDA (device
+ * memory).  Allocates the step table, dependency counters and relay buffers
+ * on the current device; they are freed by hiccl_destroy. */
+hiccl_status_t hiccl_init(hiccl_comm_t comm, const int *hierarchy, int nlevels,
+                          int stripe, int pipeline);
+
+/* Host-only variant of hiccl_init: factorize and validate without touching
+ * any GPU, so that the plan queries below work on a machine without one.
+ * Pointers are only compared, never dereferenced.  hiccl_init may follow. */
+hiccl_status_t hiccl_plan(hiccl_comm_t comm, const int *hierarchy, int nlevels,
+                          int stripe, int pipeline);
+
+/* ---- execution (Sec. 5.2) --------------------------------------------------- */
+
+/* Enqueue one execution of the collective on `cuda_stream` (a cudaStream_t,
+ * NULL for the legacy default stream) and return without waiting (the
+ * paper's non-blocking start).  HICCL_ERR_STATE before hiccl_init or while a
+ * previous start has not been waited on. */
+hiccl_status_t hiccl_start(hiccl_comm_t comm, void *cuda_stream);
+
+/* Block until the last start has finished and its buffers may be reused
+ * (the paper's blocking wait).  Returns HICCL_ERR_TIMEOUT if a dependency
+ * wait inside the executor exceeded its limit (the outputs are then
+ * undefined; the communicator is reset and may be started again), and
+ * HICCL_ERR_CUDA on a CUDA error. */
+hiccl_status_t hiccl_wait(hiccl_comm_t comm);
+
+/* ---- accounting -------------------------------------------------------------- */
+
+/* Bytes that cross each hierarchy level per execution: for every copy
+ * destination and every reduce input on another rank, the step's bytes are
+ * added to the level at which the two ranks first fall into different
+ * subgroups.  per_level receives nlevels values (top level first); nlevels
+ * must equal the hierarchy's.  Valid after hiccl_init or hiccl_plan. */
+hiccl_status_t hiccl_level_bytes(hiccl_comm_t comm, unsigned long long *per_level,
+                                 int nlevels);
+
+/* Device-memory bytes one execution reads and writes by the schedule's
+ * definition: a copy reads its bytes once and writes them once per
+ * destination; an f-input reduce reads f times its bytes and writes them once. */
+hiccl_status_t hiccl_hbm_bytes(hiccl_comm_t comm, unsigned long long *read,
+                               unsigned long long *write);
+
+typedef struct {
+  unsigned long long steps;          /* copy + reduce steps                      */
+  unsigned long long copy_steps;
+  unsigned long long reduce_steps;
+  unsigned long long items;          /* executor work items per start            */
+  unsigned long long edges;          /* dependency edges                         */
+  unsigned long long stages;         /* longest dependency chain (steps)         */
+  unsigned long long scratch_bytes;  /* relay buffers on the device              */
+  unsigned long long table_bytes;    /* step table + counters on the device      */
+  unsigned long long slots;          /* pipeline time slots of the work order    */
+} hiccl_plan_info_t;
+
+/* Summary of the factorized plan.  Valid after hiccl_init or hiccl_plan. */
+hiccl_status_t hiccl_plan_info(hiccl_comm_t comm, hiccl_plan_info_t *out);
+
+/* One step of the plan, for inspection and host-side checking.
+ *   kind: 0 copy, 1 reduce.  level: hierarchy level crossed, -1 local.
+ *   src_addr/dst_addr: device addresses, or byte offsets into the relay
+ *   arena where the matching *_scratch flag is 1.  preds: indices of the
+ *   steps this one depends on.  Arrays must hold nsrc, ndst and npreds
+ *   entries (query with NULL arrays first; counts are always written). */
+typedef struct {
+  int kind;
+  int level;
+  int nsrc;
+  int ndst;
+  int npreds;
+  int prim;
+  int branch;
+  int channel;
+  unsigned long long nbytes;
+  unsigned long long slot;
+} hiccl_step_desc_t;
+
+hiccl_status_t hiccl_get_step(hiccl_comm_t comm, unsigned long long index,
+                              hiccl_step_desc_t *desc,
+                              unsigned long long *src_addr, int *src_scratch,
+                              int *src_rank, unsigned long long *dst_addr,
+                              int *dst_scratch, int *dst_rank,
+                              unsigned long long *preds);
+
+/* ---- tuning and diagnostics -------------------------------------------------- */
+
+typedef enum {
+  HICCL_OPT_TIMEOUT_NS = 0,   /* dependency-wait limit inside the executor (default 1e9) */
+  HICCL_OPT_CTAS_PER_SM = 1,  /* resident executor CTAs per SM (default 2)               */
+  HICCL_OPT_ITEM_BYTES = 2,   /* target output bytes of one work item (default 131072)   */
+  HICCL_OPT_ORDER = 3         /* work order: 0 pipeline slots (default), 1 stage depth   */
+} hiccl_option_t;
+
+/* Set an option.  TIMEOUT_NS and CTAS_PER_SM apply to the next start;
+ * ITEM_BYTES and ORDER must be set before hiccl_init / hiccl_plan. */
+hiccl_status_t hiccl_set_option(hiccl_comm_t comm, hiccl_option_t opt, long long value);
+
+/* Fault injection for tests: add `extra` (0 restores) phantom dependencies to
+ * step `index` in the uploaded table, so that the executor's bounded wait for
+ * it runs out and hiccl_wait reports HICCL_ERR_TIMEOUT.  Host-side only: it
+ * changes one counter target; it never makes the GPU fault. */
+hiccl_status_t hiccl_debug_withhold(hiccl_comm_t comm, unsigned long long index, int extra);
+
+/* Message of the last failed call on `comm` ("" if none); a static string
+ * for comm == NULL.  Valid until the next call on comm. */
+const char *hiccl_last_error(hiccl_comm_t comm);
+
+/* Free everything the communicator owns (after waiting for a pending start).
+ * NULL is ignored. */
+void hiccl_destroy(hiccl_comm_t comm);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HICCL_H */

@@ -1,0 +1,154 @@
+// Internal data structures shared by the host factorizer (hiccl_plan.cpp) and
+// the device runtime (hiccl_runtime.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hiccl.h"
+
+#ifdef __CUDACC__
+#define HICCL_HD __host__ __device__
+#else
+#define HICCL_HD
+#endif
+
+namespace hiccl {
+
+// ---------------------------------------------------------------------------
+// device-side layout of an uploaded plan
+// ---------------------------------------------------------------------------
+
+// A warp moves one segment of a step at a time: SEG_BYTES of every operand.
+constexpr uint32_t SEG_BYTES = 4096;
+constexpr uint32_t MAX_ENTRIES_PER_ITEM = 32;
+constexpr uint32_t MAX_FANIN = 1024;    // reduce inputs / copy destinations per step
+
+enum : uint32_t { OP_COPY = 0, OP_REDUCE = 1 };
+
+// meta word of a step: op | dtype << 2 | aligned16 << 6 | nsrc << 8 (12 bits) | ndst << 20 (12 bits)
+HICCL_HD inline uint32_t meta_pack(uint32_t op, uint32_t dt, uint32_t al, uint32_t nsrc, uint32_t ndst) {
+  return op | (dt << 2) | (al << 6) | (nsrc << 8) | (ndst << 20);
+}
+HICCL_HD inline uint32_t meta_op(uint32_t m) { return m & 3u; }
+HICCL_HD inline uint32_t meta_dtype(uint32_t m) { return (m >> 2) & 15u; }
+HICCL_HD inline uint32_t meta_aligned(uint32_t m) { return (m >> 6) & 1u; }
+HICCL_HD inline uint32_t meta_nsrc(uint32_t m) { return (m >> 8) & 4095u; }
+HICCL_HD inline uint32_t meta_ndst(uint32_t m) { return (m >> 20) & 4095u; }
+
+// one contiguous run of a step's segments inside a work item
+struct DevEntry {
+  uint32_t step;
+  uint32_t seg_lo;
+  uint32_t seg_hi;
+  uint32_t pad;
+};
+
+// per-launch control block (device memory, zeroed at upload)
+struct DevCtl {
+  unsigned long long ticket;   // next work item to claim
+  unsigned long long exited;   // CTAs that left the item loop
+  unsigned long long epoch;    // completed launches; counter targets scale with it
+  unsigned long long err;      // nonzero: abort (code << 32 | step)
+};
+
+struct DevTable {
+  const unsigned long long *nbytes;   // [nsteps]
+  const uint32_t *meta;               // [nsteps]
+  const uint32_t *ptr_off;            // [nsteps] first of nsrc source then ndst destination pointers
+  const uint32_t *indeg;              // [nsteps] dependency count
+  const uint32_t *nent;               // [nsteps] entries covering the step (completion target)
+  const uint32_t *succ_off;           // [nsteps + 1]
+  const uint32_t *succ;               // [nedges]
+  const unsigned long long *ptrs;     // [nptrs] device addresses
+  const DevEntry *entries;            // [nentries]
+  const uint32_t *item_off;           // [nitems + 1] entry ranges of the work items
+  unsigned long long *dep;            // [nsteps] arrivals of predecessors (cumulative over launches)
+  unsigned long long *done;           // [nsteps] finished entries (cumulative over launches)
+  DevCtl *ctl;
+  unsigned long long *host_err;       // mapped host word mirroring ctl->err
+  unsigned long long nitems;
+  unsigned long long timeout_ns;
+};
+
+enum : uint32_t { ERR_TIMEOUT = 1, ERR_BADSTEP = 2 };
+
+// ---------------------------------------------------------------------------
+// host-side plan
+// ---------------------------------------------------------------------------
+
+struct Loc {
+  unsigned long long addr;   // device address, or relay-arena offset when scratch
+  int32_t rank;
+  uint8_t scratch;
+};
+
+struct HStep {
+  uint8_t kind;            // OP_COPY / OP_REDUCE
+  int8_t level;            // hierarchy level crossed; -1 local
+  int32_t prim;
+  int32_t epoch;
+  int32_t branch;
+  int32_t channel;
+  unsigned long long nbytes;
+  uint32_t loc0;           // first Loc: nsrc sources then ndst destinations
+  uint32_t nsrc;
+  uint32_t ndst;
+  unsigned long long slot;
+};
+
+struct Prim {
+  int kind;                                // 0 multicast, 1 reduction
+  int root;
+  std::vector<int> leaves;                 // sorted, distinct
+  size_t count;
+  std::vector<unsigned long long> send;    // per rank (0 = none)
+  std::vector<unsigned long long> recv;
+  int epoch;
+};
+
+struct DevState;   // defined by the runtime
+
+struct Plan {
+  std::vector<int> hierarchy;
+  int stripe = 1, pipeline = 1;
+  std::vector<HStep> steps;                // in execution (slot) order
+  std::vector<Loc> locs;
+  std::vector<uint32_t> pred_off, preds;   // CSR of predecessors (by new index)
+  std::vector<uint32_t> succ_off, succ;    // CSR of successors
+  std::vector<DevEntry> entries;
+  std::vector<uint32_t> item_off;
+  std::vector<uint32_t> nent;
+  unsigned long long scratch_bytes = 0;
+  std::vector<unsigned long long> level_bytes;
+  unsigned long long hbm_read = 0, hbm_write = 0;
+  unsigned long long stages = 0, slots = 0;
+  bool valid = false;
+};
+
+}  // namespace hiccl
+
+struct hiccl_comm {
+  int P = 0;
+  hiccl_dtype_t dtype = HICCL_F32;
+  int esize = 4;
+  int epochs = 1;
+  std::vector<hiccl::Prim> prims;
+  enum State { COMPOSING, PLANNED, READY, RUNNING } state = COMPOSING;
+  // options
+  unsigned long long timeout_ns = 1000000000ull;
+  int ctas_per_sm = 2;
+  unsigned long long item_bytes = 131072;
+  int order = 0;
+  hiccl::Plan plan;
+  hiccl::DevState *dev = nullptr;
+  std::string err;
+};
+
+namespace hiccl {
+hiccl_status_t fail(hiccl_comm *c, hiccl_status_t st, const std::string &msg);
+// runtime entry points (hiccl_runtime.cu)
+hiccl_status_t dev_upload(hiccl_comm *c);
+void dev_release(hiccl_comm *c);
+}  // namespace hiccl

@@ -1,0 +1,815 @@
+// Host side of the hierarchical collective engine: composition (paper Sec. 3),
+// the factorizer (Sec. 4: striping, tree, pipelining), fence dependencies,
+// race and bounds validation, the work order executed by the persistent
+// kernel, and byte accounting.  Nothing here touches a GPU.
+//
+// Readings of the paper used by the factorizer (it is silent on them):
+//  * Representative (Sec. 4.2-4.3).  A holder forwarding into a sibling
+//    subgroup targets the rank at its own offset in that subgroup when that
+//    rank is a leaf, else the subgroup's lowest leaf; empty subgroups are
+//    pruned.  Reductions mirror multicasts.
+//  * Stripe ranks (Sec. 4.3).  Branch b of s is rooted at offset (o + b) mod G
+//    of the root's smallest enclosing group of G >= s ranks (o = the root's
+//    offset); a primitive whose leaves all lie in that group is not striped.
+//  * Pieces (Sec. 4.5).  count is cut into s*m pieces at
+//    min(count, roundup(ceil(count*k/(s*m)), 16 bytes)); branch b owns pieces
+//    b*m .. b*m+m-1 (its m pipeline channels).
+//  * Self-delivery.  A multicast root that is a leaf with a separate
+//    destination copies its piece locally in its own branch and receives the
+//    other branches' pieces like any leaf; in place it takes no part.
+//  * Fences (Sec. 3.3) become per-step edges from overlapping accesses.
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "hiccl_internal.h"
+
+using namespace hiccl;
+
+namespace hiccl {
+
+hiccl_status_t fail(hiccl_comm *c, hiccl_status_t st, const std::string &msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+static int esize_of(hiccl_dtype_t dt) {
+  switch (dt) {
+    case HICCL_F32: return 4;
+    case HICCL_I32: return 4;
+    case HICCL_BF16: return 2;
+    case HICCL_FP8E4M3: return 1;
+  }
+  return 0;
+}
+
+// elements per piece-boundary quantum: 16 bytes, or the 128-element FP8 scale block
+static unsigned long long quantum_of(hiccl_dtype_t dt) {
+  switch (dt) {
+    case HICCL_F32: return 4;
+    case HICCL_I32: return 4;
+    case HICCL_BF16: return 8;
+    case HICCL_FP8E4M3: return 128;
+  }
+  return 1;
+}
+
+namespace {
+
+struct Builder {
+  const hiccl_comm &c;
+  std::vector<int> h;
+  std::vector<long long> G;   // G[l] = prod h[l..]
+  int L;
+  int s, m;
+  std::vector<HStep> steps;
+  std::vector<Loc> locs;
+  std::vector<std::pair<uint32_t, uint32_t>> edges;   // (pred, succ) in emission order
+  unsigned long long scratch_top = 0;
+  // current emission context
+  int cur_prim = 0, cur_epoch = 0, cur_branch = 0, cur_channel = 0;
+  const Prim *p = nullptr;
+  unsigned long long cur_off = 0, cur_n = 0;
+
+  Builder(const hiccl_comm &comm, const std::vector<int> &hier, int stripe, int pipeline)
+      : c(comm), h(hier), L((int)hier.size()), s(stripe), m(pipeline) {
+    G.assign(L + 1, 1);
+    for (int l = L - 1; l >= 0; --l) G[l] = G[l + 1] * h[l];
+  }
+
+  int level_of(int a, int b) const {
+    if (a == b) return -1;
+    for (int l = 0; l < L; ++l)
+      if (a / G[l + 1] != b / G[l + 1]) return l;
+    return -1;
+  }
+
+  int emit(uint8_t kind, const std::vector<Loc> &srcs, const std::vector<Loc> &dsts, int level,
+           const std::vector<int> &preds) {
+    HStep st{};
+    st.kind = kind;
+    st.level = (int8_t)level;
+    st.prim = cur_prim;
+    st.epoch = cur_epoch;
+    st.branch = cur_branch;
+    st.channel = cur_channel;
+    st.nbytes = cur_n;
+    st.loc0 = (uint32_t)locs.size();
+    st.nsrc = (uint32_t)srcs.size();
+    st.ndst = (uint32_t)dsts.size();
+    locs.insert(locs.end(), srcs.begin(), srcs.end());
+    locs.insert(locs.end(), dsts.begin(), dsts.end());
+    int idx = (int)steps.size();
+    steps.push_back(st);
+    for (int q : preds)
+      if (q >= 0) edges.emplace_back((uint32_t)q, (uint32_t)idx);
+    return idx;
+  }
+
+  Loc scratch_loc(int rank) {
+    unsigned long long off = (scratch_top + 255ull) & ~255ull;
+    scratch_top = off + cur_n;
+    return Loc{off, rank, 1};
+  }
+  Loc send_loc(int r) const { return Loc{p->send[r] + cur_off, r, 0}; }
+  Loc recv_loc(int r) const { return Loc{p->recv[r] + cur_off, r, 0}; }
+  static bool same(const Loc &a, const Loc &b) { return a.addr == b.addr && a.scratch == b.scratch; }
+
+  // leaves of `sorted` inside [lo, hi)
+  static std::vector<int> inside(const std::vector<int> &sorted, long long lo, long long hi) {
+    auto a = std::lower_bound(sorted.begin(), sorted.end(), (int)lo);
+    auto b = std::lower_bound(sorted.begin(), sorted.end(), (int)hi);
+    return std::vector<int>(a, b);
+  }
+  static int pick_rep(long long qbase, long long sub, int holder, const std::vector<int> &ql) {
+    int cand = (int)(qbase + holder % sub);
+    return std::binary_search(ql.begin(), ql.end(), cand) ? cand : ql.front();
+  }
+
+  std::vector<int> stripe_ranks(int root, const std::vector<int> &leaves) const {
+    if (s == 1) return {root};
+    int l = L;
+    while (G[l] < s) --l;   // smallest enclosing group with >= s ranks
+    long long g = G[l];
+    long long base = root - root % g, o = root % g;
+    bool all_inside = true;
+    for (int r : leaves)
+      if (r < base || r >= base + g) { all_inside = false; break; }
+    if (all_inside) return {root};
+    std::vector<int> ks(s);
+    for (int b = 0; b < s; ++b) ks[b] = (int)(base + (o + b) % g);
+    return ks;
+  }
+
+  // ---- multicast tree: deliver from `holder` to every rank of `leaves` ---------
+  void mcast_tree(int l, long long base, int holder, Loc src, int src_step,
+                  const std::vector<int> &leaves) {
+    if (l == L || leaves.empty()) return;
+    long long sub = G[l + 1];
+    std::vector<int> own;
+    long long own_base = -1;
+    std::vector<std::pair<long long, std::vector<int>>> hops;   // (qbase, leaves) per rep
+    std::vector<int> reps;
+    for (int q = 0; q < h[l]; ++q) {
+      long long qb = base + q * sub;
+      std::vector<int> ql = inside(leaves, qb, qb + sub);
+      if (holder >= qb && holder < qb + sub) {
+        own = std::move(ql);
+        own_base = qb;
+      } else if (!ql.empty()) {
+        reps.push_back(pick_rep(qb, sub, holder, ql));
+        hops.emplace_back(qb, std::move(ql));
+      }
+    }
+    int hop_step = -1;
+    if (!reps.empty()) {
+      std::vector<Loc> dsts;
+      for (int r : reps) dsts.push_back(recv_loc(r));
+      hop_step = emit(OP_COPY, {src}, dsts, l, {src_step});
+    }
+    if (own_base >= 0) mcast_tree(l + 1, own_base, holder, src, src_step, own);
+    for (size_t k = 0; k < reps.size(); ++k) {
+      std::vector<int> rest;
+      for (int r : hops[k].second)
+        if (r != reps[k]) rest.push_back(r);
+      mcast_tree(l + 1, hops[k].first, reps[k], recv_loc(reps[k]), hop_step, rest);
+    }
+  }
+
+  // ---- reduction tree: fold `leaves` at `target`; returns (location, producer) ----
+  std::pair<Loc, int> red_tree(int l, long long base, int target, const std::vector<int> &leaves,
+                               const Loc *out) {
+    if (l == L) {
+      Loc ref = send_loc(target);
+      if (!out || same(*out, ref)) return {ref, -1};
+      int st = emit(OP_COPY, {ref}, {*out}, -1, {});
+      return {*out, st};
+    }
+    long long sub = G[l + 1];
+    struct Part { long long qb; int rep; std::vector<int> ql; };
+    std::vector<Part> parts;
+    for (int q = 0; q < h[l]; ++q) {
+      long long qb = base + q * sub;
+      std::vector<int> ql = inside(leaves, qb, qb + sub);
+      if (ql.empty()) continue;
+      int rep = (target >= qb && target < qb + sub) ? target : pick_rep(qb, sub, target, ql);
+      parts.push_back(Part{qb, rep, std::move(ql)});
+    }
+    if (parts.size() == 1 && parts[0].rep == target)
+      return red_tree(l + 1, parts[0].qb, target, parts[0].ql, out);
+    std::vector<Loc> ins;
+    std::vector<int> producers;
+    for (auto &pt : parts) {
+      auto r = red_tree(l + 1, pt.qb, pt.rep, pt.ql, nullptr);
+      ins.push_back(r.first);
+      producers.push_back(r.second);
+    }
+    Loc o = out ? *out : scratch_loc(target);
+    int st = emit(ins.size() > 1 ? OP_REDUCE : OP_COPY, ins, {o}, l, producers);
+    return {o, st};
+  }
+
+  std::vector<unsigned long long> bounds(size_t count, int parts) const {
+    unsigned long long q = quantum_of(c.dtype);
+    std::vector<unsigned long long> b(parts + 1);
+    for (int k = 0; k <= parts; ++k) {
+      unsigned __int128 num = (unsigned __int128)count * (unsigned)k;
+      unsigned long long v = (unsigned long long)((num + parts - 1) / parts);
+      v = (v + q - 1) / q * q;
+      b[k] = std::min<unsigned long long>(v, count);
+    }
+    return b;
+  }
+
+  void multicast(const Prim &pr) {
+    std::vector<int> ks = stripe_ranks(pr.root, pr.leaves);
+    int nb = (int)ks.size();
+    auto bd = bounds(pr.count, nb * m);
+    bool leaf_root = std::binary_search(pr.leaves.begin(), pr.leaves.end(), pr.root);
+    bool self_copy = leaf_root && pr.recv[pr.root] != pr.send[pr.root];
+    std::vector<int> others;
+    for (int j : pr.leaves)
+      if (j != pr.root) others.push_back(j);
+    for (int b = 0; b < nb; ++b) {
+      for (int ch = 0; ch < m; ++ch) {
+        unsigned long long lo = bd[b * m + ch], hi = bd[b * m + ch + 1];
+        if (hi <= lo) continue;
+        cur_branch = b;
+        cur_channel = ch;
+        cur_off = lo * c.esize;
+        cur_n = (hi - lo) * c.esize;
+        int k = ks[b];
+        Loc src = send_loc(pr.root);
+        if (k == pr.root) {
+          if (self_copy) emit(OP_COPY, {src}, {recv_loc(pr.root)}, -1, {});
+          mcast_tree(0, 0, k, src, -1, others);
+        } else {
+          bool k_leaf = std::binary_search(pr.leaves.begin(), pr.leaves.end(), k);
+          Loc dst = k_leaf ? recv_loc(k) : scratch_loc(k);
+          int s0 = emit(OP_COPY, {src}, {dst}, level_of(pr.root, k), {});
+          std::vector<int> branch;
+          for (int j : others)
+            if (j != k) branch.push_back(j);
+          if (self_copy) branch.insert(std::lower_bound(branch.begin(), branch.end(), pr.root), pr.root);
+          mcast_tree(0, 0, k, dst, s0, branch);
+        }
+      }
+    }
+  }
+
+  void reduction(const Prim &pr) {
+    std::vector<int> ks = stripe_ranks(pr.root, pr.leaves);
+    int nb = (int)ks.size();
+    auto bd = bounds(pr.count, nb * m);
+    for (int b = 0; b < nb; ++b) {
+      for (int ch = 0; ch < m; ++ch) {
+        unsigned long long lo = bd[b * m + ch], hi = bd[b * m + ch + 1];
+        if (hi <= lo) continue;
+        cur_branch = b;
+        cur_channel = ch;
+        cur_off = lo * c.esize;
+        cur_n = (hi - lo) * c.esize;
+        int k = ks[b];
+        Loc fin = recv_loc(pr.root);
+        if (k == pr.root) {
+          red_tree(0, 0, k, pr.leaves, &fin);
+        } else {
+          auto r = red_tree(0, 0, k, pr.leaves, nullptr);
+          emit(OP_COPY, {r.first}, {fin}, level_of(k, pr.root), {r.second});
+        }
+      }
+    }
+  }
+};
+
+struct Access {
+  unsigned long long lo, hi;
+  uint32_t step;
+  bool write;
+};
+
+// fence dependencies (Sec. 3.3): edges from earlier-epoch steps to the steps
+// of epoch e whose user-buffer accesses conflict with theirs
+void fence_edges(Builder &B, const std::vector<uint32_t> &epoch_first) {
+  auto collect = [&](uint32_t s, std::vector<Access> &out) {
+    const HStep &st = B.steps[s];
+    for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k) {
+      const Loc &l = B.locs[st.loc0 + k];
+      if (l.scratch) continue;
+      out.push_back(Access{l.addr, l.addr + st.nbytes, s, k >= st.nsrc});
+    }
+  };
+  for (size_t e = 1; e + 1 < epoch_first.size(); ++e) {
+    uint32_t first = epoch_first[e], end = epoch_first[e + 1];
+    if (first == end || first == 0) continue;
+    std::vector<Access> prev;
+    for (uint32_t s = 0; s < first; ++s) collect(s, prev);
+    if (prev.empty()) continue;
+    std::sort(prev.begin(), prev.end(), [](const Access &a, const Access &b) { return a.lo < b.lo; });
+    std::vector<unsigned long long> pmax(prev.size());
+    for (size_t k = 0; k < prev.size(); ++k) pmax[k] = std::max(prev[k].hi, k ? pmax[k - 1] : 0ull);
+    std::vector<Access> cur;
+    for (uint32_t s = first; s < end; ++s) {
+      cur.clear();
+      collect(s, cur);
+      std::vector<uint32_t> found;
+      for (const Access &a : cur) {
+        size_t k = std::lower_bound(prev.begin(), prev.end(), a.hi,
+                                    [](const Access &x, unsigned long long v) { return x.lo < v; }) -
+                   prev.begin();
+        while (k > 0) {
+          --k;
+          if (pmax[k] <= a.lo) break;
+          const Access &b = prev[k];
+          if (b.hi > a.lo && b.lo < a.hi && (a.write || b.write)) found.push_back(b.step);
+        }
+      }
+      std::sort(found.begin(), found.end());
+      found.erase(std::unique(found.begin(), found.end()), found.end());
+      for (uint32_t q : found) B.edges.emplace_back(q, s);
+    }
+  }
+}
+
+struct Range {
+  unsigned long long lo, hi;
+  int prim;
+  bool write;
+};
+
+// race check (Sec. 3.2): primitives of one epoch must not write what another
+// reads or writes; a primitive's own writes must not overlap each other or its
+// reads, except an exact in-place root
+bool find_race(const hiccl_comm &c, std::string &msg) {
+  for (int e = 0; e < c.epochs; ++e) {
+    std::vector<Range> rs;
+    for (size_t i = 0; i < c.prims.size(); ++i) {
+      const Prim &p = c.prims[i];
+      if (p.epoch != e || p.count == 0) continue;
+      unsigned long long n = (unsigned long long)p.count * c.esize;
+      if (p.kind == 0) {
+        rs.push_back(Range{p.send[p.root], p.send[p.root] + n, (int)i, false});
+        for (int j : p.leaves) {
+          if (j == p.root && p.recv[j] == p.send[p.root]) continue;
+          rs.push_back(Range{p.recv[j], p.recv[j] + n, (int)i, true});
+        }
+      } else {
+        for (int j : p.leaves) {
+          if (j == p.root && p.send[j] == p.recv[p.root]) continue;   // exact in place
+          rs.push_back(Range{p.send[j], p.send[j] + n, (int)i, false});
+        }
+        rs.push_back(Range{p.recv[p.root], p.recv[p.root] + n, (int)i, true});
+      }
+    }
+    std::sort(rs.begin(), rs.end(), [](const Range &a, const Range &b) { return a.lo < b.lo; });
+    for (size_t a = 0; a < rs.size(); ++a) {
+      for (size_t b = a + 1; b < rs.size() && rs[b].lo < rs[a].hi; ++b) {
+        if (!(rs[a].write || rs[b].write)) continue;
+        msg = "primitives " + std::to_string(rs[a].prim) + " and " + std::to_string(rs[b].prim) +
+              " overlap in epoch " + std::to_string(e);
+        return true;
+      }
+    }
+  }
+  return false;
+}
+
+}  // namespace
+
+static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevels, int stripe,
+                                 int pipeline) {
+  if (!hierarchy || nlevels < 1 || nlevels > 64) return fail(c, HICCL_ERR_INVALID, "bad hierarchy");
+  std::vector<int> h(hierarchy, hierarchy + nlevels);
+  long long prod = 1;
+  for (int f : h) {
+    if (f < 1) return fail(c, HICCL_ERR_INVALID, "hierarchy factors must be >= 1");
+    prod *= f;
+    if (prod > (1ll << 30)) return fail(c, HICCL_ERR_INVALID, "hierarchy product too large");
+  }
+  if (prod != c->P)
+    return fail(c, HICCL_ERR_INVALID, "product of hierarchy (" + std::to_string(prod) +
+                                          ") != nranks (" + std::to_string(c->P) + ")");
+  if (stripe < 1 || stripe > c->P) return fail(c, HICCL_ERR_INVALID, "stripe must be in [1, nranks]");
+  if (pipeline < 1 || pipeline > 65536) return fail(c, HICCL_ERR_INVALID, "pipeline must be in [1, 65536]");
+  std::string msg;
+  if (find_race(*c, msg)) return fail(c, HICCL_ERR_RACE, "race: " + msg);
+
+  Builder B(*c, h, stripe, pipeline);
+  std::vector<uint32_t> epoch_first(c->epochs + 1, 0);
+  int e_seen = 0;
+  for (size_t i = 0; i < c->prims.size(); ++i) {
+    const Prim &p = c->prims[i];
+    while (e_seen < p.epoch) epoch_first[++e_seen] = (uint32_t)B.steps.size();
+    if (p.count == 0) continue;
+    B.p = &p;
+    B.cur_prim = (int)i;
+    B.cur_epoch = p.epoch;
+    if (p.kind == 0) B.multicast(p);
+    else B.reduction(p);
+    if (B.steps.size() > 0xFFFFFFF0ull) return fail(c, HICCL_ERR_NOMEM, "too many steps");
+  }
+  while (e_seen < c->epochs) epoch_first[++e_seen] = (uint32_t)B.steps.size();
+  fence_edges(B, epoch_first);
+
+  const size_t N = B.steps.size();
+  for (const HStep &st : B.steps)
+    if (st.nsrc > MAX_FANIN || st.ndst > MAX_FANIN)
+      return fail(c, HICCL_ERR_UNSUPPORTED, "a step has more than 1024 inputs or outputs");
+
+  // bounds: every user location lies in its primitive's registered range
+  for (const HStep &st : B.steps) {
+    const Prim &p = c->prims[st.prim];
+    unsigned long long n = (unsigned long long)p.count * c->esize;
+    for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k) {
+      const Loc &l = B.locs[st.loc0 + k];
+      bool ok;
+      if (l.scratch) {
+        ok = l.addr + st.nbytes <= B.scratch_top;
+      } else {
+        unsigned long long base_s = p.send[l.rank], base_r = p.recv[l.rank];
+        ok = (base_s && l.addr >= base_s && l.addr + st.nbytes <= base_s + n) ||
+             (base_r && l.addr >= base_r && l.addr + st.nbytes <= base_r + n);
+      }
+      if (!ok) return fail(c, HICCL_ERR_INVALID, "internal: step outside its primitive's buffers");
+    }
+  }
+
+  // predecessor lists in emission order (every edge points backwards)
+  std::vector<uint32_t> pcount(N + 1, 0);
+  std::sort(B.edges.begin(), B.edges.end(), [](auto &a, auto &b) {
+    return a.second != b.second ? a.second < b.second : a.first < b.first;
+  });
+  B.edges.erase(std::unique(B.edges.begin(), B.edges.end()), B.edges.end());
+  for (auto &e : B.edges) {
+    if (e.first >= e.second) return fail(c, HICCL_ERR_INVALID, "internal: forward dependency");
+    pcount[e.second + 1]++;
+  }
+  for (size_t i = 0; i < N; ++i) pcount[i + 1] += pcount[i];
+
+  // stage depth and pipeline slot: a step runs one slot after its latest
+  // predecessor, and channel c of a branch starts at slot c (Sec. 4.5, Fig. 7)
+  std::vector<unsigned long long> depth(N, 0), slot(N, 0);
+  unsigned long long maxdepth = 0, maxslot = 0;
+  for (size_t i = 0; i < N; ++i) {
+    unsigned long long d = 0, sl = 0;
+    for (uint32_t k = pcount[i]; k < pcount[i + 1]; ++k) {
+      uint32_t q = B.edges[k].first;
+      d = std::max(d, depth[q] + 1);
+      sl = std::max(sl, slot[q] + 1);
+    }
+    depth[i] = d;
+    slot[i] = c->order == 0 ? std::max<unsigned long long>(sl, (unsigned long long)B.steps[i].channel) : d;
+    maxdepth = std::max(maxdepth, d);
+    maxslot = std::max(maxslot, slot[i]);
+  }
+
+  // execution order: by slot, then emission order (stable)
+  std::vector<uint32_t> order(N);
+  std::iota(order.begin(), order.end(), 0u);
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return slot[a] < slot[b]; });
+  std::vector<uint32_t> pos(N);
+  for (size_t k = 0; k < N; ++k) pos[order[k]] = (uint32_t)k;
+
+  Plan plan;
+  plan.hierarchy = h;
+  plan.stripe = stripe;
+  plan.pipeline = pipeline;
+  plan.steps.resize(N);
+  plan.locs.reserve(B.locs.size());
+  for (size_t k = 0; k < N; ++k) {
+    HStep st = B.steps[order[k]];
+    uint32_t n = st.nsrc + st.ndst;
+    uint32_t old0 = st.loc0;
+    st.loc0 = (uint32_t)plan.locs.size();
+    st.slot = slot[order[k]];
+    plan.locs.insert(plan.locs.end(), B.locs.begin() + old0, B.locs.begin() + old0 + n);
+    plan.steps[k] = st;
+  }
+  // predecessor and successor CSR in the new numbering
+  plan.pred_off.assign(N + 1, 0);
+  plan.succ_off.assign(N + 1, 0);
+  for (auto &e : B.edges) {
+    plan.pred_off[pos[e.second] + 1]++;
+    plan.succ_off[pos[e.first] + 1]++;
+  }
+  for (size_t i = 0; i < N; ++i) {
+    plan.pred_off[i + 1] += plan.pred_off[i];
+    plan.succ_off[i + 1] += plan.succ_off[i];
+  }
+  plan.preds.resize(B.edges.size());
+  plan.succ.resize(B.edges.size());
+  {
+    std::vector<uint32_t> pf(plan.pred_off.begin(), plan.pred_off.end() - 1);
+    std::vector<uint32_t> sf(plan.succ_off.begin(), plan.succ_off.end() - 1);
+    for (auto &e : B.edges) {
+      uint32_t a = pos[e.first], b = pos[e.second];
+      plan.preds[pf[b]++] = a;
+      plan.succ[sf[a]++] = b;
+    }
+    for (size_t i = 0; i < N; ++i) {
+      std::sort(plan.preds.begin() + plan.pred_off[i], plan.preds.begin() + plan.pred_off[i + 1]);
+      std::sort(plan.succ.begin() + plan.succ_off[i], plan.succ.begin() + plan.succ_off[i + 1]);
+    }
+  }
+
+  // work items: consecutive steps of one slot (so no item depends on itself),
+  // cut into runs of at most item_bytes / SEG_BYTES segments
+  unsigned long long cap = std::max<unsigned long long>(1, c->item_bytes / SEG_BYTES);
+  plan.nent.assign(N, 0);
+  plan.item_off.push_back(0);
+  unsigned long long cur_segs = 0;
+  unsigned long long cur_slot = ~0ull;
+  auto close_item = [&]() {
+    if (plan.entries.size() > plan.item_off.back()) plan.item_off.push_back((uint32_t)plan.entries.size());
+    cur_segs = 0;
+  };
+  for (size_t k = 0; k < N; ++k) {
+    const HStep &st = plan.steps[k];
+    if (st.slot != cur_slot) {
+      close_item();
+      cur_slot = st.slot;
+    }
+    unsigned long long nseg = (st.nbytes + SEG_BYTES - 1) / SEG_BYTES;
+    if (nseg > 0xFFFFFFFFull) return fail(c, HICCL_ERR_UNSUPPORTED, "step too large");
+    unsigned long long done = 0;
+    while (done < nseg) {
+      unsigned long long take = std::min(nseg - done, cap - cur_segs);
+      plan.entries.push_back(DevEntry{(uint32_t)k, (uint32_t)done, (uint32_t)(done + take), 0});
+      plan.nent[k]++;
+      done += take;
+      cur_segs += take;
+      if (cur_segs >= cap || plan.entries.size() - plan.item_off.back() >= MAX_ENTRIES_PER_ITEM)
+        close_item();
+    }
+  }
+  close_item();
+
+  // accounting
+  plan.level_bytes.assign(h.size(), 0);
+  for (const HStep &st : plan.steps) {
+    const Loc *l = &plan.locs[st.loc0];
+    if (st.kind == OP_COPY) {
+      plan.hbm_read += st.nbytes;
+      plan.hbm_write += st.nbytes * st.ndst;
+      for (uint32_t k = 0; k < st.ndst; ++k) {
+        int lv = B.level_of(l[0].rank, l[st.nsrc + k].rank);
+        if (lv >= 0) plan.level_bytes[lv] += st.nbytes;
+      }
+    } else {
+      plan.hbm_read += st.nbytes * st.nsrc;
+      plan.hbm_write += st.nbytes;
+      for (uint32_t k = 0; k < st.nsrc; ++k) {
+        int lv = B.level_of(l[k].rank, l[st.nsrc].rank);
+        if (lv >= 0) plan.level_bytes[lv] += st.nbytes;
+      }
+    }
+  }
+  plan.scratch_bytes = B.scratch_top;
+  plan.stages = N ? maxdepth + 1 : 0;
+  plan.slots = N ? maxslot + 1 : 0;
+  plan.valid = true;
+  c->plan = std::move(plan);
+  return HICCL_OK;
+}
+
+}  // namespace hiccl
+
+// ============================================================================
+// C ABI: composition, planning, queries
+// ============================================================================
+
+extern "C" {
+
+hiccl_status_t hiccl_create(int nranks, hiccl_dtype_t dtype, hiccl_comm_t *out) {
+  if (!out) return HICCL_ERR_INVALID;
+  *out = nullptr;
+  if (nranks < 1 || nranks > (1 << 30)) return HICCL_ERR_INVALID;
+  if (esize_of(dtype) == 0) return HICCL_ERR_INVALID;
+  hiccl_comm *c = new (std::nothrow) hiccl_comm();
+  if (!c) return HICCL_ERR_NOMEM;
+  c->P = nranks;
+  c->dtype = dtype;
+  c->esize = esize_of(dtype);
+  *out = c;
+  return HICCL_OK;
+}
+
+static hiccl_status_t check_leaves(hiccl_comm *c, const int *leaves, int nleaves, std::vector<int> &out) {
+  if (!leaves || nleaves < 1) return fail(c, HICCL_ERR_INVALID, "need at least one leaf");
+  if (nleaves > c->P) return fail(c, HICCL_ERR_INVALID, "more leaves than ranks");
+  out.assign(leaves, leaves + nleaves);
+  for (int r : out)
+    if (r < 0 || r >= c->P) return fail(c, HICCL_ERR_INVALID, "leaf rank out of range");
+  std::sort(out.begin(), out.end());
+  if (std::adjacent_find(out.begin(), out.end()) != out.end())
+    return fail(c, HICCL_ERR_INVALID, "duplicate leaf");
+  return HICCL_OK;
+}
+
+static bool aligned_elem(const hiccl_comm *c, unsigned long long a) { return a % c->esize == 0; }
+
+hiccl_status_t hiccl_add_multicast(hiccl_comm_t c, const void *const *send, void *const *recv,
+                                   size_t count, int root, const int *leaves, int nleaves) {
+  if (!c) return HICCL_ERR_INVALID;
+  if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "add after init");
+  if (!send || !recv) return fail(c, HICCL_ERR_INVALID, "null pointer array");
+  if (root < 0 || root >= c->P) return fail(c, HICCL_ERR_INVALID, "root out of range");
+  Prim p;
+  p.kind = 0;
+  p.root = root;
+  p.count = count;
+  p.epoch = c->epochs - 1;
+  hiccl_status_t st = check_leaves(c, leaves, nleaves, p.leaves);
+  if (st != HICCL_OK) return st;
+  p.send.assign(c->P, 0);
+  p.recv.assign(c->P, 0);
+  p.send[root] = (unsigned long long)(uintptr_t)send[root];
+  for (int j : p.leaves) p.recv[j] = (unsigned long long)(uintptr_t)recv[j];
+  if (count > 0) {
+    if (!p.send[root]) return fail(c, HICCL_ERR_INVALID, "null send buffer at the root");
+    for (int j : p.leaves)
+      if (!p.recv[j]) return fail(c, HICCL_ERR_INVALID, "null recv buffer at a leaf");
+    if (!aligned_elem(c, p.send[root])) return fail(c, HICCL_ERR_INVALID, "misaligned send buffer");
+    for (int j : p.leaves)
+      if (!aligned_elem(c, p.recv[j])) return fail(c, HICCL_ERR_INVALID, "misaligned recv buffer");
+    if ((unsigned long long)count > (~0ull) / 8) return fail(c, HICCL_ERR_INVALID, "count too large");
+  }
+  c->prims.push_back(std::move(p));
+  return HICCL_OK;
+}
+
+hiccl_status_t hiccl_add_reduction(hiccl_comm_t c, const void *const *send, void *const *recv,
+                                   size_t count, const int *leaves, int nleaves, int root,
+                                   hiccl_op_t op) {
+  if (!c) return HICCL_ERR_INVALID;
+  if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "add after init");
+  if (!send || !recv) return fail(c, HICCL_ERR_INVALID, "null pointer array");
+  if (op != HICCL_SUM) return fail(c, HICCL_ERR_UNSUPPORTED, "only HICCL_SUM is implemented");
+  if (c->dtype != HICCL_F32 && c->dtype != HICCL_I32)
+    return fail(c, HICCL_ERR_UNSUPPORTED, "reductions of this dtype are not implemented");
+  if (root < 0 || root >= c->P) return fail(c, HICCL_ERR_INVALID, "root out of range");
+  Prim p;
+  p.kind = 1;
+  p.root = root;
+  p.count = count;
+  p.epoch = c->epochs - 1;
+  hiccl_status_t st = check_leaves(c, leaves, nleaves, p.leaves);
+  if (st != HICCL_OK) return st;
+  p.send.assign(c->P, 0);
+  p.recv.assign(c->P, 0);
+  for (int j : p.leaves) p.send[j] = (unsigned long long)(uintptr_t)send[j];
+  p.recv[root] = (unsigned long long)(uintptr_t)recv[root];
+  if (count > 0) {
+    if (!p.recv[root]) return fail(c, HICCL_ERR_INVALID, "null recv buffer at the root");
+    for (int j : p.leaves)
+      if (!p.send[j]) return fail(c, HICCL_ERR_INVALID, "null send buffer at a leaf");
+    if (!aligned_elem(c, p.recv[root])) return fail(c, HICCL_ERR_INVALID, "misaligned recv buffer");
+    for (int j : p.leaves)
+      if (!aligned_elem(c, p.send[j])) return fail(c, HICCL_ERR_INVALID, "misaligned send buffer");
+    if ((unsigned long long)count > (~0ull) / 8) return fail(c, HICCL_ERR_INVALID, "count too large");
+  }
+  c->prims.push_back(std::move(p));
+  return HICCL_OK;
+}
+
+hiccl_status_t hiccl_add_fence(hiccl_comm_t c) {
+  if (!c) return HICCL_ERR_INVALID;
+  if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "add after init");
+  c->epochs++;
+  return HICCL_OK;
+}
+
+hiccl_status_t hiccl_plan(hiccl_comm_t c, const int *hierarchy, int nlevels, int stripe, int pipeline) {
+  if (!c) return HICCL_ERR_INVALID;
+  if (c->state == hiccl_comm::READY || c->state == hiccl_comm::RUNNING)
+    return fail(c, HICCL_ERR_STATE, "already initialized");
+  hiccl_status_t st = build_plan(c, hierarchy, nlevels, stripe, pipeline);
+  if (st == HICCL_OK) c->state = hiccl_comm::PLANNED;
+  return st;
+}
+
+hiccl_status_t hiccl_init(hiccl_comm_t c, const int *hierarchy, int nlevels, int stripe, int pipeline) {
+  if (!c) return HICCL_ERR_INVALID;
+  if (c->state == hiccl_comm::READY || c->state == hiccl_comm::RUNNING)
+    return fail(c, HICCL_ERR_STATE, "already initialized");
+  hiccl_status_t st = build_plan(c, hierarchy, nlevels, stripe, pipeline);
+  if (st != HICCL_OK) return st;
+  c->state = hiccl_comm::PLANNED;
+  st = dev_upload(c);
+  if (st != HICCL_OK) return st;
+  c->state = hiccl_comm::READY;
+  return HICCL_OK;
+}
+
+hiccl_status_t hiccl_level_bytes(hiccl_comm_t c, unsigned long long *per_level, int nlevels) {
+  if (!c) return HICCL_ERR_INVALID;
+  if (!c->plan.valid) return fail(c, HICCL_ERR_STATE, "no plan");
+  if (!per_level || nlevels != (int)c->plan.level_bytes.size())
+    return fail(c, HICCL_ERR_INVALID, "nlevels must equal the hierarchy's");
+  for (int l = 0; l < nlevels; ++l) per_level[l] = c->plan.level_bytes[l];
+  return HICCL_OK;
+}
+
+hiccl_status_t hiccl_hbm_bytes(hiccl_comm_t c, unsigned long long *rd, unsigned long long *wr) {
+  if (!c) return HICCL_ERR_INVALID;
+  if (!c->plan.valid) return fail(c, HICCL_ERR_STATE, "no plan");
+  if (rd) *rd = c->plan.hbm_read;
+  if (wr) *wr = c->plan.hbm_write;
+  return HICCL_OK;
+}
+
+hiccl_status_t hiccl_plan_info(hiccl_comm_t c, hiccl_plan_info_t *out) {
+  if (!c || !out) return HICCL_ERR_INVALID;
+  if (!c->plan.valid) return fail(c, HICCL_ERR_STATE, "no plan");
+  const Plan &p = c->plan;
+  std::memset(out, 0, sizeof(*out));
+  out->steps = p.steps.size();
+  for (const HStep &st : p.steps) (st.kind == OP_COPY ? out->copy_steps : out->reduce_steps)++;
+  out->items = p.item_off.size() - 1;
+  out->edges = p.succ.size();
+  out->stages = p.stages;
+  out->slots = p.slots;
+  out->scratch_bytes = p.scratch_bytes;
+  unsigned long long N = p.steps.size();
+  out->table_bytes = N * (8 + 4 * 5 + 16) + 4 + p.succ.size() * 4 + p.locs.size() * 8 +
+                     p.entries.size() * sizeof(DevEntry) + p.item_off.size() * 4 + sizeof(DevCtl);
+  return HICCL_OK;
+}
+
+hiccl_status_t hiccl_get_step(hiccl_comm_t c, unsigned long long index, hiccl_step_desc_t *d,
+                              unsigned long long *src_addr, int *src_scratch, int *src_rank,
+                              unsigned long long *dst_addr, int *dst_scratch, int *dst_rank,
+                              unsigned long long *preds) {
+  if (!c || !d) return HICCL_ERR_INVALID;
+  if (!c->plan.valid) return fail(c, HICCL_ERR_STATE, "no plan");
+  const Plan &p = c->plan;
+  if (index >= p.steps.size()) return fail(c, HICCL_ERR_INVALID, "step index out of range");
+  const HStep &st = p.steps[index];
+  d->kind = st.kind;
+  d->level = st.level;
+  d->nsrc = (int)st.nsrc;
+  d->ndst = (int)st.ndst;
+  d->npreds = (int)(p.pred_off[index + 1] - p.pred_off[index]);
+  d->prim = st.prim;
+  d->branch = st.branch;
+  d->channel = st.channel;
+  d->nbytes = st.nbytes;
+  d->slot = st.slot;
+  for (uint32_t k = 0; k < st.nsrc; ++k) {
+    const Loc &l = p.locs[st.loc0 + k];
+    if (src_addr) src_addr[k] = l.addr;
+    if (src_scratch) src_scratch[k] = l.scratch;
+    if (src_rank) src_rank[k] = l.rank;
+  }
+  for (uint32_t k = 0; k < st.ndst; ++k) {
+    const Loc &l = p.locs[st.loc0 + st.nsrc + k];
+    if (dst_addr) dst_addr[k] = l.addr;
+    if (dst_scratch) dst_scratch[k] = l.scratch;
+    if (dst_rank) dst_rank[k] = l.rank;
+  }
+  if (preds)
+    for (uint32_t k = p.pred_off[index]; k < p.pred_off[index + 1]; ++k) preds[k - p.pred_off[index]] = p.preds[k];
+  return HICCL_OK;
+}
+
+hiccl_status_t hiccl_set_option(hiccl_comm_t c, hiccl_option_t opt, long long value) {
+  if (!c) return HICCL_ERR_INVALID;
+  switch (opt) {
+    case HICCL_OPT_TIMEOUT_NS:
+      if (value < 1000) return fail(c, HICCL_ERR_INVALID, "timeout below 1 us");
+      c->timeout_ns = (unsigned long long)value;
+      return HICCL_OK;
+    case HICCL_OPT_CTAS_PER_SM:
+      if (value < 1 || value > 32) return fail(c, HICCL_ERR_INVALID, "ctas per SM must be in [1, 32]");
+      c->ctas_per_sm = (int)value;
+      return HICCL_OK;
+    case HICCL_OPT_ITEM_BYTES:
+      if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "set before planning");
+      if (value < (long long)SEG_BYTES || value > (1ll << 30)) return fail(c, HICCL_ERR_INVALID, "item bytes out of range");
+      c->item_bytes = (unsigned long long)value;
+      return HICCL_OK;
+    case HICCL_OPT_ORDER:
+      if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "set before planning");
+      if (value != 0 && value != 1) return fail(c, HICCL_ERR_INVALID, "order must be 0 or 1");
+      c->order = (int)value;
+      return HICCL_OK;
+  }
+  return fail(c, HICCL_ERR_INVALID, "unknown option");
+}
+
+const char *hiccl_last_error(hiccl_comm_t c) {
+  if (!c) return "null communicator";
+  return c->err.c_str();
+}
+
+void hiccl_destroy(hiccl_comm_t c) {
+  if (!c) return;
+  dev_release(c);
+  delete c;
+}
+
+}  // extern "C"

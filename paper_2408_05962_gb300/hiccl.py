@@ -1,0 +1,303 @@
+"""Thin ctypes binding of the C ABI in ``include/hiccl.h``.
+
+Argument marshalling only: the module-level ``hiccl_*`` functions carry the
+C names and signatures (pointer arrays become Python sequences of ints,
+tensors or None) and raise ``HicclError`` on a non-OK status.  ``Comm`` is a
+small object wrapper over the same calls.  Every step of a collective runs in
+the CUDA library; there is no Python or CPU execution path, and loading fails
+loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhiccl.so")
+
+F32, I32, BF16, FP8E4M3 = 0, 1, 2, 3
+DTYPES = {"f32": F32, "i32": I32, "bf16": BF16, "fp8": FP8E4M3}
+ESIZE = {F32: 4, I32: 4, BF16: 2, FP8E4M3: 1}
+SUM = 0
+
+OK, ERR_INVALID, ERR_STATE, ERR_RACE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
+STATUS_NAMES = ["OK", "INVALID", "STATE", "RACE", "NOMEM", "CUDA", "TIMEOUT", "UNSUPPORTED"]
+
+OPT_TIMEOUT_NS, OPT_CTAS_PER_SM, OPT_ITEM_BYTES, OPT_ORDER = range(4)
+
+
+class HicclError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"HICCL_ERR_{name}: {message}")
+        self.status = status
+        self.message = message
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_ulonglong) for n in
+                ("steps", "copy_steps", "reduce_steps", "items", "edges", "stages",
+                 "scratch_bytes", "table_bytes", "slots")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class StepDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("level", ctypes.c_int), ("nsrc", ctypes.c_int),
+                ("ndst", ctypes.c_int), ("npreds", ctypes.c_int), ("prim", ctypes.c_int),
+                ("branch", ctypes.c_int), ("channel", ctypes.c_int),
+                ("nbytes", ctypes.c_ulonglong), ("slot", ctypes.c_ulonglong)]
+
+
+_lib = None
+
+_SIGS = {
+    "hiccl_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "hiccl_add_multicast": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t,
+                                           ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    "hiccl_add_reduction": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t,
+                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int]),
+    "hiccl_add_fence": (ctypes.c_int, [ctypes.c_void_p]),
+    "hiccl_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_int]),
+    "hiccl_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_int]),
+    "hiccl_start": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hiccl_wait": (ctypes.c_int, [ctypes.c_void_p]),
+    "hiccl_level_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]),
+    "hiccl_hbm_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong),
+                                       ctypes.POINTER(ctypes.c_ulonglong)]),
+    "hiccl_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]),
+    "hiccl_get_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_ulonglong, ctypes.POINTER(StepDesc),
+                                      ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_ulonglong),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_ulonglong)]),
+    "hiccl_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong]),
+    "hiccl_debug_withhold": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_int]),
+    "hiccl_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "hiccl_destroy": (None, [ctypes.c_void_p]),
+}
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2408_05962_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _addr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _ptr_array(seq: Sequence, n: int):
+    if len(seq) != n:
+        raise ValueError(f"need {n} per-rank pointers, got {len(seq)}")
+    return (ctypes.c_void_p * n)(*[_addr(v) or None for v in seq])
+
+
+def _check(comm, st: int):
+    if st != OK:
+        msg = lib().hiccl_last_error(comm).decode() if comm else ""
+        raise HicclError(st, msg)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return int(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# ---- the C names ------------------------------------------------------------
+
+def hiccl_create(nranks: int, dtype: int | str = F32):
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    out = ctypes.c_void_p()
+    st = lib().hiccl_create(int(nranks), dt, ctypes.byref(out))
+    if st != OK:
+        raise HicclError(st, "hiccl_create")
+    return out.value
+
+
+def hiccl_add_multicast(comm, send, recv, count: int, root: int, leaves: Sequence[int], nranks: int):
+    lv = (ctypes.c_int * len(leaves))(*leaves)
+    _check(comm, lib().hiccl_add_multicast(comm, _ptr_array(send, nranks), _ptr_array(recv, nranks),
+                                           int(count), int(root), lv, len(leaves)))
+
+
+def hiccl_add_reduction(comm, send, recv, count: int, leaves: Sequence[int], root: int, nranks: int,
+                        op: int = SUM):
+    lv = (ctypes.c_int * len(leaves))(*leaves)
+    _check(comm, lib().hiccl_add_reduction(comm, _ptr_array(send, nranks), _ptr_array(recv, nranks),
+                                           int(count), lv, len(leaves), int(root), int(op)))
+
+
+def hiccl_add_fence(comm):
+    _check(comm, lib().hiccl_add_fence(comm))
+
+
+def hiccl_init(comm, hierarchy: Sequence[int], stripe: int = 1, pipeline: int = 1):
+    h = (ctypes.c_int * len(hierarchy))(*hierarchy)
+    _check(comm, lib().hiccl_init(comm, h, len(hierarchy), int(stripe), int(pipeline)))
+
+
+def hiccl_plan(comm, hierarchy: Sequence[int], stripe: int = 1, pipeline: int = 1):
+    h = (ctypes.c_int * len(hierarchy))(*hierarchy)
+    _check(comm, lib().hiccl_plan(comm, h, len(hierarchy), int(stripe), int(pipeline)))
+
+
+def hiccl_start(comm, stream=None):
+    s = _stream_handle(stream)
+    _check(comm, lib().hiccl_start(comm, ctypes.c_void_p(s) if s else None))
+
+
+def hiccl_wait(comm):
+    _check(comm, lib().hiccl_wait(comm))
+
+
+def hiccl_level_bytes(comm, nlevels: int) -> list:
+    arr = (ctypes.c_ulonglong * nlevels)()
+    _check(comm, lib().hiccl_level_bytes(comm, arr, nlevels))
+    return [int(v) for v in arr]
+
+
+def hiccl_hbm_bytes(comm) -> tuple:
+    r, w = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+    _check(comm, lib().hiccl_hbm_bytes(comm, ctypes.byref(r), ctypes.byref(w)))
+    return int(r.value), int(w.value)
+
+
+def hiccl_plan_info(comm) -> dict:
+    info = PlanInfo()
+    _check(comm, lib().hiccl_plan_info(comm, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def hiccl_get_step(comm, index: int) -> dict:
+    d = StepDesc()
+    _check(comm, lib().hiccl_get_step(comm, int(index), ctypes.byref(d), None, None, None, None, None,
+                                      None, None))
+    ns, nd, npd = d.nsrc, d.ndst, d.npreds
+    sa, ss, sr = (ctypes.c_ulonglong * ns)(), (ctypes.c_int * ns)(), (ctypes.c_int * ns)()
+    da, ds, dr = (ctypes.c_ulonglong * nd)(), (ctypes.c_int * nd)(), (ctypes.c_int * nd)()
+    pr = (ctypes.c_ulonglong * max(npd, 1))()
+    _check(comm, lib().hiccl_get_step(comm, int(index), ctypes.byref(d), sa, ss, sr, da, ds, dr, pr))
+    return {
+        "kind": "copy" if d.kind == 0 else "reduce", "level": d.level, "nbytes": int(d.nbytes),
+        "prim": d.prim, "branch": d.branch, "channel": d.channel, "slot": int(d.slot),
+        "srcs": [(int(sr[k]), int(sa[k]), bool(ss[k])) for k in range(ns)],
+        "dsts": [(int(dr[k]), int(da[k]), bool(ds[k])) for k in range(nd)],
+        "preds": [int(pr[k]) for k in range(npd)],
+    }
+
+
+def hiccl_set_option(comm, opt: int, value: int):
+    _check(comm, lib().hiccl_set_option(comm, int(opt), int(value)))
+
+
+def hiccl_debug_withhold(comm, index: int, extra: int):
+    _check(comm, lib().hiccl_debug_withhold(comm, int(index), int(extra)))
+
+
+def hiccl_last_error(comm) -> str:
+    return lib().hiccl_last_error(comm).decode()
+
+
+def hiccl_destroy(comm):
+    lib().hiccl_destroy(comm)
+
+
+# ---- object wrapper -------------------------------------------------------------
+
+class Comm:
+    """A communicator (the paper's persistent ``Comm<T>``, Listing 2)."""
+
+    def __init__(self, nranks: int, dtype: int | str = "f32"):
+        self.P = int(nranks)
+        self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        self.esize = ESIZE[self.dtype]
+        self.handle = hiccl_create(self.P, self.dtype)
+        self.nlevels = None
+
+    def add_multicast(self, send, recv, count, root, leaves):
+        hiccl_add_multicast(self.handle, send, recv, count, root, list(leaves), self.P)
+
+    def add_reduction(self, send, recv, count, leaves, root):
+        hiccl_add_reduction(self.handle, send, recv, count, list(leaves), root, self.P)
+
+    def add_fence(self):
+        hiccl_add_fence(self.handle)
+
+    def init(self, hierarchy, stripe=1, pipeline=1):
+        hiccl_init(self.handle, list(hierarchy), stripe, pipeline)
+        self.nlevels = len(hierarchy)
+
+    def plan(self, hierarchy, stripe=1, pipeline=1):
+        hiccl_plan(self.handle, list(hierarchy), stripe, pipeline)
+        self.nlevels = len(hierarchy)
+
+    def start(self, stream=None):
+        hiccl_start(self.handle, stream)
+
+    def wait(self):
+        hiccl_wait(self.handle)
+
+    def level_bytes(self):
+        return hiccl_level_bytes(self.handle, self.nlevels)
+
+    def hbm_bytes(self):
+        return hiccl_hbm_bytes(self.handle)
+
+    def plan_info(self):
+        return hiccl_plan_info(self.handle)
+
+    def step(self, i):
+        return hiccl_get_step(self.handle, i)
+
+    def steps(self):
+        return [self.step(i) for i in range(self.plan_info()["steps"])]
+
+    def set_option(self, opt, value):
+        hiccl_set_option(self.handle, opt, value)
+
+    def withhold(self, index, extra):
+        hiccl_debug_withhold(self.handle, index, extra)
+
+    def destroy(self):
+        if self.handle:
+            hiccl_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -1,0 +1,98 @@
+"""Test-side glue between an oracle ``Program`` (used as a description of a
+collective) and the C-ABI library: register the same primitives on a library
+communicator at given buffer addresses, and -- on machines without a GPU --
+interpret the library's exported step table on NumPy buffers.
+
+The interpreter here is test code: it executes the *library's* plan (its
+steps, relay offsets and order) so that the host factorizer can be checked
+against the oracle without a GPU.  It shares nothing with the oracle's own
+factorizer or simulator.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle.model import DTYPES, Multicast
+from paper_2408_05962_gb300 import hiccl as H
+
+ESIZE = {"f32": 4, "i32": 4, "bf16": 2, "fp8": 1}
+
+
+class FakeAddresses:
+    """Disjoint 256-byte aligned fake device addresses for every buffer key."""
+
+    def __init__(self, prog, base=0x7f0000000000, gap=4096):
+        self.esize = ESIZE[prog.dtype]
+        self.base = {}
+        a = base
+        for key, n in prog.buffers.items():
+            self.base[key] = a
+            a += (n * self.esize + gap + 255) // 256 * 256
+        self.end = a
+
+    def addr(self, ref) -> int:
+        return self.base[ref.key] + ref.off * self.esize
+
+    def resolve(self, addr: int):
+        """(buffer key, byte offset) of a fake address."""
+        best = None
+        for key, b in self.base.items():
+            if b <= addr and (best is None or b > best[1]):
+                best = (key, b)
+        if best is None:
+            raise KeyError(hex(addr))
+        return best[0], addr - best[1]
+
+
+def register(prog, addr_of, dtype=None) -> H.Comm:
+    """A library communicator holding ``prog``'s primitives at ``addr_of(ref)``."""
+    comm = H.Comm(prog.P, dtype or prog.dtype)
+    P = prog.P
+    for e, epoch in enumerate(prog.epochs):
+        if e:
+            comm.add_fence()
+        for p in epoch:
+            send = [0] * P
+            recv = [0] * P
+            if isinstance(p, Multicast):
+                send[p.root] = addr_of(p.src)
+                for j in p.leaves:
+                    recv[j] = addr_of(p.dsts[j])
+                comm.add_multicast(send, recv, p.count, p.root, p.leaves)
+            else:
+                for i in p.leaves:
+                    send[i] = addr_of(p.srcs[i])
+                recv[p.root] = addr_of(p.dst)
+                comm.add_reduction(send, recv, p.count, p.leaves, p.root)
+    return comm
+
+
+def interpret(comm: H.Comm, fake: FakeAddresses, mem: dict, dtype: str) -> dict:
+    """Run the library's step table, in table order, on the NumPy buffers
+    ``mem`` (keyed like the program's buffers)."""
+    info = comm.plan_info()
+    dt = DTYPES[dtype]
+    byte_views = {k: v.view(np.uint8) for k, v in mem.items()}
+    scratch = np.zeros(info["scratch_bytes"] + 16, dtype=np.uint8)
+
+    def view(rank_addr_scr, n):
+        _, a, scr = rank_addr_scr
+        if scr:
+            return scratch[a:a + n]
+        key, off = fake.resolve(a)
+        return byte_views[key][off:off + n]
+
+    for i in range(info["steps"]):
+        st = comm.step(i)
+        assert all(q < i for q in st["preds"]), "table order must be topological"
+        n = st["nbytes"]
+        if st["kind"] == "copy":
+            src = view(st["srcs"][0], n).copy()
+            for d in st["dsts"]:
+                view(d, n)[...] = src
+        else:
+            acc = view(st["srcs"][0], n).copy().view(dt)
+            for s in st["srcs"][1:]:
+                acc = acc + view(s, n).copy().view(dt)
+            view(st["dsts"][0], n)[...] = acc.view(np.uint8)
+    return mem

@@ -1,0 +1,78 @@
+"""Parity at the full workload sizes, in the launch configuration the
+benchmark times: the seven collectives of P = 64 virtual ranks over
+{4,4,4} with 4 MiB fp32 per rank, stripe 4, pipeline 8 (compared in full),
+and All-reduce with P = 32 over {4, 8} at 64 MiB per rank (compared on
+sampled elements, whose nested fold the oracle computes one by one)."""
+import numpy as np
+import pytest
+
+from oracle import semantics as S
+from synth import scaled_normal_ranks, uniform_ranks
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _run(kind, P, d, h, s, m, x):
+    import torch
+    from paper_2408_05962_gb300 import collectives as C
+    from paper_2408_05962_gb300 import hiccl as H
+    bufs = C.Buffers(kind, P, d, torch.float32)
+    bufs.send.copy_(torch.from_numpy(x[:, :bufs.ls]))
+    bufs.recv.fill_(-3.0)
+    comm = H.Comm(P, "f32")
+    C.compose(comm, kind, d, bufs.send_ptrs(), bufs.recv_ptrs())
+    comm.init(h, s, m)
+    comm.start()
+    comm.wait()
+    out = bufs.recv.cpu().numpy()
+    comm.destroy()
+    return out
+
+
+@pytest.mark.parametrize("kind", ["broadcast", "scatter", "gather", "allgather", "reducescatter",
+                                  "allreduce", "alltoall"])
+def test_seven_collectives_full_size(kind):
+    P, h = 64, [4, 4, 4]
+    d = (4 << 20) // 4 // P
+    x = uniform_ranks(P, d * P, seed=1)
+    y = _run(kind, P, d, h, 4, 8, x)
+    xs = [x[r] for r in range(P)]
+    if kind == "broadcast":
+        exp = S.def_broadcast(xs, 0)
+    elif kind == "scatter":
+        exp = S.def_scatter(xs, 0)
+    elif kind == "gather":
+        exp = [None] * P
+        exp[0] = np.concatenate([v[:d] for v in xs])
+    elif kind == "allgather":
+        exp = S.def_allgather([v[:d] for v in xs])
+    elif kind == "reducescatter":
+        exp = S.def_reducescatter(xs, h)
+    elif kind == "allreduce":
+        exp = S.def_allreduce(xs, h)
+    else:
+        exp = S.def_alltoall(xs)
+    for r in range(P):
+        if exp[r] is None:
+            assert np.all(y[r] == -3.0)
+        else:
+            assert np.array_equal(y[r].view(np.uint32), exp[r].view(np.uint32)), (kind, r)
+
+
+def test_allreduce_64mib_sampled():
+    P, h = 32, [4, 8]
+    n = 16 << 20                     # 64 MiB of fp32 per rank
+    d = n // P
+    x = scaled_normal_ranks(P, n, seed=3)
+    y = _run("allreduce", P, d, h, 1, 16, x)
+    g = np.random.Generator(np.random.PCG64(5))
+    idx = np.unique(np.concatenate([g.integers(0, n, 4096), np.arange(0, n, d), [n - 1]]))
+    expect = S.nested_fold({r: x[r, idx] for r in range(P)}, h)
+    for r in range(P):
+        assert np.array_equal(y[r, idx].view(np.uint32), expect.view(np.uint32)), r

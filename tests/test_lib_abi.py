@@ -1,0 +1,119 @@
+"""The C-ABI library builds, loads without a GPU, and exports every function
+that include/hiccl.h declares; argument validation and the state machine work
+without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2408_05962_gb300 import build as B
+from paper_2408_05962_gb300 import hiccl as H
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "hiccl.h")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hiccl_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol():
+    lib = ctypes.CDLL(H.LIB_PATH)
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_header():
+    for n in declared_functions():
+        assert hasattr(H, n), n
+
+
+def _comm(P=4, dt="f32"):
+    return H.Comm(P, dt)
+
+
+def test_validation_errors():
+    c = _comm(4)
+    base = [0x1000 * (r + 1) for r in range(4)]
+    with pytest.raises(H.HicclError) as e:
+        c.add_multicast(base, base, 8, 7, [1])            # root out of range
+    assert e.value.status == H.ERR_INVALID
+    with pytest.raises(H.HicclError) as e:
+        c.add_multicast(base, base, 8, 0, [1, 1])         # duplicate leaf
+    assert e.value.status == H.ERR_INVALID
+    with pytest.raises(H.HicclError) as e:
+        c.add_multicast(base, base, 8, 0, [])             # no leaf
+    assert e.value.status == H.ERR_INVALID
+    with pytest.raises(H.HicclError) as e:
+        c.add_multicast([0] * 4, base, 8, 0, [1])         # null root buffer
+    assert e.value.status == H.ERR_INVALID
+    with pytest.raises(H.HicclError) as e:
+        c.add_multicast([b + 2 for b in base], base, 8, 0, [1])   # misaligned f32
+    assert e.value.status == H.ERR_INVALID
+    c.add_multicast(base, [b + 0x100000 for b in base], 8, 0, [1, 2])
+    for h, s, m in [([3], 1, 1), ([2, 2], 0, 1), ([2, 2], 5, 1), ([2, 2], 1, 0), ([0, 4], 1, 1)]:
+        with pytest.raises(H.HicclError) as e:
+            c.plan(h, s, m)
+        assert e.value.status == H.ERR_INVALID, (h, s, m)
+    c.plan([2, 2], 2, 2)
+    with pytest.raises(H.HicclError) as e:
+        c.add_fence()                                     # composition closed
+    assert e.value.status == H.ERR_STATE
+    with pytest.raises(H.HicclError) as e:
+        c.start()                                         # planned, not initialized
+    assert e.value.status == H.ERR_STATE
+    with pytest.raises(H.HicclError) as e:
+        c.wait()
+    assert e.value.status == H.ERR_STATE
+
+
+def test_race_rejected():
+    c = _comm(4)
+    a = [0x100000 * (r + 1) for r in range(4)]
+    c.add_multicast(a, a, 16, 0, [1, 2])
+    c.add_multicast([x + 0x10000 for x in a], [a[0], a[1] + 32, 0, 0], 4, 1, [1])  # overlaps rank 1's recv
+    with pytest.raises(H.HicclError) as e:
+        c.plan([2, 2])
+    assert e.value.status == H.ERR_RACE
+    c2 = _comm(4)
+    c2.add_multicast(a, a, 16, 0, [1, 2])
+    c2.add_fence()
+    c2.add_multicast([x + 0x10000 for x in a], [a[0], a[1] + 32, 0, 0], 4, 1, [1])
+    c2.plan([2, 2])
+
+
+def test_unsupported_op():
+    c = _comm(2)
+    a = [0x1000, 0x2000]
+    with pytest.raises(H.HicclError) as e:
+        H.hiccl_add_reduction(c.handle, a, a, 4, [0, 1], 0, 2, op=3)
+    assert e.value.status == H.ERR_UNSUPPORTED
+
+
+def test_options():
+    c = _comm(2)
+    c.set_option(H.OPT_TIMEOUT_NS, 5_000_000)
+    c.set_option(H.OPT_CTAS_PER_SM, 3)
+    c.set_option(H.OPT_ITEM_BYTES, 65536)
+    c.set_option(H.OPT_ORDER, 1)
+    with pytest.raises(H.HicclError):
+        c.set_option(H.OPT_CTAS_PER_SM, 0)
+    with pytest.raises(H.HicclError):
+        c.set_option(99, 1)
+
+
+def test_empty_program_plans():
+    c = _comm(3)
+    c.plan([3])
+    info = c.plan_info()
+    assert info["steps"] == 0 and info["items"] == 0
+    assert c.level_bytes() == [0]

@@ -1,0 +1,110 @@
+"""The library's host factorizer against the oracle, without a GPU.
+
+For every case the same program is given to the oracle and, at fake device
+addresses, to the C-ABI library in plan-only mode.  Checked: per-level link
+bytes, HBM bytes and the number of stages equal the oracle factorizer's
+(same readings of the paper), and the library's own step table -- its
+steps, relay offsets and execution order -- interpreted on NumPy buffers
+reproduces the oracle's plain semantics bit for bit."""
+import numpy as np
+import pytest
+
+from oracle import programs as PR
+from oracle import semantics as S
+from oracle.factorize import factorize
+from oracle.hierarchy import all_factorizations
+from paper_2408_05962_gb300 import build as B
+from tests._bridge import FakeAddresses, interpret, register
+from tests._cases import fill, random_program
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def _check(prog, h, s, m, seed=0, interpret_steps=True):
+    fake = FakeAddresses(prog)
+    comm = register(prog, fake.addr)
+    comm.plan(h, s, m)
+    plan = factorize(prog, h, s, m)
+    assert comm.level_bytes() == plan.level_bytes()
+    assert comm.hbm_bytes() == plan.hbm_bytes()
+    info = comm.plan_info()
+    assert info["stages"] == plan.stages()
+    assert info["steps"] == len(plan.ops)
+    if interpret_steps:
+        mem0 = fill(prog, seed)
+        ref = {k: v.copy() for k, v in mem0.items()}
+        S.run_program(prog, ref, h)
+        got = interpret(comm, fake, {k: v.copy() for k, v in mem0.items()}, prog.dtype)
+        for k in ref:
+            assert np.array_equal(ref[k], got[k]), k
+    return comm
+
+
+COLL = PR.SEVEN + ("reduce", "allreduce_single", "broadcast_ag_scatter", "reduce_gather_rs",
+                   "allgather_bcast_gather", "reducescatter_scatter_reduce", "allreduce_bcast_reduce")
+
+
+@pytest.mark.parametrize("name", COLL)
+@pytest.mark.parametrize("P,h,s,m", [(8, [2, 4], 1, 1), (8, [2, 4], 4, 3), (12, [2, 2, 3], 3, 2),
+                                     (16, [4, 4], 4, 2), (8, [8], 2, 2), (6, [3, 2], 2, 1)])
+@pytest.mark.parametrize("dtype", ["f32", "i32"])
+def test_collectives(name, P, h, s, m, dtype):
+    _check(PR.BUILDERS[name](P, 11, dtype=dtype), h, s, m, seed=P * 7 + s)
+
+
+@pytest.mark.parametrize("P", [2, 3, 4, 6, 8])
+def test_random_programs_all_hierarchies(P):
+    n = 0
+    for h in all_factorizations(P):
+        for s in sorted({1, 2, P}):
+            for m in (1, 2):
+                seed = P * 1000 + s * 10 + m + len(h)
+                prog = random_program(P, seed, "f32")
+                if S.find_race(prog) is not None:
+                    continue
+                _check(prog, h, s, m, seed=seed)
+                n += 1
+    assert n > 0
+
+
+def test_config1_allreduce_accounting():
+    """All-reduce of 65,536 fp32 per rank over {2, 4} as Listing 2 (s = 1,
+    m = 1): chunk n = 32 KiB.  Reduce-scatter moves 8 x (2*5n + 3n) = 104n of
+    device memory and All-gather 8 x (2n + 4n + 4n) = 80n, its multicast hops
+    reading their source once (top hop: 1 read + 1 write; a bottom hop into
+    three ranks: 1 read + 3 writes, in both nodes); the top level carries 16n
+    (Table 3: 2(p - g)d per node, two nodes) and the bottom level 96n."""
+    prog = PR.allreduce(8, 8192)
+    comm = _check(prog, [2, 4], 1, 1, interpret_steps=False)
+    n = 8192 * 4
+    rd, wr = comm.hbm_bytes()
+    assert rd + wr == 104 * n + 80 * n
+    assert comm.level_bytes() == [16 * n, 96 * n]
+
+
+def test_config2_shapes_plan():
+    """The seven collectives of P = 64, {4,4,4}, 4 MiB per rank, s = 4, m = 8
+    plan, and agree with the oracle's accounting (no execution: too large for
+    the interpreter)."""
+    d = (4 << 20) // 4 // 64
+    for name in PR.SEVEN:
+        prog = PR.BUILDERS[name](64, d)
+        _check(prog, [4, 4, 4], 4, 8, interpret_steps=False)
+
+
+def test_table_order_and_items():
+    prog = PR.allreduce(8, 4096)
+    fake = FakeAddresses(prog)
+    comm = register(prog, fake.addr)
+    comm.plan([2, 4], 2, 4)
+    info = comm.plan_info()
+    steps = comm.steps()
+    slots = [st["slot"] for st in steps]
+    assert slots == sorted(slots)
+    for i, st in enumerate(steps):
+        for q in st["preds"]:
+            assert steps[q]["slot"] < st["slot"]
+    assert info["items"] >= 1 and info["slots"] == slots[-1] + 1

@@ -226,46 +226,7 @@ def test_piece_bounds_properties():
 # simulator == semantics, brute force over small configurations
 # ---------------------------------------------------------------------------
 
-def _random_program(P, seed, dtype):
-    """Two epochs of multicasts and reductions on disjoint ranges with random
-    roots and sparse leaf sets; the second epoch reads what the first wrote."""
-    g = np.random.Generator(np.random.PCG64(seed))
-    prog = Program(P, dtype)
-    n = int(g.integers(1, 40))
-    k = 3
-    send = [prog.buffer(("send", r), n * k) for r in range(P)]
-    recv = [prog.buffer(("recv", r), n * k) for r in range(P)]
-    for c in range(k):
-        leaves = random_leaf_set(P, seed * 31 + c)
-        root = int(g.integers(0, P))
-        if g.integers(0, 2):
-            prog.multicast(root, leaves, n, send[root].shift(c * n),
-                           {j: recv[j].shift(c * n) for j in leaves})
-        else:
-            prog.reduction(leaves, root, n, {i: send[i].shift(c * n) for i in leaves},
-                           recv[root].shift(c * n))
-    prog.fence()
-    for c in range(k):
-        root = int(g.integers(0, P))
-        leaves = [j for j in random_leaf_set(P, seed * 97 + c) if j != root] or [(root + 1) % P]
-        leaves = [j for j in leaves if j != root]
-        if not leaves:
-            continue
-        # in place: forward what the root holds in recv chunk c
-        prog.multicast(root, leaves, n, recv[root].shift(c * n),
-                       {j: recv[j].shift(c * n) for j in leaves})
-    return prog
-
-
-def _init(prog, seed):
-    mem = prog.allocate()
-    g = np.random.Generator(np.random.PCG64(seed))
-    for k, v in mem.items():
-        if v.dtype == np.float32:
-            v[...] = g.uniform(-1, 1, size=v.shape).astype(np.float32)
-        else:
-            v[...] = g.integers(-2**31, 2**31 - 1, size=v.shape, endpoint=True, dtype=np.int64)
-    return mem
+from tests._cases import fill as _init, random_program as _random_program  # noqa: E402
 
 
 @pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 6, 8])
