@@ -287,6 +287,14 @@ def run_ours(args):
         b.send.copy_(x[:, :b.ls].to(device))
         b.recv.zero_()
         comm = H.Comm(P, "f32")
+        if args.item_bytes:
+            comm.set_option(H.OPT_ITEM_BYTES, args.item_bytes)
+        if args.order is not None:
+            comm.set_option(H.OPT_ORDER, args.order)
+        if args.ctas_per_sm:
+            comm.set_option(H.OPT_CTAS_PER_SM, args.ctas_per_sm)
+        if args.threads:
+            comm.set_option(H.OPT_THREADS, args.threads)
         C.compose(comm, kind, d, b.send_ptrs(), b.recv_ptrs())
         comm.init(HIER, STRIPE, PIPE)
         rd, wr = comm.hbm_bytes()
@@ -399,6 +407,10 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=14.0)
     ap.add_argument("--ref-budget", type=float, default=7.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--item-bytes", type=int, default=0, help="executor work-item size (0: library default)")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="executor CTAs per SM (0: library default)")
+    ap.add_argument("--threads", type=int, default=0, help="executor threads per CTA (0: library default)")
+    ap.add_argument("--order", type=int, default=None, help="work order: 0 pipeline slots, 1 stage depth")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         run_reference(args)

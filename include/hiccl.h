@@ -70,7 +70,8 @@ hiccl_status_t hiccl_create(int nranks, hiccl_dtype_t dtype, hiccl_comm_t *out);
  *                Only send[root] and recv[j] for j in leaves are read; other
  *                entries may be NULL.  A root that is also a leaf with
  *                recv[root] == send[root] is in place (nothing to copy).
- *   leaves     : nleaves (>= 1) distinct ranks in [0, nranks).
+ *   leaves     : nleaves distinct ranks in [0, nranks); nleaves == 0 registers
+ *                nothing (leaves may then be NULL).
  * The caller keeps every buffer valid and unmoved until hiccl_destroy.
  * Only allowed before hiccl_init / hiccl_plan (HICCL_ERR_STATE otherwise). */
 hiccl_status_t hiccl_add_multicast(hiccl_comm_t comm, const void *const *send,
@@ -79,7 +80,8 @@ hiccl_status_t hiccl_add_multicast(hiccl_comm_t comm, const void *const *send,
 
 /* Register R(leaves, root, count, op) (Sec. 3.1): after execution the root's
  * range recv[root][0, count) holds the sum over the leaves i of
- * send[i][0, count).  Only send[i] for i in leaves and recv[root] are read.
+ * send[i][0, count).  Only send[i] for i in leaves and recv[root] are read;
+ * leaves holds nleaves >= 1 distinct ranks.
  * Sum order (fixed, independent of root, stripe and pipeline): a rank
  * contributes its values; a group of the hierarchy contributes the left fold
  * of its non-empty subgroups' contributions in ascending subgroup order, in
@@ -192,13 +194,14 @@ hiccl_status_t hiccl_get_step(hiccl_comm_t comm, unsigned long long index,
 /* ---- tuning and diagnostics -------------------------------------------------- */
 
 typedef enum {
-  HICCL_OPT_TIMEOUT_NS = 0,   /* dependency-wait limit inside the executor (default 1e9) */
-  HICCL_OPT_CTAS_PER_SM = 1,  /* resident executor CTAs per SM (default 2)               */
-  HICCL_OPT_ITEM_BYTES = 2,   /* target output bytes of one work item (default 131072)   */
-  HICCL_OPT_ORDER = 3         /* work order: 0 pipeline slots (default), 1 stage depth   */
+  HICCL_OPT_TIMEOUT_NS = 0,   /* dependency-wait limit inside the executor (default 1e9)  */
+  HICCL_OPT_CTAS_PER_SM = 1,  /* executor CTAs per SM, capped by occupancy (default 8)    */
+  HICCL_OPT_ITEM_BYTES = 2,   /* target output bytes of one work item (default 32768)     */
+  HICCL_OPT_ORDER = 3,        /* work order: 0 pipeline slots (default), 1 stage depth    */
+  HICCL_OPT_THREADS = 4       /* threads per executor CTA: 64 (default), 128, 256, 512  */
 } hiccl_option_t;
 
-/* Set an option.  TIMEOUT_NS and CTAS_PER_SM apply to the next start;
+/* Set an option.  TIMEOUT_NS, CTAS_PER_SM and THREADS apply to the next start;
  * ITEM_BYTES and ORDER must be set before hiccl_init / hiccl_plan. */
 hiccl_status_t hiccl_set_option(hiccl_comm_t comm, hiccl_option_t opt, long long value);
 

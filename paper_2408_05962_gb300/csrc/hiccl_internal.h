@@ -138,8 +138,9 @@ struct hiccl_comm {
   enum State { COMPOSING, PLANNED, READY, RUNNING } state = COMPOSING;
   // options
   unsigned long long timeout_ns = 1000000000ull;
-  int ctas_per_sm = 2;
-  unsigned long long item_bytes = 131072;
+  int ctas_per_sm = 8;
+  int threads = 64;
+  unsigned long long item_bytes = 32768;
   int order = 0;
   hiccl::Plan plan;
   hiccl::DevState *dev = nullptr;

@@ -598,7 +598,10 @@ hiccl_status_t hiccl_create(int nranks, hiccl_dtype_t dtype, hiccl_comm_t *out) 
   return HICCL_OK;
 }
 
-static hiccl_status_t check_leaves(hiccl_comm *c, const int *leaves, int nleaves, std::vector<int> &out) {
+static hiccl_status_t check_leaves(hiccl_comm *c, const int *leaves, int nleaves, std::vector<int> &out,
+                                   bool allow_empty) {
+  out.clear();
+  if (nleaves == 0 && allow_empty) return HICCL_OK;
   if (!leaves || nleaves < 1) return fail(c, HICCL_ERR_INVALID, "need at least one leaf");
   if (nleaves > c->P) return fail(c, HICCL_ERR_INVALID, "more leaves than ranks");
   out.assign(leaves, leaves + nleaves);
@@ -623,8 +626,9 @@ hiccl_status_t hiccl_add_multicast(hiccl_comm_t c, const void *const *send, void
   p.root = root;
   p.count = count;
   p.epoch = c->epochs - 1;
-  hiccl_status_t st = check_leaves(c, leaves, nleaves, p.leaves);
+  hiccl_status_t st = check_leaves(c, leaves, nleaves, p.leaves, true);
   if (st != HICCL_OK) return st;
+  if (p.leaves.empty()) return HICCL_OK;   // nothing to deliver
   p.send.assign(c->P, 0);
   p.recv.assign(c->P, 0);
   p.send[root] = (unsigned long long)(uintptr_t)send[root];
@@ -657,7 +661,7 @@ hiccl_status_t hiccl_add_reduction(hiccl_comm_t c, const void *const *send, void
   p.root = root;
   p.count = count;
   p.epoch = c->epochs - 1;
-  hiccl_status_t st = check_leaves(c, leaves, nleaves, p.leaves);
+  hiccl_status_t st = check_leaves(c, leaves, nleaves, p.leaves, false);
   if (st != HICCL_OK) return st;
   p.send.assign(c->P, 0);
   p.recv.assign(c->P, 0);
@@ -786,6 +790,11 @@ hiccl_status_t hiccl_set_option(hiccl_comm_t c, hiccl_option_t opt, long long va
     case HICCL_OPT_CTAS_PER_SM:
       if (value < 1 || value > 32) return fail(c, HICCL_ERR_INVALID, "ctas per SM must be in [1, 32]");
       c->ctas_per_sm = (int)value;
+      return HICCL_OK;
+    case HICCL_OPT_THREADS:
+      if (value != 64 && value != 128 && value != 256 && value != 512)
+        return fail(c, HICCL_ERR_INVALID, "threads per CTA must be 64, 128, 256 or 512");
+      c->threads = (int)value;
       return HICCL_OK;
     case HICCL_OPT_ITEM_BYTES:
       if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "set before planning");

@@ -29,13 +29,11 @@
 
 namespace hiccl {
 
-constexpr int NT = 256;            // threads per CTA
-constexpr int NW = NT / 32;        // warps per CTA
 
 struct DevState {
   int device = -1;
   int nsm = 0;
-  int occ = 0;                      // resident CTAs per SM the kernel allows
+  int occ[4] = {0, 0, 0, 0};        // resident CTAs per SM for 64/128/256/512 threads
   void *table = nullptr;            // read-only arrays
   void *counters = nullptr;         // dep[], done[], ctl
   size_t counters_bytes = 0;
@@ -108,7 +106,7 @@ __device__ __forceinline__ uint4 add4(uint4 a, uint4 b, uint32_t dt) {
 // copy bytes [lo, lo + n) of the source to every destination (n <= SEG_BYTES)
 __device__ __forceinline__ void warp_copy(const unsigned long long *ptrs, uint32_t ndst, unsigned long long lo,
                                           uint32_t n, bool aligned, int lane) {
-  const char *src = reinterpret_cast<const char *>(ldg_ro(ptrs)) + lo;
+  const char *src = reinterpret_cast<const char *>(ptrs[0]) + lo;
   uint32_t done = 0;
   if (aligned) {
     constexpr int U = SEG_BYTES / (16 * 32);   // one pass covers the segment
@@ -120,7 +118,7 @@ __device__ __forceinline__ void warp_copy(const unsigned long long *ptrs, uint32
       if (i < nvec) v[u] = ld16(src + (i << 4));
     }
     for (uint32_t k = 0; k < ndst; ++k) {
-      char *dst = reinterpret_cast<char *>(ldg_ro(ptrs + 1 + k)) + lo;
+      char *dst = reinterpret_cast<char *>(ptrs[1 + k]) + lo;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const uint32_t i = u * 32 + lane;
@@ -131,28 +129,28 @@ __device__ __forceinline__ void warp_copy(const unsigned long long *ptrs, uint32
   }
   for (uint32_t b = done + lane; b < n; b += 32) {
     const char v = __ldcg(src + b);
-    for (uint32_t k = 0; k < ndst; ++k) (reinterpret_cast<char *>(ldg_ro(ptrs + 1 + k)) + lo)[b] = v;
+    for (uint32_t k = 0; k < ndst; ++k) (reinterpret_cast<char *>(ptrs[1 + k]) + lo)[b] = v;
   }
 }
 
 // out[lo, lo + n) = in_0 + in_1 + ... (left fold, fixed order; n <= SEG_BYTES)
 __device__ __forceinline__ void warp_reduce(const unsigned long long *ptrs, uint32_t nsrc, uint32_t dt,
                                             unsigned long long lo, uint32_t n, bool aligned, int lane) {
-  char *dst = reinterpret_cast<char *>(ldg_ro(ptrs + nsrc)) + lo;
+  char *dst = reinterpret_cast<char *>(ptrs[nsrc]) + lo;
   uint32_t done = 0;
   if (aligned) {
     constexpr int U = 4;
     const uint32_t nvec = n >> 4;
     for (uint32_t base = 0; base < nvec; base += 32 * U) {
       uint4 acc[U];
-      const char *s0 = reinterpret_cast<const char *>(ldg_ro(ptrs)) + lo;
+      const char *s0 = reinterpret_cast<const char *>(ptrs[0]) + lo;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const uint32_t i = base + u * 32 + lane;
         if (i < nvec) acc[u] = ld16(s0 + (i << 4));
       }
       for (uint32_t q = 1; q < nsrc; ++q) {
-        const char *sq = reinterpret_cast<const char *>(ldg_ro(ptrs + q)) + lo;
+        const char *sq = reinterpret_cast<const char *>(ptrs[q]) + lo;
         uint4 v[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -172,9 +170,9 @@ __device__ __forceinline__ void warp_reduce(const unsigned long long *ptrs, uint
   }
   // element tail (or the whole unaligned range): 4-byte elements
   for (uint32_t b = done + 4 * lane; b < n; b += 128) {
-    uint32_t acc = __ldcg(reinterpret_cast<const unsigned int *>(reinterpret_cast<const char *>(ldg_ro(ptrs)) + lo + b));
+    uint32_t acc = __ldcg(reinterpret_cast<const unsigned int *>(reinterpret_cast<const char *>(ptrs[0]) + lo + b));
     for (uint32_t q = 1; q < nsrc; ++q) {
-      const uint32_t v = __ldcg(reinterpret_cast<const unsigned int *>(reinterpret_cast<const char *>(ldg_ro(ptrs + q)) + lo + b));
+      const uint32_t v = __ldcg(reinterpret_cast<const unsigned int *>(reinterpret_cast<const char *>(ptrs[q]) + lo + b));
       if (dt == HICCL_F32)
         acc = __float_as_uint(__fadd_rn(__uint_as_float(acc), __uint_as_float(v)));
       else
@@ -188,38 +186,57 @@ __device__ __forceinline__ void warp_reduce(const unsigned long long *ptrs, uint
 // the persistent executor
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(NT, 2) hiccl_exec_kernel(const DevTable T) {
+constexpr int PMAX = 8;   // pointers of a step staged in shared memory (more: read from global)
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable T) {
+  constexpr int NW = NT / 32;   // warps per CTA
   __shared__ DevEntry s_ent[MAX_ENTRIES_PER_ITEM];
   __shared__ uint32_t s_pre[MAX_ENTRIES_PER_ITEM + 1];
-  __shared__ unsigned long long s_item;
+  __shared__ uint32_t s_meta[MAX_ENTRIES_PER_ITEM];
+  __shared__ uint32_t s_poff[MAX_ENTRIES_PER_ITEM];
+  __shared__ unsigned long long s_nb[MAX_ENTRIES_PER_ITEM];
+  __shared__ unsigned long long s_ptr[MAX_ENTRIES_PER_ITEM][PMAX];
+  __shared__ unsigned long long s_item, s_next;
   __shared__ int s_abort;
   __shared__ uint32_t s_nent;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned long long epoch = ld_relaxed(&T.ctl->epoch) + 1;   // this launch
 
+  if (tid == 0) {
+    s_item = atomicAdd(&T.ctl->ticket, 1ull);
+    s_abort = ld_relaxed(&T.ctl->err) != 0ull;
+  }
+  __syncthreads();
   for (;;) {
-    if (tid == 0) {
-      s_item = atomicAdd(&T.ctl->ticket, 1ull);
-      s_abort = ld_relaxed(&T.ctl->err) != 0ull;
-    }
-    __syncthreads();
     const unsigned long long item = s_item;
     if (item >= T.nitems || s_abort) break;
 
-    const uint32_t e0 = ldg_ro(T.item_off + item), e1 = ldg_ro(T.item_off + item + 1);
-    const uint32_t ne = e1 - e0;
+    // phase A: stage the item's entries, step descriptors and pointers in
+    // shared memory and wait for the steps' predecessors (warp 0); claim the
+    // next item meanwhile (warp 1), so its ticket latency is hidden
     if (warp == 0) {
-      uint32_t cnt = 0;
+      const uint32_t e0 = ldg_ro(T.item_off + item), e1 = ldg_ro(T.item_off + item + 1);
+      const uint32_t ne = e1 - e0;
+      uint32_t cnt = 0, s = 0;
       if (lane < (int)ne) {
-        DevEntry e = T.entries[e0 + lane];
+        const DevEntry e = T.entries[e0 + lane];
+        s = e.step;
+        const uint32_t meta = ldg_ro(T.meta + s), po = ldg_ro(T.ptr_off + s);
         s_ent[lane] = e;
+        s_meta[lane] = meta;
+        s_poff[lane] = po;
+        s_nb[lane] = ldg_ro(T.nbytes + s);
+        const uint32_t np = meta_nsrc(meta) + meta_ndst(meta);
+        if (np <= PMAX)
+          for (uint32_t q = 0; q < np; ++q) s_ptr[lane][q] = ldg_ro(T.ptrs + po + q);
         cnt = e.seg_hi - e.seg_lo;
       }
-      uint32_t inc = cnt;   // inclusive warp scan
+      uint32_t inc = cnt;   // inclusive warp scan of segment counts
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+        const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += v;
       }
       if (lane < (int)ne) s_pre[lane + 1] = inc;
@@ -227,11 +244,9 @@ __global__ void __launch_bounds__(NT, 2) hiccl_exec_kernel(const DevTable T) {
         s_pre[0] = 0;
         s_nent = ne;
       }
-      // wait for the predecessors of every step of the item
       if (lane < (int)ne) {
-        const uint32_t s = s_ent[lane].step;
         const unsigned long long target = (unsigned long long)ldg_ro(T.indeg + s) * epoch;
-        if (target) {
+        if (target && ld_acquire(T.dep + s) < target) {
           const unsigned long long t0 = global_ns();
           unsigned ns = 32;
           while (ld_acquire(T.dep + s) < target) {
@@ -245,27 +260,28 @@ __global__ void __launch_bounds__(NT, 2) hiccl_exec_kernel(const DevTable T) {
               break;
             }
             __nanosleep(ns);
-            if (ns < 1024) ns <<= 1;
+            if (ns < 256) ns <<= 1;
           }
         }
       }
+    } else if (tid == 32) {
+      s_next = atomicAdd(&T.ctl->ticket, 1ull);
+      if (ld_relaxed(&T.ctl->err)) s_abort = 1;
     }
     __syncthreads();
     if (s_abort) break;
 
-    // move the data: warp w takes segments w, w + NW, ... of the item
+    // phase B: move the data; warp w takes segments w, w + NW, ... of the item
     const uint32_t total = s_pre[s_nent];
     uint32_t k = 0;
     for (uint32_t j = warp; j < total; j += NW) {
       while (s_pre[k + 1] <= j) ++k;
-      const DevEntry e = s_ent[k];
-      const uint32_t s = e.step;
-      const unsigned long long seg = e.seg_lo + (j - s_pre[k]);
-      const unsigned long long nb = ldg_ro(T.nbytes + s);
+      const unsigned long long seg = s_ent[k].seg_lo + (j - s_pre[k]);
       const unsigned long long lo = seg * SEG_BYTES;
-      const uint32_t n = (uint32_t)min((unsigned long long)SEG_BYTES, nb - lo);
-      const uint32_t meta = ldg_ro(T.meta + s);
-      const unsigned long long *ptrs = T.ptrs + ldg_ro(T.ptr_off + s);
+      const uint32_t n = (uint32_t)min((unsigned long long)SEG_BYTES, s_nb[k] - lo);
+      const uint32_t meta = s_meta[k];
+      const uint32_t np = meta_nsrc(meta) + meta_ndst(meta);
+      const unsigned long long *ptrs = np <= PMAX ? s_ptr[k] : T.ptrs + s_poff[k];
       if (meta_op(meta) == OP_COPY)
         warp_copy(ptrs, meta_ndst(meta), lo, n, meta_aligned(meta), lane);
       else
@@ -273,7 +289,7 @@ __global__ void __launch_bounds__(NT, 2) hiccl_exec_kernel(const DevTable T) {
     }
     __syncthreads();
 
-    // completion: the last entry of a step releases its successors
+    // phase C: the last entry of a step releases its successors
     if (tid < (int)s_nent) {
       const uint32_t s = s_ent[tid].step;
       __threadfence();
@@ -284,6 +300,7 @@ __global__ void __launch_bounds__(NT, 2) hiccl_exec_kernel(const DevTable T) {
         for (uint32_t q = a; q < b; ++q) red_release_add(T.dep + ldg_ro(T.succ + q), 1ull);
       }
     }
+    if (tid == 0) s_item = s_next;
     __syncthreads();
   }
 
@@ -332,9 +349,15 @@ hiccl_status_t dev_upload(hiccl_comm *c) {
   if ((e = cudaGetDevice(&d->device)) != cudaSuccess) return cuda_fail(c, e, "cudaGetDevice");
   if ((e = cudaDeviceGetAttribute(&d->nsm, cudaDevAttrMultiProcessorCount, d->device)) != cudaSuccess)
     return cuda_fail(c, e, "cudaDeviceGetAttribute");
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d->occ, hiccl_exec_kernel, NT, 0)) != cudaSuccess)
-    return cuda_fail(c, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-  if (d->occ < 1) return fail(c, HICCL_ERR_CUDA, "executor kernel cannot be resident");
+  {
+    const void *ks[4] = {(const void *)hiccl_exec_kernel<64>, (const void *)hiccl_exec_kernel<128>,
+                         (const void *)hiccl_exec_kernel<256>, (const void *)hiccl_exec_kernel<512>};
+    for (int i = 0; i < 4; ++i) {
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d->occ[i], ks[i], 64 << i, 0)) != cudaSuccess)
+        return cuda_fail(c, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+      if (d->occ[i] < 1) return fail(c, HICCL_ERR_CUDA, "executor kernel cannot be resident");
+    }
+  }
 
   const size_t N = p.steps.size();
   unsigned long long scratch_base = 0;
@@ -450,9 +473,16 @@ hiccl_status_t hiccl_start(hiccl_comm_t c, void *stream) {
   DevTable t = d->t;
   t.timeout_ns = c->timeout_ns;
   if (t.nitems > 0) {
-    const int per_sm = std::min(c->ctas_per_sm, d->occ);
+    const int nt = c->threads;
+    const int ti = nt == 64 ? 0 : nt == 128 ? 1 : nt == 256 ? 2 : 3;
+    const int per_sm = std::min(c->ctas_per_sm, d->occ[ti]);
     const unsigned long long grid = std::min<unsigned long long>(t.nitems, (unsigned long long)d->nsm * per_sm);
-    hiccl_exec_kernel<<<(unsigned)grid, NT, 0, s>>>(t);
+    switch (nt) {
+      case 64: hiccl_exec_kernel<64><<<(unsigned)grid, 64, 0, s>>>(t); break;
+      case 128: hiccl_exec_kernel<128><<<(unsigned)grid, 128, 0, s>>>(t); break;
+      case 256: hiccl_exec_kernel<256><<<(unsigned)grid, 256, 0, s>>>(t); break;
+      default: hiccl_exec_kernel<512><<<(unsigned)grid, 512, 0, s>>>(t); break;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "executor launch");
   }

@@ -24,7 +24,7 @@ SUM = 0
 OK, ERR_INVALID, ERR_STATE, ERR_RACE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = ["OK", "INVALID", "STATE", "RACE", "NOMEM", "CUDA", "TIMEOUT", "UNSUPPORTED"]
 
-OPT_TIMEOUT_NS, OPT_CTAS_PER_SM, OPT_ITEM_BYTES, OPT_ORDER = range(4)
+OPT_TIMEOUT_NS, OPT_CTAS_PER_SM, OPT_ITEM_BYTES, OPT_ORDER, OPT_THREADS = range(5)
 
 
 class HicclError(RuntimeError):

@@ -50,8 +50,9 @@ def test_validation_errors():
     with pytest.raises(H.HicclError) as e:
         c.add_multicast(base, base, 8, 0, [1, 1])         # duplicate leaf
     assert e.value.status == H.ERR_INVALID
+    c.add_multicast(base, base, 8, 0, [])                 # no leaf: nothing registered
     with pytest.raises(H.HicclError) as e:
-        c.add_multicast(base, base, 8, 0, [])             # no leaf
+        c.add_reduction(base, base, 8, [], 0)             # a reduction needs a leaf
     assert e.value.status == H.ERR_INVALID
     with pytest.raises(H.HicclError) as e:
         c.add_multicast([0] * 4, base, 8, 0, [1])         # null root buffer
