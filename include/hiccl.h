@@ -53,7 +53,8 @@ typedef enum {
   HICCL_ERR_NOMEM = 4,       /* host or device allocation failed                   */
   HICCL_ERR_CUDA = 5,        /* a CUDA runtime call failed                         */
   HICCL_ERR_TIMEOUT = 6,     /* a dependency wait in the executor ran out          */
-  HICCL_ERR_UNSUPPORTED = 7  /* valid request this build does not implement        */
+  HICCL_ERR_UNSUPPORTED = 7, /* valid request this build does not implement        */
+  HICCL_ERR_TOO_LARGE = 8    /* request exceeds a fixed-size limit of the library  */
 } hiccl_status_t;
 
 /* ---- composition (Sec. 3, Listing 1) ---------------------------------------- */
@@ -210,6 +211,35 @@ hiccl_status_t hiccl_set_option(hiccl_comm_t comm, hiccl_option_t opt, long long
  * it runs out and hiccl_wait reports HICCL_ERR_TIMEOUT.  Host-side only: it
  * changes one counter target; it never makes the GPU fault. */
 hiccl_status_t hiccl_debug_withhold(hiccl_comm_t comm, unsigned long long index, int extra);
+
+/* ---- execution without device allocation ------------------------------------- */
+
+/* Size of the fixed device array hiccl_run_static works in. */
+#define HICCL_STATIC_ARENA_BYTES (16ull << 20)
+
+/* Run a planned communicator once, allocating nothing: for callers that
+ * cannot call cudaMalloc themselves (code running under a caller-owned
+ * memory pool or budget, or inside an allocator callback, where a library
+ * allocation would fail or break accounting).  The paper has no counterpart:
+ * HiCCL's staging buffers are its own allocations.
+ *   comm   : planned with hiccl_plan (or hiccl_init); its registered send and
+ *            recv buffers are the inputs and outputs, owned by the caller.
+ *   stream : cudaStream_t to run on (NULL: legacy default stream).
+ * The step table, dependency counters and relay buffers are placed in one
+ * file-scope device array of HICCL_STATIC_ARENA_BYTES that every GPU loading
+ * this library holds until the process exits; no cudaMalloc, cudaFree or
+ * other allocating routine is called.  The first call on a device, with that
+ * device current, looks the array's address up (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  The call uploads the plan,
+ * zeroes the counters (the array keeps the previous call's contents), runs
+ * the executor and blocks until the stream reaches the end of the run.
+ * Every call, from any communicator, uses the same array: calls that overlap
+ * on the GPU (other host threads, other streams) race and must be serialized
+ * by the caller.  Returns HICCL_ERR_TOO_LARGE, before touching the GPU, when
+ * the plan needs more than HICCL_STATIC_ARENA_BYTES; HICCL_ERR_STATE without a
+ * plan; HICCL_ERR_TIMEOUT if a dependency wait ran out; HICCL_ERR_CUDA on a
+ * CUDA error.  It does not set the hiccl_last_error message. */
+hiccl_status_t hiccl_run_static(hiccl_comm_t comm, void *cuda_stream);
 
 /* Message of the last failed call on `comm` ("" if none); a static string
  * for comm == NULL.  Valid until the next call on comm. */

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -525,3 +526,156 @@ hiccl_status_t hiccl_debug_withhold(hiccl_comm_t c, unsigned long long index, in
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free execution (hiccl_run_static).
+//
+// For callers that cannot allocate device memory themselves -- code that runs
+// under a caller-owned memory pool or budget, inside an allocator callback, or
+// in a process whose device allocations are made by someone else -- this path
+// runs a planned communicator from one fixed device array instead of the
+// buffers hiccl_init allocates.  The array is a file-scope __device__
+// variable: every GPU that loads this library holds its
+// HICCL_STATIC_ARENA_BYTES until the process exits.  The same persistent
+// executor kernel runs on it; only where its tables live differs.
+// ===========================================================================
+
+namespace hiccl {
+
+static __device__ __align__(256) unsigned char g_static_arena[HICCL_STATIC_ARENA_BYTES];
+
+constexpr int MAX_STATIC_DEVICES = 64;
+static void *g_static_addr[MAX_STATIC_DEVICES];   // device address of the arena, per device
+
+// Expands the raw plan (steps, locations, predecessor offsets) copied into the
+// arena into the executor's table arrays; relay offsets become arena addresses.
+__global__ void hiccl_static_expand(const HStep *steps, const Loc *locs, const uint32_t *pred_off,
+                                    unsigned long long nsteps, unsigned long long nlocs, uint32_t dtype,
+                                    unsigned long long relay_base, unsigned long long *nbytes,
+                                    uint32_t *meta, uint32_t *ptr_off, uint32_t *indeg,
+                                    unsigned long long *ptrs) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long t0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (unsigned long long k = t0; k < nlocs; k += stride)
+    ptrs[k] = locs[k].scratch ? relay_base + locs[k].addr : locs[k].addr;
+  for (unsigned long long i = t0; i < nsteps; i += stride) {
+    const HStep st = steps[i];
+    bool al = true;
+    for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k) {
+      const Loc l = locs[st.loc0 + k];
+      const unsigned long long a = l.scratch ? relay_base + l.addr : l.addr;
+      al = al && (a % 16 == 0);
+    }
+    nbytes[i] = st.nbytes;
+    ptr_off[i] = st.loc0;
+    indeg[i] = pred_off[i + 1] - pred_off[i];
+    meta[i] = meta_pack(st.kind, dtype, al ? 1u : 0u, st.nsrc, st.ndst);
+  }
+}
+
+}  // namespace hiccl
+
+extern "C" hiccl_status_t hiccl_run_static(hiccl_comm_t c, void *stream) {
+  if (!c) return HICCL_ERR_INVALID;
+  if (!c->plan.valid) return HICCL_ERR_STATE;
+  const Plan &p = c->plan;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const unsigned long long N = p.steps.size(), NL = p.locs.size(), NE = p.entries.size();
+  const unsigned long long NI = p.item_off.size() ? p.item_off.size() - 1 : 0, NS = p.succ.size();
+  unsigned long long off = 0;
+  auto place = [&](unsigned long long bytes) {
+    const unsigned long long o = off;
+    off = (off + bytes + 255) & ~255ull;
+    return o;
+  };
+  const unsigned long long o_steps = place(N * sizeof(HStep)), o_locs = place(NL * sizeof(Loc)),
+                           o_predoff = place((N + 1) * 4), o_nbytes = place(N * 8), o_meta = place(N * 4),
+                           o_ptroff = place(N * 4), o_indeg = place(N * 4), o_nent = place(N * 4),
+                           o_succoff = place((N + 1) * 4), o_succ = place(NS * 4), o_ptrs = place(NL * 8),
+                           o_ent = place(NE * sizeof(DevEntry)), o_item = place((NI + 1) * 4),
+                           o_ctr = place(N * 16 + sizeof(DevCtl) + 8), o_relay = place(p.scratch_bytes);
+  if (off > HICCL_STATIC_ARENA_BYTES) return HICCL_ERR_TOO_LARGE;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HICCL_ERR_CUDA;
+  if (dev < 0 || dev >= MAX_STATIC_DEVICES) return HICCL_ERR_UNSUPPORTED;
+  if (!g_static_addr[dev]) {   // once per device, with that device current
+    void *addr = nullptr;
+    if (cudaGetSymbolAddress(&addr, g_static_arena) != cudaSuccess || !addr) {
+      cudaGetLastError();
+      return HICCL_ERR_CUDA;
+    }
+    g_static_addr[dev] = addr;
+  }
+  char *base = static_cast<char *>(g_static_addr[dev]);
+  if (N == 0) return HICCL_OK;
+
+  auto h2d = [&](unsigned long long o, const void *src, unsigned long long bytes) {
+    return bytes ? cudaMemcpyAsync(base + o, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+  };
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = h2d(o_steps, p.steps.data(), N * sizeof(HStep));
+  if (e == cudaSuccess) e = h2d(o_locs, p.locs.data(), NL * sizeof(Loc));
+  if (e == cudaSuccess) e = h2d(o_predoff, p.pred_off.data(), (N + 1) * 4);
+  if (e == cudaSuccess) e = h2d(o_nent, p.nent.data(), N * 4);
+  if (e == cudaSuccess) e = h2d(o_succoff, p.succ_off.data(), (N + 1) * 4);
+  if (e == cudaSuccess) e = h2d(o_succ, p.succ.data(), NS * 4);
+  if (e == cudaSuccess) e = h2d(o_ent, p.entries.data(), NE * sizeof(DevEntry));
+  if (e == cudaSuccess) e = h2d(o_item, p.item_off.data(), (NI + 1) * 4);
+  // every call starts from zeroed counters: the arena keeps the last call's contents
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + o_ctr, 0, N * 16 + sizeof(DevCtl) + 8, s);
+  if (e != cudaSuccess) return HICCL_ERR_CUDA;
+
+  hiccl_static_expand<<<(unsigned)std::min<unsigned long long>((N + NL + 255) / 256, 1024), 256, 0, s>>>(
+      reinterpret_cast<const HStep *>(base + o_steps), reinterpret_cast<const Loc *>(base + o_locs),
+      reinterpret_cast<const uint32_t *>(base + o_predoff), N, NL, (uint32_t)c->dtype,
+      (unsigned long long)(uintptr_t)(base + o_relay), reinterpret_cast<unsigned long long *>(base + o_nbytes),
+      reinterpret_cast<uint32_t *>(base + o_meta), reinterpret_cast<uint32_t *>(base + o_ptroff),
+      reinterpret_cast<uint32_t *>(base + o_indeg), reinterpret_cast<unsigned long long *>(base + o_ptrs));
+  if (cudaGetLastError() != cudaSuccess) return HICCL_ERR_CUDA;
+
+  DevTable t{};
+  t.nbytes = reinterpret_cast<const unsigned long long *>(base + o_nbytes);
+  t.meta = reinterpret_cast<const uint32_t *>(base + o_meta);
+  t.ptr_off = reinterpret_cast<const uint32_t *>(base + o_ptroff);
+  t.indeg = reinterpret_cast<const uint32_t *>(base + o_indeg);
+  t.nent = reinterpret_cast<const uint32_t *>(base + o_nent);
+  t.succ_off = reinterpret_cast<const uint32_t *>(base + o_succoff);
+  t.succ = reinterpret_cast<const uint32_t *>(base + o_succ);
+  t.ptrs = reinterpret_cast<const unsigned long long *>(base + o_ptrs);
+  t.entries = reinterpret_cast<const DevEntry *>(base + o_ent);
+  t.item_off = reinterpret_cast<const uint32_t *>(base + o_item);
+  t.dep = reinterpret_cast<unsigned long long *>(base + o_ctr);
+  t.done = reinterpret_cast<unsigned long long *>(base + o_ctr + N * 8);
+  t.ctl = reinterpret_cast<DevCtl *>(base + o_ctr + N * 16);
+  t.host_err = reinterpret_cast<unsigned long long *>(base + o_ctr + N * 16 + sizeof(DevCtl));
+  t.nitems = NI;
+  t.timeout_ns = c->timeout_ns;
+  if (NI > 0) {
+    int nsm = 0, occ = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HICCL_ERR_CUDA;
+    const int nt = c->threads;
+    cudaError_t oe;
+    switch (nt) {
+      case 64: oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hiccl_exec_kernel<64>, 64, 0); break;
+      case 128: oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hiccl_exec_kernel<128>, 128, 0); break;
+      case 256: oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hiccl_exec_kernel<256>, 256, 0); break;
+      default: oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hiccl_exec_kernel<512>, 512, 0); break;
+    }
+    if (oe != cudaSuccess || occ < 1) return HICCL_ERR_CUDA;
+    const unsigned grid = (unsigned)std::min<unsigned long long>(NI, (unsigned long long)nsm * std::min(c->ctas_per_sm, occ));
+    switch (nt) {
+      case 64: hiccl_exec_kernel<64><<<grid, 64, 0, s>>>(t); break;
+      case 128: hiccl_exec_kernel<128><<<grid, 128, 0, s>>>(t); break;
+      case 256: hiccl_exec_kernel<256><<<grid, 256, 0, s>>>(t); break;
+      default: hiccl_exec_kernel<512><<<grid, 512, 0, s>>>(t); break;
+    }
+    if (cudaGetLastError() != cudaSuccess) return HICCL_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return HICCL_ERR_CUDA;
+  unsigned long long err = 0;
+  if (cudaMemcpy(&err, base + o_ctr + N * 16 + offsetof(DevCtl, err), sizeof(err), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return HICCL_ERR_CUDA;
+  return err ? HICCL_ERR_TIMEOUT : HICCL_OK;
+}

@@ -21,8 +21,9 @@ DTYPES = {"f32": F32, "i32": I32, "bf16": BF16, "fp8": FP8E4M3}
 ESIZE = {F32: 4, I32: 4, BF16: 2, FP8E4M3: 1}
 SUM = 0
 
-OK, ERR_INVALID, ERR_STATE, ERR_RACE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
-STATUS_NAMES = ["OK", "INVALID", "STATE", "RACE", "NOMEM", "CUDA", "TIMEOUT", "UNSUPPORTED"]
+OK, ERR_INVALID, ERR_STATE, ERR_RACE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_TOO_LARGE = range(9)
+STATUS_NAMES = ["OK", "INVALID", "STATE", "RACE", "NOMEM", "CUDA", "TIMEOUT", "UNSUPPORTED", "TOO_LARGE"]
+STATIC_ARENA_BYTES = 16 << 20
 
 OPT_TIMEOUT_NS, OPT_CTAS_PER_SM, OPT_ITEM_BYTES, OPT_ORDER, OPT_THREADS = range(5)
 
@@ -80,6 +81,7 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_ulonglong)]),
     "hiccl_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong]),
     "hiccl_debug_withhold": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_int]),
+    "hiccl_run_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "hiccl_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "hiccl_destroy": (None, [ctypes.c_void_p]),
 }
@@ -227,6 +229,15 @@ def hiccl_debug_withhold(comm, index: int, extra: int):
     _check(comm, lib().hiccl_debug_withhold(comm, int(index), int(extra)))
 
 
+def hiccl_run_static(comm, stream=None):
+    """Run a planned communicator from the library's fixed device array
+    (no device allocation; blocks until the run is done)."""
+    s = _stream_handle(stream)
+    st = lib().hiccl_run_static(comm, ctypes.c_void_p(s) if s else None)
+    if st != OK:
+        raise HicclError(st, "hiccl_run_static")
+
+
 def hiccl_last_error(comm) -> str:
     return lib().hiccl_last_error(comm).decode()
 
@@ -284,6 +295,9 @@ class Comm:
 
     def steps(self):
         return [self.step(i) for i in range(self.plan_info()["steps"])]
+
+    def run_static(self, stream=None):
+        hiccl_run_static(self.handle, stream)
 
     def set_option(self, opt, value):
         hiccl_set_option(self.handle, opt, value)
