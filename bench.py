@@ -282,7 +282,8 @@ def run_ours(args):
     d = BYTES_PER_RANK // 4 // P
     x = torch.from_numpy(uniform_ranks(P, d * P, seed=0))
     comms, bufs, nbytes, pbytes = {}, {}, {}, {}
-    for kind in KINDS:
+    kinds = tuple(args.kinds.split(",")) if args.kinds else KINDS
+    for kind in kinds:
         b = C.Buffers(kind, P, d, torch.float32, device)
         b.send.copy_(x[:, :b.ls].to(device))
         b.recv.zero_()
@@ -304,13 +305,13 @@ def run_ours(args):
     step_bytes = sum(nbytes.values())
 
     def one_step(evs=None):
-        for i, kind in enumerate(KINDS):
+        for i, kind in enumerate(kinds):
             if evs is not None:
                 evs[i].record(stream)
             comms[kind].start(stream)
         if evs is not None:
-            evs[len(KINDS)].record(stream)
-        for kind in KINDS:
+            evs[len(kinds)].record(stream)
+        for kind in kinds:
             comms[kind].wait()
 
     for _ in range(max(args.warmup, 3)):
@@ -320,7 +321,7 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    all_evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(KINDS) + 1)] for _ in range(args.steps)]
+    all_evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(kinds) + 1)] for _ in range(args.steps)]
     barrier(device)
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
@@ -331,21 +332,21 @@ def run_ours(args):
     barrier(device)
     clk = clocks.stop()
 
-    per_kind = {kind: [] for kind in KINDS}
+    per_kind = {kind: [] for kind in kinds}
     step_ms = []
     for evs in all_evs:
-        for i, kind in enumerate(KINDS):
+        for i, kind in enumerate(kinds):
             per_kind[kind].append(evs[i].elapsed_time(evs[i + 1]))
-        step_ms.append(evs[0].elapsed_time(evs[len(KINDS)]))
+        step_ms.append(evs[0].elapsed_time(evs[len(kinds)]))
     dev_s = sum(step_ms) / 1e3
     tot_bytes, tot_s = aggregate(step_bytes * args.steps, dev_s, device)
     gbs = tot_bytes / tot_s / 1e9
     peak, peak_kind = measured_peak()
 
     # end to end through the public API with host buffers (pinned)
-    h_send = {k: torch.empty(bufs[k].send.shape, dtype=torch.float32, pin_memory=True) for k in KINDS}
-    h_recv = {k: torch.empty(bufs[k].recv.shape, dtype=torch.float32, pin_memory=True) for k in KINDS}
-    for k in KINDS:
+    h_send = {k: torch.empty(bufs[k].send.shape, dtype=torch.float32, pin_memory=True) for k in kinds}
+    h_recv = {k: torch.empty(bufs[k].recv.shape, dtype=torch.float32, pin_memory=True) for k in kinds}
+    for k in kinds:
         h_send[k].copy_(x[:, :bufs[k].ls])
     h2d = sum(t.numel() * 4 for t in h_send.values())
     d2h = sum(t.numel() * 4 for t in h_recv.values())
@@ -356,10 +357,10 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(e2e_steps):
-        for k in KINDS:
+        for k in kinds:
             bufs[k].send.copy_(h_send[k], non_blocking=True)
         one_step()
-        for k in KINDS:
+        for k in kinds:
             h_recv[k].copy_(bufs[k].recv, non_blocking=True)
         torch.cuda.synchronize(device)
     e1.record(stream)
@@ -373,7 +374,7 @@ def run_ours(args):
         cpu = {"value": b / t / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc}
 
     coll = {}
-    for kind in KINDS:
+    for kind in kinds:
         med = statistics.median(per_kind[kind])
         coll[kind] = {"ms": med, "gbs": nbytes[kind] / med / 1e6, "frac": nbytes[kind] / med / 1e6 / peak,
                       "dp_over_t_gbs": pbytes[kind] / med / 1e6, "schedule_bytes": nbytes[kind],
@@ -387,7 +388,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": gbs / world, "peak": peak, "unit": "GB/s",
                      "frac": gbs / world / peak, "peak_source": peak_kind,
                      "traffic": traffic, "kernel": "hiccl_exec_kernel"},
-        "clocks": clk, "gpu_launches": len(KINDS) * args.steps * world,
+        "clocks": clk, "gpu_launches": len(kinds) * args.steps * world,
         "e2e": {"value": eb / es / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "collectives": coll, "wall_ms_per_step": wall / args.steps * 1e3,
         "cpu_baseline": cpu,
@@ -409,6 +410,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--item-bytes", type=int, default=0, help="executor work-item size (0: library default)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="executor CTAs per SM (0: library default)")
+    ap.add_argument("--kinds", default="", help="comma-separated subset of the seven collectives (profiling)")
     ap.add_argument("--threads", type=int, default=0, help="executor threads per CTA (0: library default)")
     ap.add_argument("--order", type=int, default=None, help="work order: 0 pipeline slots, 1 stage depth")
     args = ap.parse_args(argv)

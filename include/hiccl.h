@@ -196,15 +196,28 @@ hiccl_status_t hiccl_get_step(hiccl_comm_t comm, unsigned long long index,
 
 typedef enum {
   HICCL_OPT_TIMEOUT_NS = 0,   /* dependency-wait limit inside the executor (default 1e9)  */
-  HICCL_OPT_CTAS_PER_SM = 1,  /* executor CTAs per SM, capped by occupancy (default 8)    */
-  HICCL_OPT_ITEM_BYTES = 2,   /* target output bytes of one work item (default 32768)     */
-  HICCL_OPT_ORDER = 3,        /* work order: 0 pipeline slots (default), 1 stage depth    */
-  HICCL_OPT_THREADS = 4       /* threads per executor CTA: 64 (default), 128, 256, 512  */
+  HICCL_OPT_CTAS_PER_SM = 1,  /* executor CTAs per SM, capped by occupancy (default 2)    */
+  HICCL_OPT_ITEM_BYTES = 2,   /* largest work item, bytes of step data (default 65536)    */
+  HICCL_OPT_ORDER = 3,        /* work order: 0 pipeline slots, 1 stage depth (default)    */
+  HICCL_OPT_THREADS = 4,      /* threads per executor CTA: 128, 256 (default), 512       */
+  HICCL_OPT_TRACE = 5,        /* 1: record per-item timestamps (hiccl_get_trace); default 0 */
+  HICCL_OPT_SLOT_ITEMS = 6    /* items a pipeline slot is spread over (default 1024)      */
 } hiccl_option_t;
 
 /* Set an option.  TIMEOUT_NS, CTAS_PER_SM and THREADS apply to the next start;
- * ITEM_BYTES and ORDER must be set before hiccl_init / hiccl_plan. */
+ * ITEM_BYTES, ORDER and SLOT_ITEMS must be set before hiccl_init / hiccl_plan,
+ * TRACE before hiccl_init.  A work item holds at most
+ * max(4096, min(ITEM_BYTES, bytes of its slot / SLOT_ITEMS)) bytes of steps. */
 hiccl_status_t hiccl_set_option(hiccl_comm_t comm, hiccl_option_t opt, long long value);
+
+/* Executor trace of the last start (HICCL_OPT_TRACE set before hiccl_init).
+ * For every work item, in ticket order, 5 values: the %globaltimer time (ns)
+ * its staging began, the time its predecessors were satisfied and it was
+ * handed to the data warps, the time its data movement ended, the time its
+ * successors were released, and the SM that ran it.  `out` receives
+ * min(capacity, 5 * items) values; *written gets that count.  Call after
+ * hiccl_wait.  HICCL_ERR_STATE if tracing was not enabled. */
+hiccl_status_t hiccl_get_trace(hiccl_comm_t comm, unsigned long long *out, size_t capacity, size_t *written);
 
 /* Fault injection for tests: add `extra` (0 restores) phantom dependencies to
  * step `index` in the uploaded table, so that the executor's bounded wait for

@@ -22,8 +22,9 @@ namespace hiccl {
 
 // A warp moves one segment of a step at a time: SEG_BYTES of every operand.
 constexpr uint32_t SEG_BYTES = 4096;
-constexpr uint32_t MAX_ENTRIES_PER_ITEM = 32;
+constexpr uint32_t MAX_ENTRIES_PER_ITEM = 64;
 constexpr uint32_t MAX_FANIN = 1024;    // reduce inputs / copy destinations per step
+constexpr uint32_t TMA_MAX_FANIN = 8;   // reduce inputs folded in shared memory
 
 enum : uint32_t { OP_COPY = 0, OP_REDUCE = 1 };
 
@@ -70,9 +71,10 @@ struct DevTable {
   unsigned long long *host_err;       // mapped host word mirroring ctl->err
   unsigned long long nitems;
   unsigned long long timeout_ns;
+  unsigned long long *trace;          // [nitems][4] timestamps, or null (see hiccl_get_trace)
 };
 
-enum : uint32_t { ERR_TIMEOUT = 1, ERR_BADSTEP = 2 };
+enum : uint32_t { ERR_TIMEOUT = 1, ERR_BADSTEP = 2, ERR_STALL = 3 };
 
 // ---------------------------------------------------------------------------
 // host-side plan
@@ -119,7 +121,7 @@ struct Plan {
   std::vector<uint32_t> succ_off, succ;    // CSR of successors
   std::vector<DevEntry> entries;
   std::vector<uint32_t> item_off;
-  std::vector<uint32_t> nent;
+  std::vector<uint32_t> nent;             // entries covering each step
   unsigned long long scratch_bytes = 0;
   std::vector<unsigned long long> level_bytes;
   unsigned long long hbm_read = 0, hbm_write = 0;
@@ -138,10 +140,12 @@ struct hiccl_comm {
   enum State { COMPOSING, PLANNED, READY, RUNNING } state = COMPOSING;
   // options
   unsigned long long timeout_ns = 1000000000ull;
-  int ctas_per_sm = 8;
-  int threads = 64;
-  unsigned long long item_bytes = 32768;
-  int order = 0;
+  int ctas_per_sm = 2;
+  int threads = 256;
+  unsigned long long item_bytes = 65536;
+  int order = 1;
+  unsigned long long slot_items = 1024;
+  int trace = 0;
   hiccl::Plan plan;
   hiccl::DevState *dev = nullptr;
   std::string err;

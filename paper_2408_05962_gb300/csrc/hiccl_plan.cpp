@@ -467,10 +467,31 @@ static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevel
     maxslot = std::max(maxslot, slot[i]);
   }
 
-  // execution order: by slot, then emission order (stable)
+  // data-path class of a step (see the executor): 0 = copy whose operands
+  // are all 16-byte aligned, moved by bulk asynchronous copies; 1 = aligned
+  // reduce of at most TMA_MAX_FANIN inputs, bulk-loaded into shared memory and
+  // folded there; 2 = anything else, moved by vector loads and stores.  Relay
+  // buffers are 256-byte aligned.
+  std::vector<uint8_t> klass(N, 2);
+  for (size_t i = 0; i < N; ++i) {
+    const HStep &st = B.steps[i];
+    bool al = true;
+    for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k) {
+      const Loc &l = B.locs[st.loc0 + k];
+      al = al && (l.scratch || l.addr % 16 == 0);
+    }
+    if (!al) continue;
+    if (st.kind == OP_COPY) klass[i] = 0;
+    else if (st.nsrc <= TMA_MAX_FANIN) klass[i] = 1;
+  }
+
+  // execution order: by slot, then data-path class, then emission order; a
+  // slot has no internal dependencies, so any order inside it is valid
   std::vector<uint32_t> order(N);
   std::iota(order.begin(), order.end(), 0u);
-  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return slot[a] < slot[b]; });
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+    return slot[a] != slot[b] ? slot[a] < slot[b] : klass[a] < klass[b];
+  });
   std::vector<uint32_t> pos(N);
   for (size_t k = 0; k < N; ++k) pos[order[k]] = (uint32_t)k;
 
@@ -516,32 +537,49 @@ static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevel
     }
   }
 
-  // work items: consecutive steps of one slot (so no item depends on itself),
-  // cut into runs of at most item_bytes / SEG_BYTES segments
-  unsigned long long cap = std::max<unsigned long long>(1, c->item_bytes / SEG_BYTES);
+  // work items: consecutive steps of one slot (so no item depends on itself)
+  // and one data-path class, cut into runs of at most `cap` segment bytes and
+  // MAX_ENTRIES_PER_ITEM steps.  A slot with little data gets small items, so
+  // that it still spreads over about slot_items CTAs: the early levels of a
+  // tree are short but lie on the critical path.
+  std::vector<unsigned long long> slot_bytes(N ? plan.steps.back().slot + 1 : 0, 0);
+  for (const HStep &st : plan.steps) slot_bytes[st.slot] += st.nbytes;
+  auto slot_cap = [&](unsigned long long sl) {
+    unsigned long long v = (slot_bytes[sl] + c->slot_items - 1) / c->slot_items;
+    v = (v + SEG_BYTES - 1) / SEG_BYTES * SEG_BYTES;
+    return std::min<unsigned long long>(std::max<unsigned long long>(v, SEG_BYTES),
+                                        std::max<unsigned long long>(SEG_BYTES, c->item_bytes));
+  };
+  unsigned long long cap = SEG_BYTES;
   plan.nent.assign(N, 0);
   plan.item_off.push_back(0);
-  unsigned long long cur_segs = 0;
+  unsigned long long cur_segs = 0;   // bytes in the open item
   unsigned long long cur_slot = ~0ull;
+  int cur_class = -1;
   auto close_item = [&]() {
     if (plan.entries.size() > plan.item_off.back()) plan.item_off.push_back((uint32_t)plan.entries.size());
     cur_segs = 0;
   };
   for (size_t k = 0; k < N; ++k) {
     const HStep &st = plan.steps[k];
-    if (st.slot != cur_slot) {
+    if (st.slot != cur_slot || klass[order[k]] != cur_class) {
       close_item();
       cur_slot = st.slot;
+      cur_class = klass[order[k]];
+      cap = slot_cap(st.slot);
     }
     unsigned long long nseg = (st.nbytes + SEG_BYTES - 1) / SEG_BYTES;
     if (nseg > 0xFFFFFFFFull) return fail(c, HICCL_ERR_UNSUPPORTED, "step too large");
     unsigned long long done = 0;
     while (done < nseg) {
-      unsigned long long take = std::min(nseg - done, cap - cur_segs);
+      // whole segments that fit the open item (at least one)
+      const unsigned long long room = cap > cur_segs ? (cap - cur_segs) / SEG_BYTES : 0;
+      unsigned long long take = std::max<unsigned long long>(1, std::min(nseg - done, room));
       plan.entries.push_back(DevEntry{(uint32_t)k, (uint32_t)done, (uint32_t)(done + take), 0});
       plan.nent[k]++;
+      const unsigned long long bytes = std::min(st.nbytes, (done + take) * SEG_BYTES) - done * SEG_BYTES;
       done += take;
-      cur_segs += take;
+      cur_segs += bytes;
       if (cur_segs >= cap || plan.entries.size() - plan.item_off.back() >= MAX_ENTRIES_PER_ITEM)
         close_item();
     }
@@ -792,9 +830,19 @@ hiccl_status_t hiccl_set_option(hiccl_comm_t c, hiccl_option_t opt, long long va
       c->ctas_per_sm = (int)value;
       return HICCL_OK;
     case HICCL_OPT_THREADS:
-      if (value != 64 && value != 128 && value != 256 && value != 512)
-        return fail(c, HICCL_ERR_INVALID, "threads per CTA must be 64, 128, 256 or 512");
+      if (value != 128 && value != 256 && value != 512)
+        return fail(c, HICCL_ERR_INVALID, "threads per CTA must be 128, 256 or 512");
       c->threads = (int)value;
+      return HICCL_OK;
+    case HICCL_OPT_TRACE:
+      if (c->state != hiccl_comm::COMPOSING && c->state != hiccl_comm::PLANNED)
+        return fail(c, HICCL_ERR_STATE, "set before hiccl_init");
+      c->trace = value ? 1 : 0;
+      return HICCL_OK;
+    case HICCL_OPT_SLOT_ITEMS:
+      if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "set before planning");
+      if (value < 1 || value > (1ll << 24)) return fail(c, HICCL_ERR_INVALID, "slot items out of range");
+      c->slot_items = (unsigned long long)value;
       return HICCL_OK;
     case HICCL_OPT_ITEM_BYTES:
       if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "set before planning");

@@ -34,7 +34,7 @@ namespace hiccl {
 struct DevState {
   int device = -1;
   int nsm = 0;
-  int occ[4] = {0, 0, 0, 0};        // resident CTAs per SM for 64/128/256/512 threads
+  int occ[4] = {0, 0, 0, 0};        // resident CTAs per SM for 128/256/512 threads (index 1..3)
   void *table = nullptr;            // read-only arrays
   void *counters = nullptr;         // dep[], done[], ctl
   size_t counters_bytes = 0;
@@ -45,6 +45,7 @@ struct DevState {
   DevTable t{};
   std::vector<uint32_t> indeg;      // host copy, for fault injection
   uint32_t *indeg_dev = nullptr;
+  unsigned long long *trace = nullptr;   // [nitems][5] when tracing
 };
 
 // ---------------------------------------------------------------------------
@@ -67,6 +68,14 @@ __device__ __forceinline__ void red_release_add(unsigned long long *p, unsigned 
 __device__ __forceinline__ unsigned long long atom_acq_rel_add(unsigned long long *p, unsigned long long v) {
   unsigned long long old;
   asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_relaxed_add(unsigned long long *p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long atom_relaxed_add(unsigned long long *p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.relaxed.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
   return old;
 }
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -187,122 +196,458 @@ __device__ __forceinline__ void warp_reduce(const unsigned long long *ptrs, uint
 // the persistent executor
 // ---------------------------------------------------------------------------
 
-constexpr int PMAX = 8;   // pointers of a step staged in shared memory (more: read from global)
+constexpr int PMAX = 6;   // pointers of a step staged in shared memory (more: read from global)
+constexpr int NBUF = 3;   // work items staged ahead of the data warps
+
+// one staged work item: its entries, their steps' descriptors and pointers
+struct ItemBuf {
+  DevEntry ent[MAX_ENTRIES_PER_ITEM];
+  uint32_t pre[MAX_ENTRIES_PER_ITEM + 1];   // prefix sums of the entries' segment counts
+  uint32_t meta[MAX_ENTRIES_PER_ITEM];
+  uint32_t poff[MAX_ENTRIES_PER_ITEM];
+  unsigned long long nb[MAX_ENTRIES_PER_ITEM];
+  unsigned long long ptr[MAX_ENTRIES_PER_ITEM][PMAX];
+  uint32_t nent;
+  uint32_t end;                             // no more items: leave the loop
+  unsigned long long item;                  // ticket of the staged item
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// wait for the phase of `parity` to complete; false after `limit_ns`
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > limit_ns) return false;
+  return true;
+}
+
+// bulk asynchronous copies (TMA engine, no tensor map): global -> shared
+// completing on an mbarrier, shared -> global tracked by bulk groups
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *sdst, const void *gsrc, uint32_t bytes, unsigned long long *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(sdst)),
+               "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void *gdst, const void *ssrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(ssrc)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 template <int NT>
+struct ExecShape {
+  static constexpr int D = NT / 32 - 2;                 // data warps
+  static constexpr int NS = NT >= 512 ? 2 : NT >= 256 ? 3 : 4;   // staging slots per data warp
+  static constexpr int SMEM = D * NS * SEG_BYTES;       // dynamic shared memory (bytes)
+};
+
+// Locate the i-th of this warp's segments in a staged item: entry index k,
+// byte offset lo in the step, bytes n and the step's pointer list.
+struct SegRef {
+  uint32_t k;
+  unsigned long long lo;
+  uint32_t n;
+};
+template <typename Buf>
+__device__ __forceinline__ SegRef seg_of(const Buf &B, uint32_t j) {
+  uint32_t k = 0, hi = B.nent;   // largest k with pre[k] <= j
+  while (hi - k > 1) {
+    const uint32_t mid = (k + hi) >> 1;
+    if (B.pre[mid] <= j) k = mid;
+    else hi = mid;
+  }
+  SegRef r;
+  r.k = k;
+  const unsigned long long seg = B.ent[k].seg_lo + (j - B.pre[k]);
+  r.lo = seg * SEG_BYTES;
+  r.n = (uint32_t)min((unsigned long long)SEG_BYTES, B.nb[k] - r.lo);
+  return r;
+}
+
+// Warp-specialized persistent executor.  Warp 0 (control) claims work items
+// in ticket order, stages each into one of NBUF shared-memory buffers and
+// waits for the steps' predecessors; warps 2.. (data) move the staged item's
+// segments; warp 1 (completion) waits until the data warps are done with an
+// item, then releases the successors of the steps it finished and frees the
+// buffer.  The three roles are chained by mbarriers (full -> done -> empty),
+// so staging and dependency signalling overlap the data movement.  Only the
+// control warp waits on other items, and nothing it waits for depends on it.
+template <int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable T) {
-  constexpr int NW = NT / 32;   // warps per CTA
-  __shared__ DevEntry s_ent[MAX_ENTRIES_PER_ITEM];
-  __shared__ uint32_t s_pre[MAX_ENTRIES_PER_ITEM + 1];
-  __shared__ uint32_t s_meta[MAX_ENTRIES_PER_ITEM];
-  __shared__ uint32_t s_poff[MAX_ENTRIES_PER_ITEM];
-  __shared__ unsigned long long s_nb[MAX_ENTRIES_PER_ITEM];
-  __shared__ unsigned long long s_ptr[MAX_ENTRIES_PER_ITEM][PMAX];
-  __shared__ unsigned long long s_item, s_next;
-  __shared__ int s_abort;
-  __shared__ uint32_t s_nent;
+  constexpr int D = ExecShape<NT>::D;     // data warps
+  constexpr int NS = ExecShape<NT>::NS;   // staging slots per data warp
+  static_assert(D >= 1, "need at least one data warp");
+  __shared__ ItemBuf buf[NBUF];
+  __shared__ __align__(8) unsigned long long full_bar[NBUF], done_bar[NBUF], empty_bar[NBUF];
+  __shared__ __align__(8) unsigned long long ld_bar[D][NS];
+  __shared__ __align__(8) unsigned long long red_bar[D];
+  extern __shared__ __align__(128) unsigned char stage[];   // D x NS x SEG_BYTES
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned long long epoch = ld_relaxed(&T.ctl->epoch) + 1;   // this launch
-
+  const unsigned long long limit = 2 * T.timeout_ns + 1000000ull;    // bound of the in-CTA waits
   if (tid == 0) {
-    s_item = atomicAdd(&T.ctl->ticket, 1ull);
-    s_abort = ld_relaxed(&T.ctl->err) != 0ull;
+    for (int b = 0; b < NBUF; ++b) {
+      mbar_init(&full_bar[b], 32);
+      mbar_init(&done_bar[b], D * 32);
+      mbar_init(&empty_bar[b], 32);
+    }
+    for (int w = 0; w < D; ++w) {
+      for (int k = 0; k < NS; ++k) mbar_init(&ld_bar[w][k], 1);
+      mbar_init(&red_bar[w], 1);
+    }
   }
   __syncthreads();
-  for (;;) {
-    const unsigned long long item = s_item;
-    if (item >= T.nitems || s_abort) break;
 
-    // phase A: stage the item's entries, step descriptors and pointers in
-    // shared memory and wait for the steps' predecessors (warp 0); claim the
-    // next item meanwhile (warp 1), so its ticket latency is hidden
-    if (warp == 0) {
-      const uint32_t e0 = ldg_ro(T.item_off + item), e1 = ldg_ro(T.item_off + item + 1);
-      const uint32_t ne = e1 - e0;
-      uint32_t cnt = 0, s = 0;
-      if (lane < (int)ne) {
-        const DevEntry e = T.entries[e0 + lane];
-        s = e.step;
-        const uint32_t meta = ldg_ro(T.meta + s), po = ldg_ro(T.ptr_off + s);
-        s_ent[lane] = e;
-        s_meta[lane] = meta;
-        s_poff[lane] = po;
-        s_nb[lane] = ldg_ro(T.nbytes + s);
-        const uint32_t np = meta_nsrc(meta) + meta_ndst(meta);
-        if (np <= PMAX)
-          for (uint32_t q = 0; q < np; ++q) s_ptr[lane][q] = ldg_ro(T.ptrs + po + q);
-        cnt = e.seg_hi - e.seg_lo;
+  if (warp == 0) {
+    // ---- control: claim, stage, wait for predecessors ----
+    for (uint32_t r = 0;; ++r) {
+      const int b = r % NBUF;
+      const uint32_t ph = (r / NBUF) & 1u;
+      ItemBuf &B = buf[b];
+      bool stop = false;
+      if (r >= NBUF && !mbar_wait(&empty_bar[b], ph ^ 1u, limit)) {
+        if (lane == 0) raise_error(T, (unsigned long long)ERR_STALL << 32);
+        stop = true;
       }
-      uint32_t inc = cnt;   // inclusive warp scan of segment counts
+      unsigned long long item = 0;
+      const unsigned long long t_claim = T.trace ? global_ns() : 0ull;
+      if (!stop) {
+        if (lane == 0) item = atomicAdd(&T.ctl->ticket, 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        stop = item >= T.nitems || ld_relaxed(&T.ctl->err) != 0ull;
+      }
+      if (!stop) {
+        const uint32_t e0 = ldg_ro(T.item_off + item), e1 = ldg_ro(T.item_off + item + 1);
+        const uint32_t ne = e1 - e0;
+        uint32_t cnt[2] = {0, 0}, sv[2] = {0, 0};
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += v;
-      }
-      if (lane < (int)ne) s_pre[lane + 1] = inc;
-      if (lane == 0) {
-        s_pre[0] = 0;
-        s_nent = ne;
-      }
-      if (lane < (int)ne) {
-        const unsigned long long target = (unsigned long long)ldg_ro(T.indeg + s) * epoch;
-        if (target && ld_acquire(T.dep + s) < target) {
-          const unsigned long long t0 = global_ns();
-          unsigned ns = 32;
-          while (ld_acquire(T.dep + s) < target) {
-            if (ld_relaxed(&T.ctl->err)) {
-              s_abort = 1;
-              break;
-            }
-            if (global_ns() - t0 > T.timeout_ns) {
-              raise_error(T, ((unsigned long long)ERR_TIMEOUT << 32) | s);
-              s_abort = 1;
-              break;
-            }
-            __nanosleep(ns);
-            if (ns < 256) ns <<= 1;
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t x = lane + 32 * h;
+          if (x < ne) {
+            const DevEntry e = T.entries[e0 + x];
+            const uint32_t s = e.step;
+            sv[h] = s;
+            const uint32_t meta = ldg_ro(T.meta + s), po = ldg_ro(T.ptr_off + s);
+            B.ent[x] = e;
+            B.meta[x] = meta;
+            B.poff[x] = po;
+            B.nb[x] = ldg_ro(T.nbytes + s);
+            const uint32_t np = meta_nsrc(meta) + meta_ndst(meta);
+            if (np <= PMAX)
+              for (uint32_t q = 0; q < np; ++q) B.ptr[x][q] = ldg_ro(T.ptrs + po + q);
+            cnt[h] = e.seg_hi - e.seg_lo;
           }
         }
+        // inclusive warp scans of the segment counts of entries 0..31 and 32..63
+        uint32_t inc0 = cnt[0], inc1 = cnt[1];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t v0 = __shfl_up_sync(0xffffffffu, inc0, o);
+          const uint32_t v1 = __shfl_up_sync(0xffffffffu, inc1, o);
+          if (lane >= o) {
+            inc0 += v0;
+            inc1 += v1;
+          }
+        }
+        const uint32_t half = __shfl_sync(0xffffffffu, inc0, 31);
+        if (lane < (int)ne) B.pre[lane + 1] = inc0;
+        if (lane + 32 < (int)ne) B.pre[lane + 33] = half + inc1;
+        if (lane == 0) {
+          B.pre[0] = 0;
+          B.nent = ne;
+        }
+        bool bad = false;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t x = lane + 32 * h;
+          if (x < ne && !bad) {
+            const uint32_t s = sv[h];
+            const unsigned long long target = (unsigned long long)ldg_ro(T.indeg + s) * epoch;
+            if (target && ld_acquire(T.dep + s) < target) {
+              const unsigned long long t0 = global_ns();
+              unsigned ns = 32;
+              while (ld_acquire(T.dep + s) < target) {
+                if (ld_relaxed(&T.ctl->err)) {
+                  bad = true;
+                  break;
+                }
+                if (global_ns() - t0 > T.timeout_ns) {
+                  raise_error(T, ((unsigned long long)ERR_TIMEOUT << 32) | s);
+                  bad = true;
+                  break;
+                }
+                __nanosleep(ns);
+                if (ns < 256) ns <<= 1;
+              }
+            }
+          }
+        }
+        stop = __any_sync(0xffffffffu, bad);
       }
-    } else if (tid == 32) {
-      s_next = atomicAdd(&T.ctl->ticket, 1ull);
-      if (ld_relaxed(&T.ctl->err)) s_abort = 1;
+      if (lane == 0) {
+        B.end = stop ? 1u : 0u;
+        if (!stop) B.item = item;
+        if (T.trace && !stop) {
+          T.trace[item * 5 + 0] = t_claim;
+          T.trace[item * 5 + 1] = global_ns();
+          unsigned smid;
+          asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+          T.trace[item * 5 + 4] = smid;
+        }
+      }
+      __syncwarp();
+      mbar_arrive(&full_bar[b]);
+      if (stop) break;
     }
-    __syncthreads();
-    if (s_abort) break;
-
-    // phase B: move the data; warp w takes segments w, w + NW, ... of the item
-    const uint32_t total = s_pre[s_nent];
-    uint32_t k = 0;
-    for (uint32_t j = warp; j < total; j += NW) {
-      while (s_pre[k + 1] <= j) ++k;
-      const unsigned long long seg = s_ent[k].seg_lo + (j - s_pre[k]);
-      const unsigned long long lo = seg * SEG_BYTES;
-      const uint32_t n = (uint32_t)min((unsigned long long)SEG_BYTES, s_nb[k] - lo);
-      const uint32_t meta = s_meta[k];
-      const uint32_t np = meta_nsrc(meta) + meta_ndst(meta);
-      const unsigned long long *ptrs = np <= PMAX ? s_ptr[k] : T.ptrs + s_poff[k];
-      if (meta_op(meta) == OP_COPY)
-        warp_copy(ptrs, meta_ndst(meta), lo, n, meta_aligned(meta), lane);
-      else
-        warp_reduce(ptrs, meta_nsrc(meta), meta_dtype(meta), lo, n, meta_aligned(meta), lane);
-    }
-    __syncthreads();
-
-    // phase C: the last entry of a step releases its successors
-    if (tid < (int)s_nent) {
-      const uint32_t s = s_ent[tid].step;
+  } else if (warp == 1) {
+    // ---- completion: release the successors of finished steps ----
+    for (uint32_t r = 0;; ++r) {
+      const int b = r % NBUF;
+      const uint32_t ph = (r / NBUF) & 1u;
+      ItemBuf &B = buf[b];
+      if (!mbar_wait(&full_bar[b], ph, limit)) {
+        if (lane == 0) raise_error(T, (unsigned long long)ERR_STALL << 32);
+        break;
+      }
+      if (B.end) break;
+      if (!mbar_wait(&done_bar[b], ph, limit)) {
+        if (lane == 0) raise_error(T, (unsigned long long)ERR_STALL << 32);
+        break;
+      }
+      if (T.trace && lane == 0) T.trace[B.item * 5 + 2] = global_ns();
+      // fence-based release: one fence orders this item's data before the
+      // counter updates; the last finisher of a step fences again (acquiring
+      // the other finishers' data) before it releases the step's successors
       __threadfence();
-      const unsigned long long old = atom_acq_rel_add(T.done + s, 1ull);
-      if (old + 1 == (unsigned long long)ldg_ro(T.nent + s) * epoch) {
-        __threadfence();
-        const uint32_t a = ldg_ro(T.succ_off + s), b = ldg_ro(T.succ_off + s + 1);
-        for (uint32_t q = a; q < b; ++q) red_release_add(T.dep + ldg_ro(T.succ + q), 1ull);
+      for (uint32_t x = lane; x < B.nent; x += 32) {
+        const uint32_t s = B.ent[x].step;
+        const unsigned long long old = atom_relaxed_add(T.done + s, 1ull);
+        if (old + 1 == (unsigned long long)ldg_ro(T.nent + s) * epoch) {
+          __threadfence();
+          const uint32_t a = ldg_ro(T.succ_off + s), z = ldg_ro(T.succ_off + s + 1);
+          for (uint32_t q = a; q < z; ++q) red_relaxed_add(T.dep + ldg_ro(T.succ + q), 1ull);
+        }
       }
+      __syncwarp();
+      if (T.trace && lane == 0) T.trace[B.item * 5 + 3] = global_ns();
+      mbar_arrive(&empty_bar[b]);
     }
-    if (tid == 0) s_item = s_next;
-    __syncthreads();
+  } else {
+    // ---- data: warp d moves segments d, d + D, ... of each staged item ----
+    // Aligned copies go through the bulk-copy engine: each segment is loaded
+    // once into one of NS staging slots and stored from there to every
+    // destination.  The first loads of the next staged item are issued before
+    // the current item's stores are drained, so the drain overlaps them.
+    const int dw = warp - 2;
+    unsigned char *my_stage = stage + (size_t)dw * NS * SEG_BYTES;
+    uint32_t seq = 0;        // bulk loads issued by this warp (slot = seq % NS, phase = seq / NS)
+    uint32_t pre_issued = 0; // loads of the current item issued early (during the previous item)
+    uint32_t rseq = 0;       // completed phases of this warp's reduce barrier
+    auto is_tma = [](const ItemBuf &X) { return meta_op(X.meta[0]) == OP_COPY && meta_aligned(X.meta[0]) != 0; };
+    auto is_tma_reduce = [](const ItemBuf &X) {
+      return meta_op(X.meta[0]) == OP_REDUCE && meta_aligned(X.meta[0]) != 0 && meta_nsrc(X.meta[0]) <= TMA_MAX_FANIN;
+    };
+    auto mine = [&](const ItemBuf &X) {
+      const uint32_t total = X.pre[X.nent];
+      return total > (uint32_t)dw ? (total - dw + D - 1) / D : 0u;
+    };
+    auto issue = [&](const ItemBuf &X, uint32_t i, uint32_t at) {   // segment i of X into load number `at`
+      const SegRef g = seg_of(X, dw + i * D);
+      const uint32_t np = meta_nsrc(X.meta[g.k]) + meta_ndst(X.meta[g.k]);
+      const unsigned long long *ptrs = np <= PMAX ? X.ptr[g.k] : T.ptrs + X.poff[g.k];
+      const uint32_t slot = at % NS;
+      const uint32_t n16 = g.n & ~15u;
+      mbar_expect_tx(&ld_bar[dw][slot], n16);
+      if (n16)
+        bulk_g2s(my_stage + slot * SEG_BYTES, reinterpret_cast<const char *>(ptrs[0]) + g.lo, n16, &ld_bar[dw][slot]);
+    };
+    for (uint32_t r = 0;; ++r) {
+      const int b = r % NBUF;
+      const uint32_t ph = (r / NBUF) & 1u;
+      const ItemBuf &B = buf[b];
+      if (!mbar_wait(&full_bar[b], ph, limit)) {
+        if (lane == 0) raise_error(T, (unsigned long long)ERR_STALL << 32);
+        break;
+      }
+      if (B.end) break;
+      const uint32_t total = B.pre[B.nent];
+      if (is_tma(B)) {
+        const uint32_t nm = mine(B);
+        bool stalled = false;
+        if (lane == 0) {
+          if (nm) {
+            const uint32_t pro = nm < (uint32_t)NS ? nm : (uint32_t)NS;
+            if (!pre_issued) fence_proxy_async_global();   // inputs were acquired through the generic proxy
+            for (uint32_t i = pre_issued; i < pro; ++i) issue(B, i, seq + i);
+            for (uint32_t i = 0; i < nm; ++i) {
+              const uint32_t slot = (seq + i) % NS, par = ((seq + i) / NS) & 1u;
+              if (!mbar_wait(&ld_bar[dw][slot], par, limit)) {
+                raise_error(T, (unsigned long long)ERR_STALL << 32);
+                stalled = true;
+                break;
+              }
+              const SegRef g = seg_of(B, dw + i * D);
+              const uint32_t meta = B.meta[g.k];
+              const uint32_t np = meta_nsrc(meta) + meta_ndst(meta);
+              const unsigned long long *ptrs = np <= PMAX ? B.ptr[g.k] : T.ptrs + B.poff[g.k];
+              const uint32_t n16 = g.n & ~15u;
+              if (n16) {
+                for (uint32_t q = 0; q < meta_ndst(meta); ++q)
+                  bulk_s2g(reinterpret_cast<char *>(ptrs[1 + q]) + g.lo, my_stage + slot * SEG_BYTES, n16);
+                bulk_commit();
+              }
+              if (i + NS < nm) {
+                bulk_wait_read_all();   // the slot's stores have read it
+                issue(B, i + NS, seq + i + NS);
+              }
+            }
+            if (!stalled) seq += nm;
+          }
+          pre_issued = 0;
+          if (!stalled) {
+            // start the next staged item's loads (its slots are free once the
+            // stores above have read them), then drain this item's stores
+            bulk_wait_read_all();
+            const int b2 = (r + 1) % NBUF;
+            const ItemBuf &B2 = buf[b2];
+            if (mbar_try_wait(&full_bar[b2], ((r + 1) / NBUF) & 1u) && !B2.end && is_tma(B2)) {
+              const uint32_t nm2 = mine(B2);
+              const uint32_t pro2 = nm2 < (uint32_t)NS ? nm2 : (uint32_t)NS;
+              fence_proxy_async_global();
+              for (uint32_t i = 0; i < pro2; ++i) issue(B2, i, seq + i);
+              pre_issued = pro2;
+            }
+          }
+          bulk_wait_all();             // every store of this item is complete
+          fence_proxy_async_global();  // and ordered before the completion warp's generic release
+        }
+        if (__shfl_sync(0xffffffffu, stalled ? 1 : 0, 0)) break;
+        pre_issued = __shfl_sync(0xffffffffu, pre_issued, 0);
+        // ragged tails (the last few bytes of a step that are not a 16-byte multiple)
+        for (uint32_t i = 0; i < nm; ++i) {
+          const SegRef g = seg_of(B, dw + i * D);
+          const uint32_t n16 = g.n & ~15u;
+          if (n16 == g.n) continue;
+          const uint32_t meta = B.meta[g.k];
+          const uint32_t np = meta_nsrc(meta) + meta_ndst(meta);
+          const unsigned long long *ptrs = np <= PMAX ? B.ptr[g.k] : T.ptrs + B.poff[g.k];
+          if (lane < (int)(g.n - n16)) {
+            const char v = __ldcg(reinterpret_cast<const char *>(ptrs[0]) + g.lo + n16 + lane);
+            for (uint32_t q = 0; q < meta_ndst(meta); ++q)
+              (reinterpret_cast<char *>(ptrs[1 + q]) + g.lo + n16)[lane] = v;
+          }
+        }
+        __syncwarp();
+      } else if (is_tma_reduce(B)) {
+        // aligned reduces: bulk-load the f inputs of a chunk into the warp's
+        // staging area, fold them in order from shared memory, and bulk-store
+        // the result from shared memory
+        constexpr uint32_t AREA = NS * SEG_BYTES;
+        if (lane == 0) fence_proxy_async_global();   // inputs were acquired through the generic proxy
+        bool stalled = false;
+        const uint32_t nm = mine(B);
+        for (uint32_t i = 0; i < nm && !stalled; ++i) {
+          const SegRef g = seg_of(B, dw + i * D);
+          const uint32_t meta = B.meta[g.k];
+          const uint32_t f = meta_nsrc(meta);
+          const unsigned long long *ptrs = (f + 1) <= PMAX ? B.ptr[g.k] : T.ptrs + B.poff[g.k];
+          const uint32_t n16 = g.n & ~15u;
+          const uint32_t chunk = (AREA / f) & ~15u;
+          for (uint32_t off = 0; off < n16; off += chunk) {
+            const uint32_t len = min(chunk, n16 - off);
+            if (lane == 0) {
+              bulk_wait_read_all();   // the previous chunk's store has read the area
+              mbar_expect_tx(&red_bar[dw], f * len);
+              for (uint32_t q = 0; q < f; ++q)
+                bulk_g2s(my_stage + q * chunk, reinterpret_cast<const char *>(ptrs[q]) + g.lo + off, len,
+                         &red_bar[dw]);
+            }
+            if (!mbar_wait(&red_bar[dw], rseq & 1u, limit)) {
+              if (lane == 0) raise_error(T, (unsigned long long)ERR_STALL << 32);
+              stalled = true;
+              break;
+            }
+            ++rseq;
+            for (uint32_t v = lane; v < len / 16; v += 32) {
+              uint4 acc = *reinterpret_cast<const uint4 *>(my_stage + v * 16);
+              for (uint32_t q = 1; q < f; ++q)
+                acc = add4(acc, *reinterpret_cast<const uint4 *>(my_stage + q * chunk + v * 16), meta_dtype(meta));
+              *reinterpret_cast<uint4 *>(my_stage + v * 16) = acc;
+            }
+            fence_proxy_async_smem();   // the folded chunk is read by the bulk store
+            __syncwarp();
+            if (lane == 0) {
+              bulk_s2g(reinterpret_cast<char *>(ptrs[f]) + g.lo + off, my_stage, len);
+              bulk_commit();
+            }
+          }
+          // element tail of the last segment of a step (fewer than 16 bytes)
+          if (!stalled && n16 != g.n && lane < (int)((g.n - n16) / 4)) {
+            const unsigned long long b = g.lo + n16 + 4 * lane;
+            uint32_t acc = __ldcg(reinterpret_cast<const unsigned int *>(reinterpret_cast<const char *>(ptrs[0]) + b));
+            for (uint32_t q = 1; q < f; ++q) {
+              const uint32_t v = __ldcg(reinterpret_cast<const unsigned int *>(reinterpret_cast<const char *>(ptrs[q]) + b));
+              acc = meta_dtype(meta) == HICCL_F32 ? __float_as_uint(__fadd_rn(__uint_as_float(acc), __uint_as_float(v)))
+                                                  : acc + v;
+            }
+            *reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(ptrs[f]) + b) = acc;
+          }
+        }
+        if (lane == 0) {
+          bulk_wait_all();             // every store of this item is complete
+          fence_proxy_async_global();  // and ordered before the completion warp's generic release
+        }
+        if (__any_sync(0xffffffffu, stalled)) break;
+        __syncwarp();
+      } else {
+        uint32_t k = 0;
+        for (uint32_t j = dw; j < total; j += D) {
+          while (B.pre[k + 1] <= j) ++k;
+          const unsigned long long seg = B.ent[k].seg_lo + (j - B.pre[k]);
+          const unsigned long long lo = seg * SEG_BYTES;
+          const uint32_t n = (uint32_t)min((unsigned long long)SEG_BYTES, B.nb[k] - lo);
+          const uint32_t meta = B.meta[k];
+          const uint32_t np = meta_nsrc(meta) + meta_ndst(meta);
+          const unsigned long long *ptrs = np <= PMAX ? B.ptr[k] : T.ptrs + B.poff[k];
+          if (meta_op(meta) == OP_COPY)
+            warp_copy(ptrs, meta_ndst(meta), lo, n, meta_aligned(meta), lane);
+          else
+            warp_reduce(ptrs, meta_nsrc(meta), meta_dtype(meta), lo, n, meta_aligned(meta), lane);
+        }
+      }
+      mbar_arrive(&done_bar[b]);
+    }
   }
 
   // the last CTA out re-arms the control block for the next launch
@@ -316,6 +661,35 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
       __threadfence();
       if (ld_relaxed(&T.ctl->err) == 0ull) T.ctl->epoch = epoch;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers (shared by hiccl_start and hiccl_run_static)
+// ---------------------------------------------------------------------------
+
+template <int NT>
+static cudaError_t exec_prepare(int *occ) {
+  cudaError_t e = cudaFuncSetAttribute(hiccl_exec_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       ExecShape<NT>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, hiccl_exec_kernel<NT>, NT, ExecShape<NT>::SMEM);
+}
+
+// set the kernel's shared-memory limit and return its resident CTAs per SM
+static cudaError_t exec_occupancy(int nt, int *occ) {
+  switch (nt) {
+    case 128: return exec_prepare<128>(occ);
+    case 256: return exec_prepare<256>(occ);
+    default: return exec_prepare<512>(occ);
+  }
+}
+
+static void exec_launch(int nt, unsigned grid, cudaStream_t s, const DevTable &t) {
+  switch (nt) {
+    case 128: hiccl_exec_kernel<128><<<grid, 128, ExecShape<128>::SMEM, s>>>(t); break;
+    case 256: hiccl_exec_kernel<256><<<grid, 256, ExecShape<256>::SMEM, s>>>(t); break;
+    default: hiccl_exec_kernel<512><<<grid, 512, ExecShape<512>::SMEM, s>>>(t); break;
   }
 }
 
@@ -336,6 +710,7 @@ void dev_release(hiccl_comm *c) {
   if (d->counters) cudaFree(d->counters);
   if (d->scratch) cudaFree(d->scratch);
   if (d->host_err) cudaFreeHost(d->host_err);
+  if (d->trace) cudaFree(d->trace);
   delete d;
   c->dev = nullptr;
 }
@@ -350,14 +725,9 @@ hiccl_status_t dev_upload(hiccl_comm *c) {
   if ((e = cudaGetDevice(&d->device)) != cudaSuccess) return cuda_fail(c, e, "cudaGetDevice");
   if ((e = cudaDeviceGetAttribute(&d->nsm, cudaDevAttrMultiProcessorCount, d->device)) != cudaSuccess)
     return cuda_fail(c, e, "cudaDeviceGetAttribute");
-  {
-    const void *ks[4] = {(const void *)hiccl_exec_kernel<64>, (const void *)hiccl_exec_kernel<128>,
-                         (const void *)hiccl_exec_kernel<256>, (const void *)hiccl_exec_kernel<512>};
-    for (int i = 0; i < 4; ++i) {
-      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d->occ[i], ks[i], 64 << i, 0)) != cudaSuccess)
-        return cuda_fail(c, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-      if (d->occ[i] < 1) return fail(c, HICCL_ERR_CUDA, "executor kernel cannot be resident");
-    }
+  for (int i = 1; i < 4; ++i) {
+    if ((e = exec_occupancy(64 << i, &d->occ[i])) != cudaSuccess) return cuda_fail(c, e, "executor occupancy");
+    if (d->occ[i] < 1) return fail(c, HICCL_ERR_CUDA, "executor kernel cannot be resident");
   }
 
   const size_t N = p.steps.size();
@@ -453,6 +823,14 @@ hiccl_status_t dev_upload(hiccl_comm *c) {
   t.host_err = d->host_err_dev;
   t.nitems = p.item_off.size() - 1;
   t.timeout_ns = c->timeout_ns;
+  t.trace = nullptr;
+  if (c->trace && t.nitems) {
+    if ((e = cudaMalloc(&d->trace, t.nitems * 5 * sizeof(unsigned long long))) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, HICCL_ERR_NOMEM, "trace buffer");
+    }
+    t.trace = d->trace;
+  }
   d->indeg = std::move(indeg);
   d->indeg_dev = reinterpret_cast<uint32_t *>(tb + o_indeg);
   return HICCL_OK;
@@ -475,15 +853,10 @@ hiccl_status_t hiccl_start(hiccl_comm_t c, void *stream) {
   t.timeout_ns = c->timeout_ns;
   if (t.nitems > 0) {
     const int nt = c->threads;
-    const int ti = nt == 64 ? 0 : nt == 128 ? 1 : nt == 256 ? 2 : 3;
+    const int ti = nt == 128 ? 1 : nt == 256 ? 2 : 3;
     const int per_sm = std::min(c->ctas_per_sm, d->occ[ti]);
     const unsigned long long grid = std::min<unsigned long long>(t.nitems, (unsigned long long)d->nsm * per_sm);
-    switch (nt) {
-      case 64: hiccl_exec_kernel<64><<<(unsigned)grid, 64, 0, s>>>(t); break;
-      case 128: hiccl_exec_kernel<128><<<(unsigned)grid, 128, 0, s>>>(t); break;
-      case 256: hiccl_exec_kernel<256><<<(unsigned)grid, 256, 0, s>>>(t); break;
-      default: hiccl_exec_kernel<512><<<(unsigned)grid, 512, 0, s>>>(t); break;
-    }
+    exec_launch(nt, (unsigned)grid, s, t);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "executor launch");
   }
@@ -509,8 +882,24 @@ hiccl_status_t hiccl_wait(hiccl_comm_t c) {
     const unsigned code = (unsigned)(err >> 32), step = (unsigned)(err & 0xffffffffu);
     if (code == ERR_TIMEOUT)
       return fail(c, HICCL_ERR_TIMEOUT, "dependency wait of step " + std::to_string(step) + " timed out");
+    if (code == ERR_STALL) return fail(c, HICCL_ERR_TIMEOUT, "an executor pipeline wait timed out");
     return fail(c, HICCL_ERR_CUDA, "executor error " + std::to_string(code));
   }
+  return HICCL_OK;
+}
+
+hiccl_status_t hiccl_get_trace(hiccl_comm_t c, unsigned long long *out, size_t capacity, size_t *written) {
+  if (!c || !written) return HICCL_ERR_INVALID;
+  *written = 0;
+  if (c->state != hiccl_comm::READY || !c->dev) return fail(c, HICCL_ERR_STATE, "needs an idle initialized communicator");
+  DevState *d = c->dev;
+  if (!d->trace) return fail(c, HICCL_ERR_STATE, "tracing is off (HICCL_OPT_TRACE)");
+  const size_t n = std::min<size_t>(capacity, (size_t)d->t.nitems * 5);
+  if (n && out) {
+    cudaError_t e = cudaMemcpy(out, d->trace, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "trace copy");
+  }
+  *written = n;
   return HICCL_OK;
 }
 
@@ -651,25 +1040,14 @@ extern "C" hiccl_status_t hiccl_run_static(hiccl_comm_t c, void *stream) {
   t.host_err = reinterpret_cast<unsigned long long *>(base + o_ctr + N * 16 + sizeof(DevCtl));
   t.nitems = NI;
   t.timeout_ns = c->timeout_ns;
+  t.trace = nullptr;
   if (NI > 0) {
     int nsm = 0, occ = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HICCL_ERR_CUDA;
     const int nt = c->threads;
-    cudaError_t oe;
-    switch (nt) {
-      case 64: oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hiccl_exec_kernel<64>, 64, 0); break;
-      case 128: oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hiccl_exec_kernel<128>, 128, 0); break;
-      case 256: oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hiccl_exec_kernel<256>, 256, 0); break;
-      default: oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hiccl_exec_kernel<512>, 512, 0); break;
-    }
-    if (oe != cudaSuccess || occ < 1) return HICCL_ERR_CUDA;
+    if (exec_occupancy(nt, &occ) != cudaSuccess || occ < 1) return HICCL_ERR_CUDA;
     const unsigned grid = (unsigned)std::min<unsigned long long>(NI, (unsigned long long)nsm * std::min(c->ctas_per_sm, occ));
-    switch (nt) {
-      case 64: hiccl_exec_kernel<64><<<grid, 64, 0, s>>>(t); break;
-      case 128: hiccl_exec_kernel<128><<<grid, 128, 0, s>>>(t); break;
-      case 256: hiccl_exec_kernel<256><<<grid, 256, 0, s>>>(t); break;
-      default: hiccl_exec_kernel<512><<<grid, 512, 0, s>>>(t); break;
-    }
+    exec_launch(nt, grid, s, t);
     if (cudaGetLastError() != cudaSuccess) return HICCL_ERR_CUDA;
   }
   if (cudaStreamSynchronize(s) != cudaSuccess) return HICCL_ERR_CUDA;

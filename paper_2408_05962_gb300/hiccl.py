@@ -25,7 +25,7 @@ OK, ERR_INVALID, ERR_STATE, ERR_RACE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSU
 STATUS_NAMES = ["OK", "INVALID", "STATE", "RACE", "NOMEM", "CUDA", "TIMEOUT", "UNSUPPORTED", "TOO_LARGE"]
 STATIC_ARENA_BYTES = 16 << 20
 
-OPT_TIMEOUT_NS, OPT_CTAS_PER_SM, OPT_ITEM_BYTES, OPT_ORDER, OPT_THREADS = range(5)
+OPT_TIMEOUT_NS, OPT_CTAS_PER_SM, OPT_ITEM_BYTES, OPT_ORDER, OPT_THREADS, OPT_TRACE, OPT_SLOT_ITEMS = range(7)
 
 
 class HicclError(RuntimeError):
@@ -82,6 +82,8 @@ _SIGS = {
     "hiccl_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong]),
     "hiccl_debug_withhold": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_int]),
     "hiccl_run_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hiccl_get_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_size_t,
+                                       ctypes.POINTER(ctypes.c_size_t)]),
     "hiccl_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "hiccl_destroy": (None, [ctypes.c_void_p]),
 }
@@ -238,6 +240,17 @@ def hiccl_run_static(comm, stream=None):
         raise HicclError(st, "hiccl_run_static")
 
 
+def hiccl_get_trace(comm, nitems: int):
+    """Per-item executor timestamps of the last start: a list of
+    (staging began, handed to data warps, data done, successors released, SM)."""
+    cap = 5 * int(nitems)
+    buf = (ctypes.c_ulonglong * max(cap, 1))()
+    n = ctypes.c_size_t()
+    _check(comm, lib().hiccl_get_trace(comm, buf, cap, ctypes.byref(n)))
+    v = [int(x) for x in buf[:n.value]]
+    return [tuple(v[i:i + 5]) for i in range(0, len(v), 5)]
+
+
 def hiccl_last_error(comm) -> str:
     return lib().hiccl_last_error(comm).decode()
 
@@ -295,6 +308,9 @@ class Comm:
 
     def steps(self):
         return [self.step(i) for i in range(self.plan_info()["steps"])]
+
+    def trace(self):
+        return hiccl_get_trace(self.handle, self.plan_info()["items"])
 
     def run_static(self, stream=None):
         hiccl_run_static(self.handle, stream)
