@@ -12,7 +12,7 @@ writes once), summed over the seven collectives and divided by their summed
 kernel time, with the fraction of the measured HBM bandwidth; per-collective
 GB/s and the paper-style d*p/t are reported beside it.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload seven|allreduce64]
 Under torchrun each rank runs an independent replica on its own GPU
 ("replicas only": the virtual-rank path does not shard across devices).
 """
@@ -42,12 +42,27 @@ KERNEL_SRC = os.path.join(ROOT, "paper_2408_05962_gb300", "csrc", "hiccl_runtime
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "executor_traffic_seven_p64.txt")
 
 
-def workload_config(extra=None):
-    cfg = {"workload": "seven collectives, P=64 virtual ranks, hierarchy {4,4,4}, 4 MiB fp32 per rank, "
-                       "stripe 4, pipeline 8",
-           "ranks": P, "hierarchy": HIER, "stripe": STRIPE, "pipeline": PIPE,
-           "bytes_per_rank": BYTES_PER_RANK, "collectives": list(KINDS),
-           "l2": "working set of one step ~3.5 GB > 129 MB L2; no flush between steps"}
+# the two single-GPU workloads: the seven collectives (the headline), and the
+# large All-reduce of 64 MiB per rank used for the >= 16 MiB-per-rank bandwidth
+WORKLOADS = {
+    "seven": {"ranks": 64, "hierarchy": [4, 4, 4], "stripe": 4, "pipeline": 8, "bytes_per_rank": 4 << 20,
+              "kinds": KINDS, "data": "uniform[-1,1] fp32, seed 0",
+              "name": "seven collectives, P=64 virtual ranks, hierarchy {4,4,4}, 4 MiB fp32 per rank, "
+                      "stripe 4, pipeline 8",
+              "l2": "working set of one step ~3.5 GB > 129 MB L2; no flush between steps"},
+    "allreduce64": {"ranks": 32, "hierarchy": [4, 8], "stripe": 1, "pipeline": 4, "bytes_per_rank": 64 << 20,
+                    "kinds": ("allreduce",), "data": "N(0,1) * 10**U(-3,3) per rank fp32, seed 0",
+                    "name": "All-reduce (Listing 2), P=32 virtual ranks, hierarchy {4,8}, 64 MiB fp32 per rank, "
+                            "stripe 1, pipeline 4",
+                    "l2": "working set 4 GiB > 129 MB L2; no flush between steps"},
+}
+
+
+def workload_config(extra=None, w="seven"):
+    W = WORKLOADS[w]
+    cfg = {"workload": W["name"], "ranks": W["ranks"], "hierarchy": W["hierarchy"], "stripe": W["stripe"],
+           "pipeline": W["pipeline"], "bytes_per_rank": W["bytes_per_rank"], "collectives": list(W["kinds"]),
+           "inputs": W["data"], "l2": W["l2"]}
     if extra:
         cfg.update(extra)
     return cfg
@@ -279,15 +294,21 @@ def run_ours(args):
     from paper_2408_05962_gb300 import hiccl as H
     from synth import uniform_ranks
 
-    d = BYTES_PER_RANK // 4 // P
-    x = torch.from_numpy(uniform_ranks(P, d * P, seed=0))
+    W = WORKLOADS[args.workload]
+    Pw, hier, stripe, pipe = W["ranks"], W["hierarchy"], W["stripe"], W["pipeline"]
+    d = W["bytes_per_rank"] // 4 // Pw
+    if args.workload == "seven":
+        x = torch.from_numpy(uniform_ranks(Pw, d * Pw, seed=0))
+    else:
+        from synth import scaled_normal_ranks
+        x = torch.from_numpy(scaled_normal_ranks(Pw, d * Pw, seed=0))
     comms, bufs, nbytes, pbytes = {}, {}, {}, {}
-    kinds = tuple(args.kinds.split(",")) if args.kinds else KINDS
+    kinds = tuple(args.kinds.split(",")) if args.kinds else W["kinds"]
     for kind in kinds:
-        b = C.Buffers(kind, P, d, torch.float32, device)
+        b = C.Buffers(kind, Pw, d, torch.float32, device)
         b.send.copy_(x[:, :b.ls].to(device))
         b.recv.zero_()
-        comm = H.Comm(P, "f32")
+        comm = H.Comm(Pw, "f32")
         if args.item_bytes:
             comm.set_option(H.OPT_ITEM_BYTES, args.item_bytes)
         if args.order is not None:
@@ -297,10 +318,10 @@ def run_ours(args):
         if args.threads:
             comm.set_option(H.OPT_THREADS, args.threads)
         C.compose(comm, kind, d, b.send_ptrs(), b.recv_ptrs())
-        comm.init(HIER, STRIPE, PIPE)
+        comm.init(hier, stripe, pipe)
         rd, wr = comm.hbm_bytes()
         comms[kind], bufs[kind], nbytes[kind] = comm, b, rd + wr
-        pbytes[kind] = d * 4 * P                       # the paper's d*p per collective
+        pbytes[kind] = d * 4 * Pw                      # the paper's d*p per collective
     stream = torch.cuda.current_stream(device)
     step_bytes = sum(nbytes.values())
 
@@ -369,7 +390,7 @@ def run_ours(args):
     eb, es = aggregate(step_bytes * e2e_steps, e2e_s, device)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "seven":
         b, t, desc = oracle_sample(args.cpu_budget)
         cpu = {"value": b / t / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc}
 
@@ -384,7 +405,7 @@ def run_ours(args):
         "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": statistics.mean(step_ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": workload_config({"parallelism": f"replicas{world}"}),
+        "data": "synthetic", "config": workload_config({"parallelism": f"replicas{world}"}, args.workload),
         "roofline": {"bound": "hbm", "achieved": gbs / world, "peak": peak, "unit": "GB/s",
                      "frac": gbs / world / peak, "peak_source": peak_kind,
                      "traffic": traffic, "kernel": "hiccl_exec_kernel"},
@@ -410,6 +431,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--item-bytes", type=int, default=0, help="executor work-item size (0: library default)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="executor CTAs per SM (0: library default)")
+    ap.add_argument("--workload", default="seven", choices=sorted(WORKLOADS))
     ap.add_argument("--kinds", default="", help="comma-separated subset of the seven collectives (profiling)")
     ap.add_argument("--threads", type=int, default=0, help="executor threads per CTA (0: library default)")
     ap.add_argument("--order", type=int, default=None, help="work order: 0 pipeline slots, 1 stage depth")
