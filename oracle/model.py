@@ -20,15 +20,19 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+from .lowprec import FP8_BLOCK_DTYPE
+
+# storage of one counted unit: a value, or for FP8 a 144-byte block of 128
+# values and their scale (counts of FP8 programs are in blocks)
 DTYPES = {
     "f32": np.dtype(np.float32),
     "i32": np.dtype(np.int32),
     "bf16": np.dtype(np.uint16),     # bit patterns; see lowprec
-    "fp8": np.dtype(np.uint8),       # e4m3 bit patterns; see lowprec
+    "fp8": FP8_BLOCK_DTYPE,          # 128 e4m3 codes + binary32 scale; see lowprec
 }
 
-# elements per 16-byte quantum; FP8 pieces also align to its 128-element scale blocks
-QUANTUM = {"f32": 4, "i32": 4, "bf16": 8, "fp8": 128}
+# units per piece-boundary quantum: 16 bytes of values, one FP8 block
+QUANTUM = {"f32": 4, "i32": 4, "bf16": 8, "fp8": 1}
 
 
 @dataclass(frozen=True)

@@ -5,7 +5,8 @@ Readings (the paper is silent on these; each is stated once here):
 * Sum order.  A reduction's result is the *hierarchical nested fold*: a rank
   contributes its own values; a level-l group contributes the left fold, in
   the payload's arithmetic (FP32 round-to-nearest-even, no fused
-  multiply-add; int32 wraps), of the contributions of its non-empty
+  multiply-add; int32 wraps; BF16 and FP8 decoded to FP32, folded, and the
+  group's result encoded once), of the contributions of its non-empty
   subgroups in ascending index order.  It depends only on the hierarchy and
   the leaf set -- not on the root, striping, pipeline depth or
   representatives -- so a factorized schedule must reproduce it exactly.
@@ -21,6 +22,7 @@ from __future__ import annotations
 import numpy as np
 
 from .hierarchy import check, group_sizes
+from .lowprec import from_acc, to_acc
 from .model import Multicast, Program, Reduction
 
 
@@ -28,34 +30,46 @@ from .model import Multicast, Program, Reduction
 # the fixed-order sum
 # ---------------------------------------------------------------------------
 
-def nested_fold(values: dict, hierarchy, add=None) -> np.ndarray:
+def nested_fold(values: dict, hierarchy, dtype: str | None = None) -> np.ndarray:
     """Hierarchical nested fold of ``values`` (rank -> array) over ``hierarchy``.
 
-    S(rank r) = values[r]; S(group) = left fold over the S(subgroup) of the
-    subgroups that hold at least one contributing rank, in ascending order.
-    ``add`` combines two partials (default: NumPy's elementwise add in the
-    arrays' own dtype, i.e. IEEE RNE for float32 and wrapping for int32).
+    S(rank r) = values[r]; S(group) = the left fold over the S(subgroup) of
+    the subgroups that hold at least one contributing rank, in ascending
+    order.  For f32 / i32 (and ``dtype`` None) the fold adds in the arrays'
+    own dtype (IEEE RNE for float32, wrapping for int32).  For the reduced
+    precision payloads ("bf16", "fp8") the subgroup values are decoded to
+    binary32, folded with binary32 adds and the group's result encoded once
+    (lowprec); a group with a single contributing subgroup passes its value
+    through unchanged.
     """
     if not values:
         raise ValueError("empty leaf set")
     h = list(hierarchy)
     G = group_sizes(h)
     ranks = sorted(values)
-    add = add or (lambda a, b: a + b)
+    low = dtype in ("bf16", "fp8")
 
     def S(level: int, base: int, members: list):
         if level == len(h):
             return values[base]
         sub = G[level + 1]
-        acc = None
+        parts = []
         for q in range(h[level]):
             lo = base + q * sub
             inside = [r for r in members if lo <= r < lo + sub]
-            if not inside:
-                continue
-            part = S(level + 1, lo, inside)
-            acc = part.copy() if acc is None else add(acc, part)
-        return acc
+            if inside:
+                parts.append(S(level + 1, lo, inside))
+        if len(parts) == 1:
+            return parts[0].copy()
+        if not low:
+            acc = parts[0].copy()
+            for p in parts[1:]:
+                acc = acc + p
+            return acc
+        acc = to_acc(parts[0], dtype).copy()
+        for p in parts[1:]:
+            acc = (acc + to_acc(p, dtype)).astype(np.float32)
+        return from_acc(acc, dtype)
 
     return S(0, 0, ranks)
 
@@ -83,16 +97,16 @@ def apply_multicast(p: Multicast, mem: dict) -> None:
         _view(mem, p.dsts[j], p.count)[...] = src
 
 
-def apply_reduction(p: Reduction, mem: dict, hierarchy, add=None) -> None:
+def apply_reduction(p: Reduction, mem: dict, hierarchy, dtype: str | None = None) -> None:
     """R(i, j, d, sum): the root's destination receives the fixed-order sum of
     the leaves' d elements (Sec. 3.1)."""
     if p.count == 0:
         return
     vals = {i: _view(mem, p.srcs[i], p.count).copy() for i in p.leaves}
-    _view(mem, p.dst, p.count)[...] = nested_fold(vals, hierarchy, add)
+    _view(mem, p.dst, p.count)[...] = nested_fold(vals, hierarchy, dtype)
 
 
-def run_program(prog: Program, mem: dict, hierarchy, add=None) -> dict:
+def run_program(prog: Program, mem: dict, hierarchy) -> dict:
     """Execute the program's epochs in order; inside an epoch the (race-free)
     primitives are applied in registration order, which Sec. 3.2 makes
     irrelevant."""
@@ -102,7 +116,7 @@ def run_program(prog: Program, mem: dict, hierarchy, add=None) -> dict:
             if isinstance(p, Multicast):
                 apply_multicast(p, mem)
             else:
-                apply_reduction(p, mem, hierarchy, add)
+                apply_reduction(p, mem, hierarchy, prog.dtype)
     return mem
 
 
@@ -167,10 +181,10 @@ def def_broadcast(x, root):
     return [x[root].copy() for _ in range(len(x))]
 
 
-def def_reduce(x, root, hierarchy):
+def def_reduce(x, root, hierarchy, dtype=None):
     """Only the root's result is defined; other ranks' y are untouched (None)."""
     y = [None] * len(x)
-    y[root] = nested_fold({r: x[r] for r in range(len(x))}, hierarchy)
+    y[root] = nested_fold({r: x[r] for r in range(len(x))}, hierarchy, dtype)
     return y
 
 
@@ -178,13 +192,13 @@ def def_allgather(x):
     return [np.concatenate(x) for _ in range(len(x))]
 
 
-def def_reducescatter(x, hierarchy):
+def def_reducescatter(x, hierarchy, dtype=None):
     P = len(x)
-    return [nested_fold({r: _chunks(x[r], P)[j] for r in range(P)}, hierarchy) for j in range(P)]
+    return [nested_fold({r: _chunks(x[r], P)[j] for r in range(P)}, hierarchy, dtype) for j in range(P)]
 
 
-def def_allreduce(x, hierarchy):
-    s = nested_fold({r: x[r] for r in range(len(x))}, hierarchy)
+def def_allreduce(x, hierarchy, dtype=None):
+    s = nested_fold({r: x[r] for r in range(len(x))}, hierarchy, dtype)
     return [s.copy() for _ in range(len(x))]
 
 

@@ -9,6 +9,7 @@ from __future__ import annotations
 import numpy as np
 
 from .factorize import Plan
+from .lowprec import from_acc, to_acc
 from .model import DTYPES
 
 
@@ -16,16 +17,23 @@ def _view(mem, ref, n):
     return mem[ref.key][ref.off:ref.off + n]
 
 
-def execute_op(op, mem: dict, add=None) -> None:
-    add = add or (lambda a, b: a + b)
+def execute_op(op, mem: dict, dtype: str | None = None) -> None:
+    """Run one operation.  A reduce folds its inputs in order; reduced-precision
+    payloads are decoded to binary32, folded, and encoded once (lowprec)."""
     if op.kind == "copy":
         src = _view(mem, op.srcs[0][1], op.n).copy()
         for _, d in op.dsts:
             _view(mem, d, op.n)[...] = src
         return
+    if dtype in ("bf16", "fp8"):
+        acc = to_acc(_view(mem, op.srcs[0][1], op.n), dtype).copy()
+        for _, s in op.srcs[1:]:
+            acc = (acc + to_acc(_view(mem, s, op.n), dtype)).astype(np.float32)
+        _view(mem, op.dsts[0][1], op.n)[...] = from_acc(acc, dtype)
+        return
     acc = _view(mem, op.srcs[0][1], op.n).copy()
     for _, s in op.srcs[1:]:
-        acc = add(acc, _view(mem, s, op.n))
+        acc = acc + _view(mem, s, op.n)
     _view(mem, op.dsts[0][1], op.n)[...] = acc
 
 
@@ -55,12 +63,12 @@ def topo_order(plan: Plan, seed: int | None):
     return order
 
 
-def simulate(plan: Plan, mem: dict, order_seed: int | None = None, add=None) -> dict:
+def simulate(plan: Plan, mem: dict, order_seed: int | None = None) -> dict:
     """Run every op of ``plan`` on ``mem`` (modified in place; relay buffers
     are added under their scratch keys)."""
     dt = DTYPES[plan.dtype]
     for k, n in plan.scratch.items():
         mem[k] = np.zeros(n, dtype=dt)
     for i in topo_order(plan, order_seed):
-        execute_op(plan.ops[i], mem, add)
+        execute_op(plan.ops[i], mem, plan.dtype)
     return mem

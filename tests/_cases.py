@@ -37,14 +37,18 @@ def random_program(P: int, seed: int, dtype: str = "f32", chunks: int = 3, max_n
 
 
 def fill(prog: Program, seed: int) -> dict:
-    """Random contents for every buffer of ``prog`` (NumPy)."""
+    """Random contents for every buffer of ``prog`` (NumPy): uniform[-1, 1]
+    values (encoded for BF16 / FP8 payloads), full-range int32."""
+    from oracle.lowprec import encode
     mem = prog.allocate()
     g = np.random.Generator(np.random.PCG64(seed))
     for k, v in mem.items():
-        if v.dtype == np.float32:
+        if prog.dtype == "f32":
             v[...] = g.uniform(-1, 1, size=v.shape).astype(np.float32)
-        elif v.dtype == np.int32:
+        elif prog.dtype == "i32":
             v[...] = g.integers(-2**31, 2**31 - 1, size=v.shape, endpoint=True, dtype=np.int64)
-        else:
-            v[...] = g.integers(0, np.iinfo(v.dtype).max, size=v.shape, endpoint=True).astype(v.dtype)
+        elif prog.dtype == "bf16":
+            v[...] = encode(g.uniform(-1, 1, size=v.shape).astype(np.float32), "bf16")
+        else:   # fp8 blocks of 128 values
+            v[...] = encode(g.uniform(-1, 1, size=v.shape[0] * 128).astype(np.float32), "fp8")
     return mem
