@@ -23,7 +23,7 @@ alltoall             d*P         d*P
 """
 from __future__ import annotations
 
-from .hiccl import ESIZE, Comm
+from .hiccl import FP8_BLOCK_BYTES, Comm, nbytes
 
 SEND_RECV = {
     "broadcast": (1, 1), "reduce": (1, 1), "allgather": (0, 1), "gather": (0, 1),
@@ -39,15 +39,21 @@ def buffer_lengths(kind: str, P: int, d: int) -> tuple:
 
 
 class Buffers:
-    """P send rows and P recv rows in two device tensors (row r = rank r)."""
+    """P send rows and P recv rows in two device tensors (row r = rank r).
+    For FP8 payloads pass ``torch.uint8``: rows then hold the 144-byte blocks
+    of ``ls`` / ``lr`` values."""
 
     def __init__(self, kind: str, P: int, d: int, torch_dtype, device="cuda", pad_elems: int = 0):
         import torch
         self.kind, self.P, self.d = kind, P, d
         ls, lr = buffer_lengths(kind, P, d)
-        self.send = torch.empty((P, ls + pad_elems), dtype=torch_dtype, device=device)
-        self.recv = torch.empty((P, lr + pad_elems), dtype=torch_dtype, device=device)
         self.ls, self.lr = ls, lr
+        if torch_dtype == torch.uint8:           # FP8 blocks
+            self.send = torch.empty((P, ls // 128 * FP8_BLOCK_BYTES + pad_elems), dtype=torch_dtype, device=device)
+            self.recv = torch.empty((P, lr // 128 * FP8_BLOCK_BYTES + pad_elems), dtype=torch_dtype, device=device)
+        else:
+            self.send = torch.empty((P, ls + pad_elems), dtype=torch_dtype, device=device)
+            self.recv = torch.empty((P, lr + pad_elems), dtype=torch_dtype, device=device)
 
     def send_ptrs(self):
         return [int(self.send[r].data_ptr()) for r in range(self.P)]
@@ -56,8 +62,9 @@ class Buffers:
         return [int(self.recv[r].data_ptr()) for r in range(self.P)]
 
 
-def _off(ptrs, k_elems, esize):
-    return [p + k_elems * esize if p else 0 for p in ptrs]
+def _off(ptrs, k_elems, dtype):
+    b = nbytes(dtype, k_elems)
+    return [p + b if p else 0 for p in ptrs]
 
 
 def _one(P, r, addr):
@@ -68,8 +75,12 @@ def _one(P, r, addr):
 
 def compose(comm: Comm, kind: str, d: int, send, recv, root: int = 0) -> None:
     """Register collective ``kind`` over chunk length ``d`` on ``comm``."""
-    P, e = comm.P, ESIZE[comm.dtype]
+    P, e = comm.P, comm.dtype
     ranks = list(range(P))
+
+    def at(base, k_elems):                        # address of element k of a buffer
+        return base + nbytes(e, k_elems)
+
     if kind == "broadcast":                       # M(i, U, dp)
         comm.add_multicast(send, recv, d * P, root, ranks)
     elif kind == "reduce":                        # R(U, j, dp)
@@ -85,25 +96,25 @@ def compose(comm: Comm, kind: str, d: int, send, recv, root: int = 0) -> None:
             comm.add_reduction(send, recv, d * P, ranks, j)
     elif kind == "scatter":                       # sum_j R(i, j, d)
         for j in ranks:
-            comm.add_reduction(_one(P, root, send[root] + j * d * e), recv, d, [root], j)
+            comm.add_reduction(_one(P, root, at(send[root], j * d)), recv, d, [root], j)
     elif kind == "gather":                        # sum_i M(i, j, d)
         for i in ranks:
-            comm.add_multicast(send, _one(P, root, recv[root] + i * d * e), d, i, [root])
+            comm.add_multicast(send, _one(P, root, at(recv[root], i * d)), d, i, [root])
     elif kind == "alltoall":                      # sum_i sum_j M(i, j, d)
         for i in ranks:
             for j in ranks:
-                comm.add_multicast(_one(P, i, send[i] + j * d * e), _one(P, j, recv[j] + i * d * e),
+                comm.add_multicast(_one(P, i, at(send[i], j * d)), _one(P, j, at(recv[j], i * d)),
                                    d, i, [j])
     elif kind == "allreduce":                     # Listing 2
         for j in ranks:
-            comm.add_reduction(_off(send, j * d, e), _one(P, j, recv[j] + j * d * e), d, ranks, j)
+            comm.add_reduction(_off(send, j * d, e), _one(P, j, at(recv[j], j * d)), d, ranks, j)
         comm.add_fence()
         for i in ranks:
             others = [r for r in ranks if r != i]
             comm.add_multicast(_off(recv, i * d, e), _off(recv, i * d, e), d, i, others)
     elif kind == "broadcast_via_ag_scatter":      # All-gather . Scatter
         for j in ranks:
-            comm.add_reduction(_one(P, root, send[root] + j * d * e), _one(P, j, recv[j] + j * d * e),
+            comm.add_reduction(_one(P, root, at(send[root], j * d)), _one(P, j, at(recv[j], j * d)),
                                d, [root], j)
         comm.add_fence()
         for i in ranks:
@@ -111,15 +122,15 @@ def compose(comm: Comm, kind: str, d: int, send, recv, root: int = 0) -> None:
             comm.add_multicast(_off(recv, i * d, e), _off(recv, i * d, e), d, i, others)
     elif kind == "reduce_via_gather_rs":          # Gather . Reduce-scatter
         for j in ranks:
-            comm.add_reduction(_off(send, j * d, e), _one(P, j, recv[j] + j * d * e), d, ranks, j)
+            comm.add_reduction(_off(send, j * d, e), _one(P, j, at(recv[j], j * d)), d, ranks, j)
         comm.add_fence()
         for j in ranks:
             if j != root:
-                comm.add_multicast(_one(P, j, recv[j] + j * d * e), _one(P, root, recv[root] + j * d * e),
+                comm.add_multicast(_one(P, j, at(recv[j], j * d)), _one(P, root, at(recv[root], j * d)),
                                    d, j, [root])
     elif kind == "allgather_via_bcast_gather":    # Broadcast . Gather
         for i in ranks:
-            comm.add_multicast(send, _one(P, root, recv[root] + i * d * e), d, i, [root])
+            comm.add_multicast(send, _one(P, root, at(recv[root], i * d)), d, i, [root])
         comm.add_fence()
         others = [r for r in ranks if r != root]
         comm.add_multicast(recv, recv, d * P, root, others)

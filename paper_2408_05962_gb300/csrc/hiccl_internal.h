@@ -20,8 +20,13 @@ namespace hiccl {
 // device-side layout of an uploaded plan
 // ---------------------------------------------------------------------------
 
-// A warp moves one segment of a step at a time: SEG_BYTES of every operand.
+// A warp moves one segment of a step at a time: at most SEG_BYTES of every
+// operand (the staging slot size).  FP8 steps use segments of whole 144-byte
+// blocks.
 constexpr uint32_t SEG_BYTES = 4096;
+constexpr uint32_t FP8_BLOCK_ELEMS = 128;
+constexpr uint32_t FP8_BLOCK_BYTES = 144;   // 128 e4m3 codes, binary32 scale, 12 zero bytes
+HICCL_HD inline uint32_t seg_bytes_of(uint32_t dtype) { return dtype == 3u ? 28u * FP8_BLOCK_BYTES : SEG_BYTES; }
 constexpr uint32_t MAX_ENTRIES_PER_ITEM = 64;
 constexpr uint32_t MAX_FANIN = 1024;    // reduce inputs / copy destinations per step
 constexpr uint32_t TMA_MAX_FANIN = 8;   // reduce inputs folded in shared memory
@@ -71,6 +76,7 @@ struct DevTable {
   unsigned long long *host_err;       // mapped host word mirroring ctl->err
   unsigned long long nitems;
   unsigned long long timeout_ns;
+  unsigned long long seg;             // segment bytes of this plan
   unsigned long long *trace;          // [nitems][4] timestamps, or null (see hiccl_get_trace)
 };
 
@@ -115,6 +121,7 @@ struct DevState;   // defined by the runtime
 struct Plan {
   std::vector<int> hierarchy;
   int stripe = 1, pipeline = 1;
+  unsigned long long seg = SEG_BYTES;      // segment bytes (seg_bytes_of(dtype))
   std::vector<HStep> steps;                // in execution (slot) order
   std::vector<Loc> locs;
   std::vector<uint32_t> pred_off, preds;   // CSR of predecessors (by new index)

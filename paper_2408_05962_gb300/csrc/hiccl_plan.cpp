@@ -37,25 +37,38 @@ hiccl_status_t fail(hiccl_comm *c, hiccl_status_t st, const std::string &msg) {
   return st;
 }
 
+// bytes of one counted unit: a value, or for FP8 a block of 128 values with
+// its scale (FP8 counts are converted from values to blocks at registration)
 static int esize_of(hiccl_dtype_t dt) {
   switch (dt) {
     case HICCL_F32: return 4;
     case HICCL_I32: return 4;
     case HICCL_BF16: return 2;
-    case HICCL_FP8E4M3: return 1;
+    case HICCL_FP8E4M3: return (int)FP8_BLOCK_BYTES;
   }
   return 0;
 }
 
-// elements per piece-boundary quantum: 16 bytes, or the 128-element FP8 scale block
+// units per piece-boundary quantum: 16 bytes of values, one FP8 block
 static unsigned long long quantum_of(hiccl_dtype_t dt) {
   switch (dt) {
     case HICCL_F32: return 4;
     case HICCL_I32: return 4;
     case HICCL_BF16: return 8;
-    case HICCL_FP8E4M3: return 128;
+    case HICCL_FP8E4M3: return 1;
   }
   return 1;
+}
+
+// FP8 payloads are counted in values by the caller and in blocks inside
+static bool to_units(hiccl_comm *c, size_t count, size_t &units) {
+  if (c->dtype != HICCL_FP8E4M3) {
+    units = count;
+    return true;
+  }
+  if (count % FP8_BLOCK_ELEMS) return false;
+  units = count / FP8_BLOCK_ELEMS;
+  return true;
 }
 
 namespace {
@@ -542,15 +555,17 @@ static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevel
   // MAX_ENTRIES_PER_ITEM steps.  A slot with little data gets small items, so
   // that it still spreads over about slot_items CTAs: the early levels of a
   // tree are short but lie on the critical path.
+  const unsigned long long SEGB = seg_bytes_of((uint32_t)c->dtype);
+  plan.seg = SEGB;
   std::vector<unsigned long long> slot_bytes(N ? plan.steps.back().slot + 1 : 0, 0);
   for (const HStep &st : plan.steps) slot_bytes[st.slot] += st.nbytes;
   auto slot_cap = [&](unsigned long long sl) {
     unsigned long long v = (slot_bytes[sl] + c->slot_items - 1) / c->slot_items;
-    v = (v + SEG_BYTES - 1) / SEG_BYTES * SEG_BYTES;
-    return std::min<unsigned long long>(std::max<unsigned long long>(v, SEG_BYTES),
-                                        std::max<unsigned long long>(SEG_BYTES, c->item_bytes));
+    v = (v + SEGB - 1) / SEGB * SEGB;
+    return std::min<unsigned long long>(std::max<unsigned long long>(v, SEGB),
+                                        std::max<unsigned long long>(SEGB, c->item_bytes));
   };
-  unsigned long long cap = SEG_BYTES;
+  unsigned long long cap = SEGB;
   plan.nent.assign(N, 0);
   plan.item_off.push_back(0);
   unsigned long long cur_segs = 0;   // bytes in the open item
@@ -568,16 +583,16 @@ static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevel
       cur_class = klass[order[k]];
       cap = slot_cap(st.slot);
     }
-    unsigned long long nseg = (st.nbytes + SEG_BYTES - 1) / SEG_BYTES;
+    unsigned long long nseg = (st.nbytes + SEGB - 1) / SEGB;
     if (nseg > 0xFFFFFFFFull) return fail(c, HICCL_ERR_UNSUPPORTED, "step too large");
     unsigned long long done = 0;
     while (done < nseg) {
       // whole segments that fit the open item (at least one)
-      const unsigned long long room = cap > cur_segs ? (cap - cur_segs) / SEG_BYTES : 0;
+      const unsigned long long room = cap > cur_segs ? (cap - cur_segs) / SEGB : 0;
       unsigned long long take = std::max<unsigned long long>(1, std::min(nseg - done, room));
       plan.entries.push_back(DevEntry{(uint32_t)k, (uint32_t)done, (uint32_t)(done + take), 0});
       plan.nent[k]++;
-      const unsigned long long bytes = std::min(st.nbytes, (done + take) * SEG_BYTES) - done * SEG_BYTES;
+      const unsigned long long bytes = std::min(st.nbytes, (done + take) * SEGB) - done * SEGB;
       done += take;
       cur_segs += bytes;
       if (cur_segs >= cap || plan.entries.size() - plan.item_off.back() >= MAX_ENTRIES_PER_ITEM)
@@ -651,7 +666,9 @@ static hiccl_status_t check_leaves(hiccl_comm *c, const int *leaves, int nleaves
   return HICCL_OK;
 }
 
-static bool aligned_elem(const hiccl_comm *c, unsigned long long a) { return a % c->esize == 0; }
+static bool aligned_elem(const hiccl_comm *c, unsigned long long a) {
+  return c->dtype == HICCL_FP8E4M3 ? a % 16 == 0 : a % c->esize == 0;
+}
 
 hiccl_status_t hiccl_add_multicast(hiccl_comm_t c, const void *const *send, void *const *recv,
                                    size_t count, int root, const int *leaves, int nleaves) {
@@ -662,7 +679,7 @@ hiccl_status_t hiccl_add_multicast(hiccl_comm_t c, const void *const *send, void
   Prim p;
   p.kind = 0;
   p.root = root;
-  p.count = count;
+  if (!to_units(c, count, p.count)) return fail(c, HICCL_ERR_INVALID, "FP8 counts must be multiples of 128");
   p.epoch = c->epochs - 1;
   hiccl_status_t st = check_leaves(c, leaves, nleaves, p.leaves, true);
   if (st != HICCL_OK) return st;
@@ -678,7 +695,7 @@ hiccl_status_t hiccl_add_multicast(hiccl_comm_t c, const void *const *send, void
     if (!aligned_elem(c, p.send[root])) return fail(c, HICCL_ERR_INVALID, "misaligned send buffer");
     for (int j : p.leaves)
       if (!aligned_elem(c, p.recv[j])) return fail(c, HICCL_ERR_INVALID, "misaligned recv buffer");
-    if ((unsigned long long)count > (~0ull) / 8) return fail(c, HICCL_ERR_INVALID, "count too large");
+    if ((unsigned long long)p.count > (~0ull) / 256) return fail(c, HICCL_ERR_INVALID, "count too large");
   }
   c->prims.push_back(std::move(p));
   return HICCL_OK;
@@ -691,13 +708,11 @@ hiccl_status_t hiccl_add_reduction(hiccl_comm_t c, const void *const *send, void
   if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "add after init");
   if (!send || !recv) return fail(c, HICCL_ERR_INVALID, "null pointer array");
   if (op != HICCL_SUM) return fail(c, HICCL_ERR_UNSUPPORTED, "only HICCL_SUM is implemented");
-  if (c->dtype != HICCL_F32 && c->dtype != HICCL_I32)
-    return fail(c, HICCL_ERR_UNSUPPORTED, "reductions of this dtype are not implemented");
   if (root < 0 || root >= c->P) return fail(c, HICCL_ERR_INVALID, "root out of range");
   Prim p;
   p.kind = 1;
   p.root = root;
-  p.count = count;
+  if (!to_units(c, count, p.count)) return fail(c, HICCL_ERR_INVALID, "FP8 counts must be multiples of 128");
   p.epoch = c->epochs - 1;
   hiccl_status_t st = check_leaves(c, leaves, nleaves, p.leaves, false);
   if (st != HICCL_OK) return st;
@@ -712,7 +727,7 @@ hiccl_status_t hiccl_add_reduction(hiccl_comm_t c, const void *const *send, void
     if (!aligned_elem(c, p.recv[root])) return fail(c, HICCL_ERR_INVALID, "misaligned recv buffer");
     for (int j : p.leaves)
       if (!aligned_elem(c, p.send[j])) return fail(c, HICCL_ERR_INVALID, "misaligned send buffer");
-    if ((unsigned long long)count > (~0ull) / 8) return fail(c, HICCL_ERR_INVALID, "count too large");
+    if ((unsigned long long)p.count > (~0ull) / 256) return fail(c, HICCL_ERR_INVALID, "count too large");
   }
   c->prims.push_back(std::move(p));
   return HICCL_OK;

@@ -113,6 +113,110 @@ __device__ __forceinline__ uint4 add4(uint4 a, uint4 b, uint32_t dt) {
   return a;
 }
 
+// ---- reduced-precision payloads -------------------------------------------
+// BF16: the upper half of a binary32; rounding to nearest even by cvt.rn.
+__device__ __forceinline__ uint32_t f32_to_bf16_rn(float x) {
+  unsigned short h;
+  asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(x));
+  return h;
+}
+// FP8 e4m3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits, no
+// infinities, S.1111.111 = NaN): exact decode from the bit fields
+__device__ __forceinline__ float e4m3_to_f32(uint32_t c) {
+  const uint32_t e = (c >> 3) & 15u, m = c & 7u;
+  float v = e ? __uint_as_float(((e + 120u) << 23) | (m << 20))   // (1 + m/8) * 2^(e-7)
+              : (float)m * 0.001953125f;                          // m * 2^-9
+  if (e == 15u && m == 7u) v = __uint_as_float(0x7fc00000u);
+  return (c & 0x80u) ? -v : v;
+}
+// two binary32 -> two e4m3 codes (round to nearest even, saturating at 448);
+// the first value lands in the low byte
+__device__ __forceinline__ uint32_t f32x2_to_e4m3x2(float lo, float hi) {
+  unsigned short d;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
+// fold of one 16-byte vector position over f inputs, ld(q) giving input q's
+// vector: f32 / i32 natively (add4), BF16 decoded to binary32, folded in
+// order and rounded once
+template <typename LD>
+__device__ __forceinline__ uint4 fold16(LD ld, uint32_t f, uint32_t dt) {
+  uint4 v = ld(0);
+  if (dt != HICCL_BF16) {
+    for (uint32_t q = 1; q < f; ++q) v = add4(v, ld(q), dt);
+    return v;
+  }
+  float a[8];
+  const uint32_t w0[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    a[2 * i] = __uint_as_float(w0[i] << 16);
+    a[2 * i + 1] = __uint_as_float(w0[i] & 0xffff0000u);
+  }
+  for (uint32_t q = 1; q < f; ++q) {
+    const uint4 u = ld(q);
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      a[2 * i] = __fadd_rn(a[2 * i], __uint_as_float(w[i] << 16));
+      a[2 * i + 1] = __fadd_rn(a[2 * i + 1], __uint_as_float(w[i] & 0xffff0000u));
+    }
+  }
+  uint4 r;
+  r.x = f32_to_bf16_rn(a[0]) | (f32_to_bf16_rn(a[1]) << 16);
+  r.y = f32_to_bf16_rn(a[2]) | (f32_to_bf16_rn(a[3]) << 16);
+  r.z = f32_to_bf16_rn(a[4]) | (f32_to_bf16_rn(a[5]) << 16);
+  r.w = f32_to_bf16_rn(a[6]) | (f32_to_bf16_rn(a[7]) << 16);
+  return r;
+}
+
+// FP8 blocks (128 codes, binary32 scale at byte 128, zero bytes 132..143):
+// a group of 8 lanes folds one block, lane `sub` owning codes 16*sub..16*sub+15;
+// blk(q) is input q's block, out the result block.  Inputs are decoded
+// (code value x scale), folded in order in binary32, and the result gets a
+// fresh scale amax / 448 (1 when amax is 0) and codes of value / scale.
+// All 32 lanes must call it together (the amax exchange is warp-wide);
+// `active` lanes read and write.
+template <typename BLK>
+__device__ __forceinline__ void fp8_fold_block(BLK blk, char *out, uint32_t f, uint32_t sub, bool active) {
+  float acc[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+  if (active) {
+    for (uint32_t q = 0; q < f; ++q) {
+      const char *b = blk(q);
+      const uint4 c = *reinterpret_cast<const uint4 *>(b + 16 * sub);
+      const float sc = *reinterpret_cast<const float *>(b + 128);
+      const uint32_t w[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const float x = __fmul_rn(e4m3_to_f32((w[i >> 2] >> (8 * (i & 3))) & 0xffu), sc);
+        acc[i] = q ? __fadd_rn(acc[i], x) : x;
+      }
+    }
+  }
+  float amax = 0.f;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) amax = fmaxf(amax, fabsf(acc[i]));
+  amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, 1));
+  amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, 2));
+  amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, 4));
+  if (!active) return;
+  const float scale = amax > 0.f ? __fdiv_rn(amax, 448.f) : 1.f;
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t lo = f32x2_to_e4m3x2(__fdiv_rn(acc[4 * i], scale), __fdiv_rn(acc[4 * i + 1], scale));
+    const uint32_t hi = f32x2_to_e4m3x2(__fdiv_rn(acc[4 * i + 2], scale), __fdiv_rn(acc[4 * i + 3], scale));
+    w[i] = lo | (hi << 16);
+  }
+  *reinterpret_cast<uint4 *>(out + 16 * sub) = make_uint4(w[0], w[1], w[2], w[3]);
+  if (sub == 0) {
+    *reinterpret_cast<uint4 *>(out + 128) = make_uint4(__float_as_uint(scale), 0u, 0u, 0u);
+  }
+}
+
 // copy bytes [lo, lo + n) of the source to every destination (n <= SEG_BYTES)
 __device__ __forceinline__ void warp_copy(const unsigned long long *ptrs, uint32_t ndst, unsigned long long lo,
                                           uint32_t n, bool aligned, int lane) {
@@ -147,8 +251,19 @@ __device__ __forceinline__ void warp_copy(const unsigned long long *ptrs, uint32
 __device__ __forceinline__ void warp_reduce(const unsigned long long *ptrs, uint32_t nsrc, uint32_t dt,
                                             unsigned long long lo, uint32_t n, bool aligned, int lane) {
   char *dst = reinterpret_cast<char *>(ptrs[nsrc]) + lo;
+  if (dt == HICCL_FP8E4M3) {   // whole 144-byte blocks, four per warp pass
+    const uint32_t nblk = n / FP8_BLOCK_BYTES, grp = lane >> 3, sub = lane & 7;
+    for (uint32_t b0 = 0; b0 < nblk; b0 += 4) {
+      const uint32_t blk = b0 + grp;
+      const bool act = blk < nblk;
+      const unsigned long long off = lo + (unsigned long long)blk * FP8_BLOCK_BYTES;
+      fp8_fold_block([&](uint32_t q) { return reinterpret_cast<const char *>(ptrs[q]) + off; },
+                     reinterpret_cast<char *>(ptrs[nsrc]) + off, nsrc, sub, act);
+    }
+    return;
+  }
   uint32_t done = 0;
-  if (aligned) {
+  if (aligned && dt != HICCL_BF16) {
     constexpr int U = 4;
     const uint32_t nvec = n >> 4;
     for (uint32_t base = 0; base < nvec; base += 32 * U) {
@@ -177,8 +292,25 @@ __device__ __forceinline__ void warp_reduce(const unsigned long long *ptrs, uint
       }
     }
     done = nvec << 4;
+  } else if (aligned) {   // BF16 vectors of 8 values
+    const uint32_t nvec = n >> 4;
+    for (uint32_t i = lane; i < nvec; i += 32)
+      st16(dst + (i << 4),
+           fold16([&](uint32_t q) { return ld16(reinterpret_cast<const char *>(ptrs[q]) + lo + (i << 4)); }, nsrc, dt));
+    done = nvec << 4;
   }
-  // element tail (or the whole unaligned range): 4-byte elements
+  // element tail (or the whole unaligned range)
+  if (dt == HICCL_BF16) {
+    for (uint32_t b = done + 2 * lane; b < n; b += 64) {
+      float acc = __uint_as_float((uint32_t)__ldcg(reinterpret_cast<const unsigned short *>(
+                                      reinterpret_cast<const char *>(ptrs[0]) + lo + b)) << 16);
+      for (uint32_t q = 1; q < nsrc; ++q)
+        acc = __fadd_rn(acc, __uint_as_float((uint32_t)__ldcg(reinterpret_cast<const unsigned short *>(
+                                                 reinterpret_cast<const char *>(ptrs[q]) + lo + b)) << 16));
+      *reinterpret_cast<unsigned short *>(dst + b) = (unsigned short)f32_to_bf16_rn(acc);
+    }
+    return;
+  }
   for (uint32_t b = done + 4 * lane; b < n; b += 128) {
     uint32_t acc = __ldcg(reinterpret_cast<const unsigned int *>(reinterpret_cast<const char *>(ptrs[0]) + lo + b));
     for (uint32_t q = 1; q < nsrc; ++q) {
@@ -191,10 +323,6 @@ __device__ __forceinline__ void warp_reduce(const unsigned long long *ptrs, uint
     *reinterpret_cast<uint32_t *>(dst + b) = acc;
   }
 }
-
-// ---------------------------------------------------------------------------
-// the persistent executor
-// ---------------------------------------------------------------------------
 
 constexpr int PMAX = 6;   // pointers of a step staged in shared memory (more: read from global)
 constexpr int NBUF = 3;   // work items staged ahead of the data warps
@@ -279,7 +407,7 @@ struct SegRef {
   uint32_t n;
 };
 template <typename Buf>
-__device__ __forceinline__ SegRef seg_of(const Buf &B, uint32_t j) {
+__device__ __forceinline__ SegRef seg_of(const Buf &B, uint32_t j, unsigned long long segb) {
   uint32_t k = 0, hi = B.nent;   // largest k with pre[k] <= j
   while (hi - k > 1) {
     const uint32_t mid = (k + hi) >> 1;
@@ -289,8 +417,8 @@ __device__ __forceinline__ SegRef seg_of(const Buf &B, uint32_t j) {
   SegRef r;
   r.k = k;
   const unsigned long long seg = B.ent[k].seg_lo + (j - B.pre[k]);
-  r.lo = seg * SEG_BYTES;
-  r.n = (uint32_t)min((unsigned long long)SEG_BYTES, B.nb[k] - r.lo);
+  r.lo = seg * segb;
+  r.n = (uint32_t)min(segb, B.nb[k] - r.lo);
   return r;
 }
 
@@ -483,7 +611,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
       return total > (uint32_t)dw ? (total - dw + D - 1) / D : 0u;
     };
     auto issue = [&](const ItemBuf &X, uint32_t i, uint32_t at) {   // segment i of X into load number `at`
-      const SegRef g = seg_of(X, dw + i * D);
+      const SegRef g = seg_of(X, dw + i * D, T.seg);
       const uint32_t np = meta_nsrc(X.meta[g.k]) + meta_ndst(X.meta[g.k]);
       const unsigned long long *ptrs = np <= PMAX ? X.ptr[g.k] : T.ptrs + X.poff[g.k];
       const uint32_t slot = at % NS;
@@ -517,7 +645,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
                 stalled = true;
                 break;
               }
-              const SegRef g = seg_of(B, dw + i * D);
+              const SegRef g = seg_of(B, dw + i * D, T.seg);
               const uint32_t meta = B.meta[g.k];
               const uint32_t np = meta_nsrc(meta) + meta_ndst(meta);
               const unsigned long long *ptrs = np <= PMAX ? B.ptr[g.k] : T.ptrs + B.poff[g.k];
@@ -556,7 +684,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         pre_issued = __shfl_sync(0xffffffffu, pre_issued, 0);
         // ragged tails (the last few bytes of a step that are not a 16-byte multiple)
         for (uint32_t i = 0; i < nm; ++i) {
-          const SegRef g = seg_of(B, dw + i * D);
+          const SegRef g = seg_of(B, dw + i * D, T.seg);
           const uint32_t n16 = g.n & ~15u;
           if (n16 == g.n) continue;
           const uint32_t meta = B.meta[g.k];
@@ -578,12 +706,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         bool stalled = false;
         const uint32_t nm = mine(B);
         for (uint32_t i = 0; i < nm && !stalled; ++i) {
-          const SegRef g = seg_of(B, dw + i * D);
+          const SegRef g = seg_of(B, dw + i * D, T.seg);
           const uint32_t meta = B.meta[g.k];
           const uint32_t f = meta_nsrc(meta);
           const unsigned long long *ptrs = (f + 1) <= PMAX ? B.ptr[g.k] : T.ptrs + B.poff[g.k];
           const uint32_t n16 = g.n & ~15u;
-          const uint32_t chunk = (AREA / f) & ~15u;
+          const uint32_t dt = meta_dtype(meta);
+          const uint32_t chunk = dt == HICCL_FP8E4M3 ? (AREA / f) / FP8_BLOCK_BYTES * FP8_BLOCK_BYTES
+                                                     : (AREA / f) & ~15u;
           for (uint32_t off = 0; off < n16; off += chunk) {
             const uint32_t len = min(chunk, n16 - off);
             if (lane == 0) {
@@ -599,11 +729,18 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
               break;
             }
             ++rseq;
-            for (uint32_t v = lane; v < len / 16; v += 32) {
-              uint4 acc = *reinterpret_cast<const uint4 *>(my_stage + v * 16);
-              for (uint32_t q = 1; q < f; ++q)
-                acc = add4(acc, *reinterpret_cast<const uint4 *>(my_stage + q * chunk + v * 16), meta_dtype(meta));
-              *reinterpret_cast<uint4 *>(my_stage + v * 16) = acc;
+            if (dt == HICCL_FP8E4M3) {
+              const uint32_t nblk = len / FP8_BLOCK_BYTES, grp = lane >> 3, sub = lane & 7;
+              for (uint32_t b0 = 0; b0 < nblk; b0 += 4) {
+                const uint32_t blk = b0 + grp;
+                const uint32_t boff = blk * FP8_BLOCK_BYTES;
+                fp8_fold_block([&](uint32_t q) { return reinterpret_cast<const char *>(my_stage + q * chunk + boff); },
+                               reinterpret_cast<char *>(my_stage + boff), f, sub, blk < nblk);
+              }
+            } else {
+              for (uint32_t v = lane; v < len / 16; v += 32)
+                *reinterpret_cast<uint4 *>(my_stage + v * 16) = fold16(
+                    [&](uint32_t q) { return *reinterpret_cast<const uint4 *>(my_stage + q * chunk + v * 16); }, f, dt);
             }
             fence_proxy_async_smem();   // the folded chunk is read by the bulk store
             __syncwarp();
@@ -613,13 +750,20 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
             }
           }
           // element tail of the last segment of a step (fewer than 16 bytes)
-          if (!stalled && n16 != g.n && lane < (int)((g.n - n16) / 4)) {
+          if (!stalled && n16 != g.n && dt == HICCL_BF16 && lane < (int)((g.n - n16) / 2)) {
+            const unsigned long long b = g.lo + n16 + 2 * lane;
+            float acc = __uint_as_float((uint32_t)__ldcg(reinterpret_cast<const unsigned short *>(
+                                            reinterpret_cast<const char *>(ptrs[0]) + b)) << 16);
+            for (uint32_t q = 1; q < f; ++q)
+              acc = __fadd_rn(acc, __uint_as_float((uint32_t)__ldcg(reinterpret_cast<const unsigned short *>(
+                                                       reinterpret_cast<const char *>(ptrs[q]) + b)) << 16));
+            *reinterpret_cast<unsigned short *>(reinterpret_cast<char *>(ptrs[f]) + b) = (unsigned short)f32_to_bf16_rn(acc);
+          } else if (!stalled && n16 != g.n && dt != HICCL_BF16 && lane < (int)((g.n - n16) / 4)) {
             const unsigned long long b = g.lo + n16 + 4 * lane;
             uint32_t acc = __ldcg(reinterpret_cast<const unsigned int *>(reinterpret_cast<const char *>(ptrs[0]) + b));
             for (uint32_t q = 1; q < f; ++q) {
               const uint32_t v = __ldcg(reinterpret_cast<const unsigned int *>(reinterpret_cast<const char *>(ptrs[q]) + b));
-              acc = meta_dtype(meta) == HICCL_F32 ? __float_as_uint(__fadd_rn(__uint_as_float(acc), __uint_as_float(v)))
-                                                  : acc + v;
+              acc = dt == HICCL_F32 ? __float_as_uint(__fadd_rn(__uint_as_float(acc), __uint_as_float(v))) : acc + v;
             }
             *reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(ptrs[f]) + b) = acc;
           }
@@ -635,8 +779,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         for (uint32_t j = dw; j < total; j += D) {
           while (B.pre[k + 1] <= j) ++k;
           const unsigned long long seg = B.ent[k].seg_lo + (j - B.pre[k]);
-          const unsigned long long lo = seg * SEG_BYTES;
-          const uint32_t n = (uint32_t)min((unsigned long long)SEG_BYTES, B.nb[k] - lo);
+          const unsigned long long lo = seg * T.seg;
+          const uint32_t n = (uint32_t)min(T.seg, B.nb[k] - lo);
           const uint32_t meta = B.meta[k];
           const uint32_t np = meta_nsrc(meta) + meta_ndst(meta);
           const unsigned long long *ptrs = np <= PMAX ? B.ptr[k] : T.ptrs + B.poff[k];
@@ -752,9 +896,6 @@ hiccl_status_t dev_upload(hiccl_comm *c) {
     indeg[i] = p.pred_off[i + 1] - p.pred_off[i];
     bool al = true;
     for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k) al = al && (ptrs[st.loc0 + k] % 16 == 0);
-    // the unaligned reduce path moves 4-byte elements
-    if (st.kind == OP_REDUCE && !al && c->esize != 4)
-      return fail(c, HICCL_ERR_UNSUPPORTED, "reduction buffers must be 16-byte aligned for this dtype");
     meta[i] = meta_pack(st.kind, (uint32_t)c->dtype, al ? 1u : 0u, st.nsrc, st.ndst);
   }
 
@@ -823,6 +964,7 @@ hiccl_status_t dev_upload(hiccl_comm *c) {
   t.host_err = d->host_err_dev;
   t.nitems = p.item_off.size() - 1;
   t.timeout_ns = c->timeout_ns;
+  t.seg = p.seg;
   t.trace = nullptr;
   if (c->trace && t.nitems) {
     if ((e = cudaMalloc(&d->trace, t.nitems * 5 * sizeof(unsigned long long))) != cudaSuccess) {
@@ -1040,6 +1182,7 @@ extern "C" hiccl_status_t hiccl_run_static(hiccl_comm_t c, void *stream) {
   t.host_err = reinterpret_cast<unsigned long long *>(base + o_ctr + N * 16 + sizeof(DevCtl));
   t.nitems = NI;
   t.timeout_ns = c->timeout_ns;
+  t.seg = p.seg;
   t.trace = nullptr;
   if (NI > 0) {
     int nsm = 0, occ = 0;

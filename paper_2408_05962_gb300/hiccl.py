@@ -18,7 +18,17 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libhiccl.so")
 
 F32, I32, BF16, FP8E4M3 = 0, 1, 2, 3
 DTYPES = {"f32": F32, "i32": I32, "bf16": BF16, "fp8": FP8E4M3}
-ESIZE = {F32: 4, I32: 4, BF16: 2, FP8E4M3: 1}
+ESIZE = {F32: 4, I32: 4, BF16: 2}
+FP8_BLOCK, FP8_BLOCK_BYTES = 128, 144     # FP8 payload: 128 e4m3 codes + binary32 scale + 12 zero bytes
+
+
+def nbytes(dtype: int, elems: int) -> int:
+    """Bytes of ``elems`` values of a payload (FP8: whole 128-value blocks)."""
+    if dtype == FP8E4M3:
+        if elems % FP8_BLOCK:
+            raise ValueError("FP8 counts must be multiples of 128")
+        return elems // FP8_BLOCK * FP8_BLOCK_BYTES
+    return elems * ESIZE[dtype]
 SUM = 0
 
 OK, ERR_INVALID, ERR_STATE, ERR_RACE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_TOO_LARGE = range(9)
@@ -267,7 +277,6 @@ class Comm:
     def __init__(self, nranks: int, dtype: int | str = "f32"):
         self.P = int(nranks)
         self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
-        self.esize = ESIZE[self.dtype]
         self.handle = hiccl_create(self.P, self.dtype)
         self.nlevels = None
 

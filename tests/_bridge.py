@@ -12,17 +12,19 @@ from __future__ import annotations
 
 import numpy as np
 
+from oracle.lowprec import from_acc, to_acc
 from oracle.model import DTYPES, Multicast
 from paper_2408_05962_gb300 import hiccl as H
 
-ESIZE = {"f32": 4, "i32": 4, "bf16": 2, "fp8": 1}
+# the oracle counts FP8 programs in 128-value blocks, the C ABI in values
+COUNT_SCALE = {"f32": 1, "i32": 1, "bf16": 1, "fp8": 128}
 
 
 class FakeAddresses:
     """Disjoint 256-byte aligned fake device addresses for every buffer key."""
 
     def __init__(self, prog, base=0x7f0000000000, gap=4096):
-        self.esize = ESIZE[prog.dtype]
+        self.esize = DTYPES[prog.dtype].itemsize
         self.base = {}
         a = base
         for key, n in prog.buffers.items():
@@ -48,6 +50,7 @@ def register(prog, addr_of, dtype=None) -> H.Comm:
     """A library communicator holding ``prog``'s primitives at ``addr_of(ref)``."""
     comm = H.Comm(prog.P, dtype or prog.dtype)
     P = prog.P
+    k = COUNT_SCALE[prog.dtype]
     for e, epoch in enumerate(prog.epochs):
         if e:
             comm.add_fence()
@@ -58,12 +61,12 @@ def register(prog, addr_of, dtype=None) -> H.Comm:
                 send[p.root] = addr_of(p.src)
                 for j in p.leaves:
                     recv[j] = addr_of(p.dsts[j])
-                comm.add_multicast(send, recv, p.count, p.root, p.leaves)
+                comm.add_multicast(send, recv, p.count * k, p.root, p.leaves)
             else:
                 for i in p.leaves:
                     send[i] = addr_of(p.srcs[i])
                 recv[p.root] = addr_of(p.dst)
-                comm.add_reduction(send, recv, p.count, p.leaves, p.root)
+                comm.add_reduction(send, recv, p.count * k, p.leaves, p.root)
     return comm
 
 
@@ -90,6 +93,11 @@ def interpret(comm: H.Comm, fake: FakeAddresses, mem: dict, dtype: str) -> dict:
             src = view(st["srcs"][0], n).copy()
             for d in st["dsts"]:
                 view(d, n)[...] = src
+        elif dtype in ("bf16", "fp8"):
+            acc = to_acc(view(st["srcs"][0], n).copy().view(dt), dtype).copy()
+            for s in st["srcs"][1:]:
+                acc = (acc + to_acc(view(s, n).copy().view(dt), dtype)).astype(np.float32)
+            view(st["dsts"][0], n)[...] = from_acc(acc, dtype).view(np.uint8)
         else:
             acc = view(st["srcs"][0], n).copy().view(dt)
             for s in st["srcs"][1:]:

@@ -22,7 +22,7 @@ def run_on_gpu(prog, h, s, m, mem0: dict, repeats: int = 1, misalign_elems: int 
     dev = torch.device("cuda:0")
     tdt = torch_dtype(prog.dtype)
     dev_bufs, base_addr = {}, {}
-    esize = np.dtype(mem0[next(iter(mem0))].dtype).itemsize
+    esize = np.dtype(mem0[next(iter(mem0))].dtype).itemsize   # FP8: one 144-byte block
     sentinel = {}
     for kidx, (key, arr) in enumerate(mem0.items()):
         n = arr.shape[0]

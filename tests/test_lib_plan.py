@@ -108,3 +108,26 @@ def test_table_order_and_items():
         for q in st["preds"]:
             assert steps[q]["slot"] < st["slot"]
     assert info["items"] >= 1 and info["slots"] == slots[-1] + 1
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+@pytest.mark.parametrize("name", ["allreduce", "reducescatter", "reduce", "allgather", "alltoall", "broadcast"])
+@pytest.mark.parametrize("P,h,s,m", [(8, [2, 4], 1, 1), (8, [2, 4], 4, 3), (12, [2, 2, 3], 3, 2)])
+def test_lowprec_collectives(dtype, name, P, h, s, m):
+    """BF16 and block-scaled FP8 payloads: the library's step table, run by
+    the NumPy interpreter with the payloads' decode / fold / encode, equals
+    the oracle bit for bit (FP8 counts are 128-value blocks)."""
+    d = 37 if dtype == "bf16" else 3
+    _check(PR.BUILDERS[name](P, d, dtype=dtype), h, s, m, seed=P + s + m)
+
+
+def test_fp8_count_must_be_block_multiple():
+    from paper_2408_05962_gb300 import hiccl as H
+    c = H.Comm(2, "fp8")
+    a = [0x100000, 0x200000]
+    with pytest.raises(H.HicclError) as e:
+        c.add_multicast(a, a, 100, 0, [1])
+    assert e.value.status == H.ERR_INVALID
+    c.add_multicast(a, [0, 0x300000], 256, 0, [1])
+    c.plan([2])
+    assert c.hbm_bytes() == (2 * 144, 2 * 144)
