@@ -13,8 +13,9 @@ Formats, written from their definitions:
 * **FP8 block** (this library's payload layout): 128 e4m3 codes followed by
   their binary32 scale and 12 zero bytes -- 144 bytes per 128 elements.  The
   value of code q is decode(q) * scale.  Quantizing a block of binary32
-  values x: amax = max|x|; scale = amax / 448 (binary32 division), or 1 when
-  amax is 0; codes = encode(x / scale) (binary32 division).
+  values x: amax = max|x|; scale = amax / 448 and inv = 448 / amax (binary32
+  divisions; both 1 when amax is 0); codes = encode(x * inv) (binary32
+  multiply: one reciprocal per block rather than a division per value).
 
 Reduction of these payloads (the reading of "FP32 accumulation"): every
 input of a reduce step is decoded to binary32, the inputs are folded in the
@@ -110,9 +111,12 @@ def fp8_quantize(x: np.ndarray) -> np.ndarray:
     x = np.asarray(x, dtype=np.float32).reshape(-1, FP8_BLOCK)
     out = np.zeros(x.shape[0], dtype=FP8_BLOCK_DTYPE)
     amax = np.max(np.abs(x), axis=1)
-    scale = np.where(amax == 0, np.float32(1.0), (amax / np.float32(FP8_MAX)).astype(np.float32)).astype(np.float32)
+    zero = amax == 0
+    safe = np.where(zero, np.float32(1.0), amax).astype(np.float32)
+    scale = np.where(zero, np.float32(1.0), (safe / np.float32(FP8_MAX)).astype(np.float32)).astype(np.float32)
+    inv = np.where(zero, np.float32(1.0), (np.float32(FP8_MAX) / safe).astype(np.float32)).astype(np.float32)
     out["s"] = scale
-    out["q"] = e4m3_encode((x / scale[:, None]).astype(np.float32))
+    out["q"] = e4m3_encode((x * inv[:, None]).astype(np.float32))
     return out
 
 

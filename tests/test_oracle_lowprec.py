@@ -96,6 +96,8 @@ def test_fp8_block_quantize_bounds():
     xb = x.reshape(-1, 128)
     amax = np.abs(xb).max(axis=1)
     assert np.array_equal(b["s"], (amax / np.float32(448)).astype(np.float32))
+    inv = (np.float32(448) / amax).astype(np.float32)
+    assert np.array_equal(b["q"], LP.e4m3_encode((xb * inv[:, None]).astype(np.float32)))
     assert np.all(np.abs(LP.e4m3_decode(b["q"])).max(axis=1) == 448.0)   # the max element maps to +-448
     y = LP.fp8_dequantize(b).reshape(-1, 128)
     err = np.abs(y.astype(np.float64) - xb)
