@@ -279,6 +279,24 @@ def run_reference(args):
 # the CUDA path
 # ---------------------------------------------------------------------------
 
+def _fp8_blocks(x):
+    """Encode binary32 rows into the FP8 payload (per 128 values: e4m3
+    codes of x * (448 / amax), the binary32 scale amax / 448, 12 zero bytes), on the
+    GPU with torch's float8_e4m3fn conversion (round to nearest even).
+    Input encoding is set-up, not part of the timed path."""
+    import torch
+    P, n = x.shape
+    xb = x.reshape(P, n // 128, 128)
+    amax = xb.abs().amax(dim=2, keepdim=True)
+    scale = torch.where(amax == 0, torch.ones_like(amax), amax / 448.0)
+    inv = torch.where(amax == 0, torch.ones_like(amax), 448.0 / amax)
+    q = (xb * inv).clamp(-448.0, 448.0).to(torch.float8_e4m3fn).view(torch.uint8)
+    out = torch.zeros(P, n // 128, 144, dtype=torch.uint8, device=x.device)
+    out[:, :, :128] = q
+    out[:, :, 128:132] = scale.view(torch.uint8).reshape(P, n // 128, 4)
+    return out.reshape(P, -1)
+
+
 def run_ours(args):
     import torch
 
@@ -296,19 +314,33 @@ def run_ours(args):
 
     W = WORKLOADS[args.workload]
     Pw, hier, stripe, pipe = W["ranks"], W["hierarchy"], W["stripe"], W["pipeline"]
-    d = W["bytes_per_rank"] // 4 // Pw
+    d = W["bytes_per_rank"] // 4 // Pw            # values per chunk (64 MiB of fp32 values per rank)
+    dtype = args.dtype
     if args.workload == "seven":
+        if dtype != "f32":
+            raise SystemExit("the seven-collective workload is fp32")
         x = torch.from_numpy(uniform_ranks(Pw, d * Pw, seed=0))
     else:
         from synth import scaled_normal_ranks
-        x = torch.from_numpy(scaled_normal_ranks(Pw, d * Pw, seed=0))
+        xs = scaled_normal_ranks(Pw, d * Pw, seed=0)
+        if dtype == "bf16":       # round to nearest even on the upper 16 bits (payload encoding)
+            t = torch.from_numpy(xs).view(torch.int32)
+            x = ((t + 0x7FFF + ((t >> 16) & 1)) >> 16).to(torch.int16)
+        elif dtype == "fp8":      # per-128-value block scales, e4m3 codes (payload encoding on the GPU)
+            x = None
+        else:
+            x = torch.from_numpy(xs)
     comms, bufs, nbytes, pbytes = {}, {}, {}, {}
     kinds = tuple(args.kinds.split(",")) if args.kinds else W["kinds"]
+    tdt = {"f32": torch.float32, "bf16": torch.int16, "fp8": torch.uint8}[dtype]
     for kind in kinds:
-        b = C.Buffers(kind, Pw, d, torch.float32, device)
-        b.send.copy_(x[:, :b.ls].to(device))
+        b = C.Buffers(kind, Pw, d, tdt, device)
+        if x is None:
+            b.send.copy_(_fp8_blocks(torch.from_numpy(xs).to(device)))
+        else:
+            b.send.copy_(x[:, :b.send.shape[1]].to(device))
         b.recv.zero_()
-        comm = H.Comm(Pw, "f32")
+        comm = H.Comm(Pw, dtype)
         if args.item_bytes:
             comm.set_option(H.OPT_ITEM_BYTES, args.item_bytes)
         if args.order is not None:
@@ -321,7 +353,7 @@ def run_ours(args):
         comm.init(hier, stripe, pipe)
         rd, wr = comm.hbm_bytes()
         comms[kind], bufs[kind], nbytes[kind] = comm, b, rd + wr
-        pbytes[kind] = d * 4 * Pw                      # the paper's d*p per collective
+        pbytes[kind] = H.nbytes(H.DTYPES[dtype], d * Pw)   # the paper's d*p per collective
     stream = torch.cuda.current_stream(device)
     step_bytes = sum(nbytes.values())
 
@@ -365,12 +397,12 @@ def run_ours(args):
     peak, peak_kind = measured_peak()
 
     # end to end through the public API with host buffers (pinned)
-    h_send = {k: torch.empty(bufs[k].send.shape, dtype=torch.float32, pin_memory=True) for k in kinds}
-    h_recv = {k: torch.empty(bufs[k].recv.shape, dtype=torch.float32, pin_memory=True) for k in kinds}
+    h_send = {k: torch.empty(bufs[k].send.shape, dtype=tdt, pin_memory=True) for k in kinds}
+    h_recv = {k: torch.empty(bufs[k].recv.shape, dtype=tdt, pin_memory=True) for k in kinds}
     for k in kinds:
-        h_send[k].copy_(x[:, :bufs[k].ls])
-    h2d = sum(t.numel() * 4 for t in h_send.values())
-    d2h = sum(t.numel() * 4 for t in h_recv.values())
+        h_send[k].copy_(bufs[k].send)
+    h2d = sum(t.numel() * t.element_size() for t in h_send.values())
+    d2h = sum(t.numel() * t.element_size() for t in h_recv.values())
     e2e_steps = max(1, min(args.steps, 3))
     barrier(device)
     torch.cuda.synchronize(device)
@@ -404,8 +436,9 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": statistics.mean(step_ms),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": workload_config({"parallelism": f"replicas{world}"}, args.workload),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+        "data": "synthetic", "config": workload_config({"parallelism": f"replicas{world}", "payload": dtype},
+                                                       args.workload),
         "roofline": {"bound": "hbm", "achieved": gbs / world, "peak": peak, "unit": "GB/s",
                      "frac": gbs / world / peak, "peak_source": peak_kind,
                      "traffic": traffic, "kernel": "hiccl_exec_kernel"},
@@ -432,6 +465,8 @@ def main(argv=None):
     ap.add_argument("--item-bytes", type=int, default=0, help="executor work-item size (0: library default)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="executor CTAs per SM (0: library default)")
     ap.add_argument("--workload", default="seven", choices=sorted(WORKLOADS))
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8"],
+                    help="payload of the allreduce64 workload (accumulation is FP32)")
     ap.add_argument("--kinds", default="", help="comma-separated subset of the seven collectives (profiling)")
     ap.add_argument("--threads", type=int, default=0, help="executor threads per CTA (0: library default)")
     ap.add_argument("--order", type=int, default=None, help="work order: 0 pipeline slots, 1 stage depth")

@@ -121,13 +121,16 @@ __device__ __forceinline__ uint32_t f32_to_bf16_rn(float x) {
   return h;
 }
 // FP8 e4m3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits, no
-// infinities, S.1111.111 = NaN): exact decode from the bit fields
-__device__ __forceinline__ float e4m3_to_f32(uint32_t c) {
-  const uint32_t e = (c >> 3) & 15u, m = c & 7u;
-  float v = e ? __uint_as_float(((e + 120u) << 23) | (m << 20))   // (1 + m/8) * 2^(e-7)
-              : (float)m * 0.001953125f;                          // m * 2^-9
-  if (e == 15u && m == 7u) v = __uint_as_float(0x7fc00000u);
-  return (c & 0x80u) ? -v : v;
+// infinities, S.1111.111 = NaN): two codes -> two binary32 values, exactly
+// (every e4m3 value is a binary16 value); the low byte gives .x
+__device__ __forceinline__ float2 e4m3x2_to_f32x2(uint32_t two) {
+  uint32_t h2;
+  asm("{\n\t.reg .b16 t;\n\tmov.b16 t, %1;\n\tcvt.rn.f16x2.e4m3x2 %0, t;\n\t}" : "=r"(h2) : "h"((unsigned short)two));
+  float lo, hi;
+  asm("{\n\t.reg .b16 a, b;\n\tmov.b32 {a, b}, %2;\n\tcvt.f32.f16 %0, a;\n\tcvt.f32.f16 %1, b;\n\t}"
+      : "=f"(lo), "=f"(hi)
+      : "r"(h2));
+  return make_float2(lo, hi);
 }
 // two binary32 -> two e4m3 codes (round to nearest even, saturating at 448);
 // the first value lands in the low byte
@@ -175,7 +178,8 @@ __device__ __forceinline__ uint4 fold16(LD ld, uint32_t f, uint32_t dt) {
 // a group of 8 lanes folds one block, lane `sub` owning codes 16*sub..16*sub+15;
 // blk(q) is input q's block, out the result block.  Inputs are decoded
 // (code value x scale), folded in order in binary32, and the result gets a
-// fresh scale amax / 448 (1 when amax is 0) and codes of value / scale.
+// fresh scale amax / 448 and codes of value x (448 / amax) (both factors 1
+// when amax is 0).
 // All 32 lanes must call it together (the amax exchange is warp-wide);
 // `active` lanes read and write.
 template <typename BLK>
@@ -190,9 +194,11 @@ __device__ __forceinline__ void fp8_fold_block(BLK blk, char *out, uint32_t f, u
       const float sc = *reinterpret_cast<const float *>(b + 128);
       const uint32_t w[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const float x = __fmul_rn(e4m3_to_f32((w[i >> 2] >> (8 * (i & 3))) & 0xffu), sc);
-        acc[i] = q ? __fadd_rn(acc[i], x) : x;
+      for (int i = 0; i < 16; i += 2) {
+        const float2 v = e4m3x2_to_f32x2((w[i >> 2] >> (8 * (i & 3))) & 0xffffu);
+        const float x0 = __fmul_rn(v.x, sc), x1 = __fmul_rn(v.y, sc);
+        acc[i] = q ? __fadd_rn(acc[i], x0) : x0;
+        acc[i + 1] = q ? __fadd_rn(acc[i + 1], x1) : x1;
       }
     }
   }
@@ -204,11 +210,12 @@ __device__ __forceinline__ void fp8_fold_block(BLK blk, char *out, uint32_t f, u
   amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, 4));
   if (!active) return;
   const float scale = amax > 0.f ? __fdiv_rn(amax, 448.f) : 1.f;
+  const float inv = amax > 0.f ? __fdiv_rn(448.f, amax) : 1.f;
   uint32_t w[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const uint32_t lo = f32x2_to_e4m3x2(__fdiv_rn(acc[4 * i], scale), __fdiv_rn(acc[4 * i + 1], scale));
-    const uint32_t hi = f32x2_to_e4m3x2(__fdiv_rn(acc[4 * i + 2], scale), __fdiv_rn(acc[4 * i + 3], scale));
+    const uint32_t lo = f32x2_to_e4m3x2(__fmul_rn(acc[4 * i], inv), __fmul_rn(acc[4 * i + 1], inv));
+    const uint32_t hi = f32x2_to_e4m3x2(__fmul_rn(acc[4 * i + 2], inv), __fmul_rn(acc[4 * i + 3], inv));
     w[i] = lo | (hi << 16);
   }
   *reinterpret_cast<uint4 *>(out + 16 * sub) = make_uint4(w[0], w[1], w[2], w[3]);
