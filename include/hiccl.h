@@ -161,6 +161,7 @@ typedef struct {
   unsigned long long scratch_bytes;  /* relay buffers on the device              */
   unsigned long long table_bytes;    /* step table + counters on the device      */
   unsigned long long slots;          /* pipeline time slots of the work order    */
+  unsigned long long runs;           /* contiguous data ranges the items move     */
 } hiccl_plan_info_t;
 
 /* Summary of the factorized plan.  Valid after hiccl_init or hiccl_plan. */

@@ -51,6 +51,17 @@ struct DevEntry {
   uint32_t pad;
 };
 
+// A run of an item: consecutive entries whose steps have identical shape and
+// operands that continue one another in memory (adjacent pipeline channels of
+// one branch), moved as one range.  `entry` is the run's first entry within
+// the item; `off` the byte offset in that entry's step where the run starts.
+struct DevRun {
+  uint32_t entry;
+  uint32_t pad;
+  unsigned long long off;
+  unsigned long long bytes;
+};
+
 // per-launch control block (device memory, zeroed at upload)
 struct DevCtl {
   unsigned long long ticket;   // next work item to claim
@@ -70,6 +81,8 @@ struct DevTable {
   const unsigned long long *ptrs;     // [nptrs] device addresses
   const DevEntry *entries;            // [nentries]
   const uint32_t *item_off;           // [nitems + 1] entry ranges of the work items
+  const DevRun *runs;                 // [nruns] data ranges of the work items
+  const uint32_t *run_off;            // [nitems + 1] run ranges of the work items
   unsigned long long *dep;            // [nsteps] arrivals of predecessors (cumulative over launches)
   unsigned long long *done;           // [nsteps] finished entries (cumulative over launches)
   DevCtl *ctl;
@@ -104,6 +117,8 @@ struct HStep {
   uint32_t nsrc;
   uint32_t ndst;
   unsigned long long slot;
+  uint32_t local;          // emission index inside its piece (same tree position in every channel)
+  uint32_t pad2;
 };
 
 struct Prim {
@@ -128,6 +143,8 @@ struct Plan {
   std::vector<uint32_t> succ_off, succ;    // CSR of successors
   std::vector<DevEntry> entries;
   std::vector<uint32_t> item_off;
+  std::vector<DevRun> runs;
+  std::vector<uint32_t> run_off;
   std::vector<uint32_t> nent;             // entries covering each step
   unsigned long long scratch_bytes = 0;
   std::vector<unsigned long long> level_bytes;

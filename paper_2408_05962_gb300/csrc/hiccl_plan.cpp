@@ -85,8 +85,17 @@ struct Builder {
   unsigned long long scratch_top = 0;
   // current emission context
   int cur_prim = 0, cur_epoch = 0, cur_branch = 0, cur_channel = 0;
+  uint32_t cur_local = 0, cur_relay = 0;   // steps / relays emitted in the current piece
   const Prim *p = nullptr;
   unsigned long long cur_off = 0, cur_n = 0;
+  // relay buffers: allocated with ids during emission, laid out afterwards so
+  // that the same relay of adjacent channels is adjacent in memory
+  struct Relay {
+    int prim, branch, channel;
+    uint32_t local;
+    unsigned long long bytes, off;
+  };
+  std::vector<Relay> relays;
 
   Builder(const hiccl_comm &comm, const std::vector<int> &hier, int stripe, int pipeline)
       : c(comm), h(hier), L((int)hier.size()), s(stripe), m(pipeline) {
@@ -111,6 +120,7 @@ struct Builder {
     st.branch = cur_branch;
     st.channel = cur_channel;
     st.nbytes = cur_n;
+    st.local = cur_local++;
     st.loc0 = (uint32_t)locs.size();
     st.nsrc = (uint32_t)srcs.size();
     st.ndst = (uint32_t)dsts.size();
@@ -123,10 +133,43 @@ struct Builder {
     return idx;
   }
 
-  Loc scratch_loc(int rank) {
-    unsigned long long off = (scratch_top + 255ull) & ~255ull;
-    scratch_top = off + cur_n;
-    return Loc{off, rank, 1};
+  Loc scratch_loc(int rank) {   // addr holds the relay id until layout_relays()
+    relays.push_back(Relay{cur_prim, cur_branch, cur_channel, cur_relay++, cur_n, 0});
+    return Loc{relays.size() - 1, rank, 1};
+  }
+  void begin_piece(int b, int ch, unsigned long long lo_bytes, unsigned long long n_bytes) {
+    cur_branch = b;
+    cur_channel = ch;
+    cur_off = lo_bytes;
+    cur_n = n_bytes;
+    cur_local = 0;
+    cur_relay = 0;
+  }
+  // place relays: the same relay of consecutive channels back to back (16-byte
+  // granules), groups 256-byte aligned; then replace relay ids by offsets
+  void layout_relays() {
+    std::vector<uint32_t> ord(relays.size());
+    std::iota(ord.begin(), ord.end(), 0u);
+    std::sort(ord.begin(), ord.end(), [&](uint32_t a, uint32_t b) {
+      const Relay &x = relays[a], &y = relays[b];
+      if (x.prim != y.prim) return x.prim < y.prim;
+      if (x.branch != y.branch) return x.branch < y.branch;
+      if (x.local != y.local) return x.local < y.local;
+      return x.channel < y.channel;
+    });
+    unsigned long long top = 0;
+    for (size_t i = 0; i < ord.size(); ++i) {
+      Relay &r = relays[ord[i]];
+      const bool cont = i > 0 && relays[ord[i - 1]].prim == r.prim && relays[ord[i - 1]].branch == r.branch &&
+                        relays[ord[i - 1]].local == r.local && relays[ord[i - 1]].channel + 1 == r.channel &&
+                        top % 16 == 0;
+      if (!cont) top = (top + 255ull) & ~255ull;
+      r.off = top;
+      top += r.bytes;
+    }
+    scratch_top = top;
+    for (Loc &l : locs)
+      if (l.scratch) l.addr = relays[l.addr].off;
   }
   Loc send_loc(int r) const { return Loc{p->send[r] + cur_off, r, 0}; }
   Loc recv_loc(int r) const { return Loc{p->recv[r] + cur_off, r, 0}; }
@@ -251,10 +294,7 @@ struct Builder {
       for (int ch = 0; ch < m; ++ch) {
         unsigned long long lo = bd[b * m + ch], hi = bd[b * m + ch + 1];
         if (hi <= lo) continue;
-        cur_branch = b;
-        cur_channel = ch;
-        cur_off = lo * c.esize;
-        cur_n = (hi - lo) * c.esize;
+        begin_piece(b, ch, lo * c.esize, (hi - lo) * c.esize);
         int k = ks[b];
         Loc src = send_loc(pr.root);
         if (k == pr.root) {
@@ -282,10 +322,7 @@ struct Builder {
       for (int ch = 0; ch < m; ++ch) {
         unsigned long long lo = bd[b * m + ch], hi = bd[b * m + ch + 1];
         if (hi <= lo) continue;
-        cur_branch = b;
-        cur_channel = ch;
-        cur_off = lo * c.esize;
-        cur_n = (hi - lo) * c.esize;
+        begin_piece(b, ch, lo * c.esize, (hi - lo) * c.esize);
         int k = ks[b];
         Loc fin = recv_loc(pr.root);
         if (k == pr.root) {
@@ -426,6 +463,7 @@ static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevel
     if (B.steps.size() > 0xFFFFFFF0ull) return fail(c, HICCL_ERR_NOMEM, "too many steps");
   }
   while (e_seen < c->epochs) epoch_first[++e_seen] = (uint32_t)B.steps.size();
+  B.layout_relays();
   fence_edges(B, epoch_first);
 
   const size_t N = B.steps.size();
@@ -502,8 +540,16 @@ static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevel
   // slot has no internal dependencies, so any order inside it is valid
   std::vector<uint32_t> order(N);
   std::iota(order.begin(), order.end(), 0u);
+  // (inside a slot: primitive, branch, tree position, channel -- so the same
+  // step of adjacent channels is adjacent and can move as one range)
   std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
-    return slot[a] != slot[b] ? slot[a] < slot[b] : klass[a] < klass[b];
+    if (slot[a] != slot[b]) return slot[a] < slot[b];
+    if (klass[a] != klass[b]) return klass[a] < klass[b];
+    const HStep &x = B.steps[a], &y = B.steps[b];
+    if (x.prim != y.prim) return x.prim < y.prim;
+    if (x.branch != y.branch) return x.branch < y.branch;
+    if (x.local != y.local) return x.local < y.local;
+    return x.channel < y.channel;
   });
   std::vector<uint32_t> pos(N);
   for (size_t k = 0; k < N; ++k) pos[order[k]] = (uint32_t)k;
@@ -600,6 +646,36 @@ static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevel
     }
   }
   close_item();
+
+  // runs: within an item, entries whose steps have the same shape and whose
+  // every operand continues the previous step's in memory move as one range
+  plan.run_off.push_back(0);
+  auto same_loc = [&](const Loc &a, const Loc &b, unsigned long long shift) {
+    return a.scratch == b.scratch && a.addr + shift == b.addr;
+  };
+  for (size_t it = 0; it + 1 < plan.item_off.size(); ++it) {
+    const uint32_t e0 = plan.item_off[it], e1 = plan.item_off[it + 1];
+    for (uint32_t e = e0; e < e1; ++e) {
+      const DevEntry &en = plan.entries[e];
+      const HStep &st = plan.steps[en.step];
+      const unsigned long long lo = en.seg_lo * SEGB;
+      const unsigned long long hi = std::min<unsigned long long>(st.nbytes, (unsigned long long)en.seg_hi * SEGB);
+      bool extend = false;
+      if (e > e0 && plan.runs.size() > plan.run_off.back()) {
+        const DevEntry &pe = plan.entries[e - 1];
+        const HStep &ps = plan.steps[pe.step];
+        if (pe.step != en.step && en.seg_lo == 0 && (unsigned long long)pe.seg_hi * SEGB >= ps.nbytes &&
+            ps.kind == st.kind && ps.nsrc == st.nsrc && ps.ndst == st.ndst) {
+          extend = true;
+          for (uint32_t k = 0; k < st.nsrc + st.ndst && extend; ++k)
+            extend = same_loc(plan.locs[ps.loc0 + k], plan.locs[st.loc0 + k], ps.nbytes);
+        }
+      }
+      if (extend) plan.runs.back().bytes += hi - lo;
+      else plan.runs.push_back(DevRun{e - e0, 0, lo, hi - lo});
+    }
+    plan.run_off.push_back((uint32_t)plan.runs.size());
+  }
 
   // accounting
   plan.level_bytes.assign(h.size(), 0);
@@ -790,10 +866,12 @@ hiccl_status_t hiccl_plan_info(hiccl_comm_t c, hiccl_plan_info_t *out) {
   out->edges = p.succ.size();
   out->stages = p.stages;
   out->slots = p.slots;
+  out->runs = p.runs.size();
   out->scratch_bytes = p.scratch_bytes;
   unsigned long long N = p.steps.size();
   out->table_bytes = N * (8 + 4 * 5 + 16) + 4 + p.succ.size() * 4 + p.locs.size() * 8 +
-                     p.entries.size() * sizeof(DevEntry) + p.item_off.size() * 4 + sizeof(DevCtl);
+                     p.entries.size() * sizeof(DevEntry) + p.item_off.size() * 8 +
+                     p.runs.size() * sizeof(DevRun) + sizeof(DevCtl);
   return HICCL_OK;
 }
 

@@ -345,6 +345,9 @@ struct ItemBuf {
   uint32_t nent;
   uint32_t end;                             // no more items: leave the loop
   unsigned long long item;                  // ticket of the staged item
+  DevRun run[MAX_ENTRIES_PER_ITEM];         // data ranges (runs of contiguous entries)
+  uint32_t rpre[MAX_ENTRIES_PER_ITEM + 1];  // prefix sums of the runs' segment counts
+  uint32_t nrun;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -415,17 +418,18 @@ struct SegRef {
 };
 template <typename Buf>
 __device__ __forceinline__ SegRef seg_of(const Buf &B, uint32_t j, unsigned long long segb) {
-  uint32_t k = 0, hi = B.nent;   // largest k with pre[k] <= j
+  uint32_t k = 0, hi = B.nrun;   // largest k with rpre[k] <= j
   while (hi - k > 1) {
     const uint32_t mid = (k + hi) >> 1;
-    if (B.pre[mid] <= j) k = mid;
+    if (B.rpre[mid] <= j) k = mid;
     else hi = mid;
   }
   SegRef r;
-  r.k = k;
-  const unsigned long long seg = B.ent[k].seg_lo + (j - B.pre[k]);
-  r.lo = seg * segb;
-  r.n = (uint32_t)min(segb, B.nb[k] - r.lo);
+  const DevRun &run = B.run[k];
+  r.k = run.entry;
+  const unsigned long long s = j - B.rpre[k];
+  r.lo = run.off + s * segb;
+  r.n = (uint32_t)min(segb, run.bytes - s * segb);
   return r;
 }
 
@@ -522,6 +526,36 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
           B.pre[0] = 0;
           B.nent = ne;
         }
+        {   // the item's runs and the prefix sums of their segment counts
+          const uint32_t r0 = ldg_ro(T.run_off + item), nr = ldg_ro(T.run_off + item + 1) - r0;
+          uint32_t rc[2] = {0, 0};
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t x = lane + 32 * h;
+            if (x < nr) {
+              const DevRun rn = T.runs[r0 + x];
+              B.run[x] = rn;
+              rc[h] = (uint32_t)((rn.bytes + T.seg - 1) / T.seg);
+            }
+          }
+          uint32_t i0 = rc[0], i1 = rc[1];
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v0 = __shfl_up_sync(0xffffffffu, i0, o);
+            const uint32_t v1 = __shfl_up_sync(0xffffffffu, i1, o);
+            if (lane >= o) {
+              i0 += v0;
+              i1 += v1;
+            }
+          }
+          const uint32_t hf = __shfl_sync(0xffffffffu, i0, 31);
+          if (lane < (int)nr) B.rpre[lane + 1] = i0;
+          if (lane + 32 < (int)nr) B.rpre[lane + 33] = hf + i1;
+          if (lane == 0) {
+            B.rpre[0] = 0;
+            B.nrun = nr;
+          }
+        }
         bool bad = false;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -614,7 +648,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
       return meta_op(X.meta[0]) == OP_REDUCE && meta_aligned(X.meta[0]) != 0 && meta_nsrc(X.meta[0]) <= TMA_MAX_FANIN;
     };
     auto mine = [&](const ItemBuf &X) {
-      const uint32_t total = X.pre[X.nent];
+      const uint32_t total = X.rpre[X.nrun];
       return total > (uint32_t)dw ? (total - dw + D - 1) / D : 0u;
     };
     auto issue = [&](const ItemBuf &X, uint32_t i, uint32_t at) {   // segment i of X into load number `at`
@@ -636,7 +670,6 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         break;
       }
       if (B.end) break;
-      const uint32_t total = B.pre[B.nent];
       if (is_tma(B)) {
         const uint32_t nm = mine(B);
         bool stalled = false;
@@ -782,19 +815,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         if (__any_sync(0xffffffffu, stalled)) break;
         __syncwarp();
       } else {
-        uint32_t k = 0;
-        for (uint32_t j = dw; j < total; j += D) {
-          while (B.pre[k + 1] <= j) ++k;
-          const unsigned long long seg = B.ent[k].seg_lo + (j - B.pre[k]);
-          const unsigned long long lo = seg * T.seg;
-          const uint32_t n = (uint32_t)min(T.seg, B.nb[k] - lo);
-          const uint32_t meta = B.meta[k];
+        const uint32_t rtotal = B.rpre[B.nrun];
+        for (uint32_t j = dw; j < rtotal; j += D) {
+          const SegRef g = seg_of(B, j, T.seg);
+          const uint32_t meta = B.meta[g.k];
           const uint32_t np = meta_nsrc(meta) + meta_ndst(meta);
-          const unsigned long long *ptrs = np <= PMAX ? B.ptr[k] : T.ptrs + B.poff[k];
+          const unsigned long long *ptrs = np <= PMAX ? B.ptr[g.k] : T.ptrs + B.poff[g.k];
           if (meta_op(meta) == OP_COPY)
-            warp_copy(ptrs, meta_ndst(meta), lo, n, meta_aligned(meta), lane);
+            warp_copy(ptrs, meta_ndst(meta), g.lo, g.n, meta_aligned(meta), lane);
           else
-            warp_reduce(ptrs, meta_nsrc(meta), meta_dtype(meta), lo, n, meta_aligned(meta), lane);
+            warp_reduce(ptrs, meta_nsrc(meta), meta_dtype(meta), g.lo, g.n, meta_aligned(meta), lane);
         }
       }
       mbar_arrive(&done_bar[b]);
@@ -916,7 +946,8 @@ hiccl_status_t dev_upload(hiccl_comm *c) {
   const size_t o_nbytes = place(N * 8), o_meta = place(N * 4), o_ptroff = place(N * 4), o_indeg = place(N * 4),
                o_nent = place(N * 4), o_succoff = place((N + 1) * 4), o_succ = place(p.succ.size() * 4),
                o_ptrs = place(ptrs.size() * 8), o_ent = place(p.entries.size() * sizeof(DevEntry)),
-               o_item = place(p.item_off.size() * 4);
+               o_item = place(p.item_off.size() * 4), o_runs = place(p.runs.size() * sizeof(DevRun)),
+               o_runoff = place(p.run_off.size() * 4);
   std::vector<char> img(std::max<size_t>(off, 256), 0);
   auto put = [&](size_t o, const void *src, size_t bytes) {
     if (bytes) std::memcpy(img.data() + o, src, bytes);
@@ -931,6 +962,8 @@ hiccl_status_t dev_upload(hiccl_comm *c) {
   put(o_ptrs, ptrs.data(), ptrs.size() * 8);
   put(o_ent, p.entries.data(), p.entries.size() * sizeof(DevEntry));
   put(o_item, p.item_off.data(), p.item_off.size() * 4);
+  put(o_runs, p.runs.data(), p.runs.size() * sizeof(DevRun));
+  put(o_runoff, p.run_off.data(), p.run_off.size() * 4);
   if ((e = cudaMalloc(&d->table, img.size())) != cudaSuccess) {
     cudaGetLastError();
     return fail(c, HICCL_ERR_NOMEM, "step table: " + std::string(cudaGetErrorString(e)));
@@ -965,6 +998,8 @@ hiccl_status_t dev_upload(hiccl_comm *c) {
   t.ptrs = reinterpret_cast<const unsigned long long *>(tb + o_ptrs);
   t.entries = reinterpret_cast<const DevEntry *>(tb + o_ent);
   t.item_off = reinterpret_cast<const uint32_t *>(tb + o_item);
+  t.runs = reinterpret_cast<const DevRun *>(tb + o_runs);
+  t.run_off = reinterpret_cast<const uint32_t *>(tb + o_runoff);
   t.dep = reinterpret_cast<unsigned long long *>(cb);
   t.done = reinterpret_cast<unsigned long long *>(cb + N * 8);
   t.ctl = reinterpret_cast<DevCtl *>(cb + N * 16);
@@ -1131,6 +1166,7 @@ extern "C" hiccl_status_t hiccl_run_static(hiccl_comm_t c, void *stream) {
                            o_ptroff = place(N * 4), o_indeg = place(N * 4), o_nent = place(N * 4),
                            o_succoff = place((N + 1) * 4), o_succ = place(NS * 4), o_ptrs = place(NL * 8),
                            o_ent = place(NE * sizeof(DevEntry)), o_item = place((NI + 1) * 4),
+                           o_runs = place(p.runs.size() * sizeof(DevRun)), o_runoff = place((NI + 1) * 4),
                            o_ctr = place(N * 16 + sizeof(DevCtl) + 8), o_relay = place(p.scratch_bytes);
   if (off > HICCL_STATIC_ARENA_BYTES) return HICCL_ERR_TOO_LARGE;
 
@@ -1160,6 +1196,8 @@ extern "C" hiccl_status_t hiccl_run_static(hiccl_comm_t c, void *stream) {
   if (e == cudaSuccess) e = h2d(o_succ, p.succ.data(), NS * 4);
   if (e == cudaSuccess) e = h2d(o_ent, p.entries.data(), NE * sizeof(DevEntry));
   if (e == cudaSuccess) e = h2d(o_item, p.item_off.data(), (NI + 1) * 4);
+  if (e == cudaSuccess) e = h2d(o_runs, p.runs.data(), p.runs.size() * sizeof(DevRun));
+  if (e == cudaSuccess) e = h2d(o_runoff, p.run_off.data(), (NI + 1) * 4);
   // every call starts from zeroed counters: the arena keeps the last call's contents
   if (e == cudaSuccess) e = cudaMemsetAsync(base + o_ctr, 0, N * 16 + sizeof(DevCtl) + 8, s);
   if (e != cudaSuccess) return HICCL_ERR_CUDA;
@@ -1183,6 +1221,8 @@ extern "C" hiccl_status_t hiccl_run_static(hiccl_comm_t c, void *stream) {
   t.ptrs = reinterpret_cast<const unsigned long long *>(base + o_ptrs);
   t.entries = reinterpret_cast<const DevEntry *>(base + o_ent);
   t.item_off = reinterpret_cast<const uint32_t *>(base + o_item);
+  t.runs = reinterpret_cast<const DevRun *>(base + o_runs);
+  t.run_off = reinterpret_cast<const uint32_t *>(base + o_runoff);
   t.dep = reinterpret_cast<unsigned long long *>(base + o_ctr);
   t.done = reinterpret_cast<unsigned long long *>(base + o_ctr + N * 8);
   t.ctl = reinterpret_cast<DevCtl *>(base + o_ctr + N * 16);

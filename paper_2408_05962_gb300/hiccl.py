@@ -49,7 +49,7 @@ class HicclError(RuntimeError):
 class PlanInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_ulonglong) for n in
                 ("steps", "copy_steps", "reduce_steps", "items", "edges", "stages",
-                 "scratch_bytes", "table_bytes", "slots")]
+                 "scratch_bytes", "table_bytes", "slots", "runs")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
