@@ -135,6 +135,25 @@ hiccl_status_t hiccl_start(hiccl_comm_t comm, void *cuda_stream);
  * HICCL_ERR_CUDA on a CUDA error. */
 hiccl_status_t hiccl_wait(hiccl_comm_t comm);
 
+/* ---- batched execution ---------------------------------------------------------- */
+
+/* One communicator whose program is the union of the programs of `n` planned
+ * communicators (hiccl_plan or hiccl_init), executed by one persistent launch
+ * per hiccl_start: their steps share one ticket order, interleaved by
+ * dependency depth so that the short early levels of one collective overlap
+ * the bulk of another.  The members keep their own state; the group copies
+ * their plans, allocates its own table, counters and relay buffers on the
+ * current device, and references the members' user buffers (which must stay
+ * valid).  Start, wait, hbm_bytes, plan_info, trace and destroy apply;
+ * hiccl_level_bytes does not (query the members).  FP8 members cannot be
+ * grouped with other payloads (HICCL_ERR_UNSUPPORTED).
+ *
+ * hiccl_start of any communicator may be recorded in a CUDA graph: under
+ * stream capture it records only the executor launch (no state change), each
+ * replay is a complete execution (the dependency counters re-arm on the
+ * device), and the caller synchronizes replays on its stream. */
+hiccl_status_t hiccl_group(const hiccl_comm_t *comms, int n, hiccl_comm_t *out);
+
 /* ---- accounting -------------------------------------------------------------- */
 
 /* Bytes that cross each hierarchy level per execution: for every copy

@@ -118,7 +118,7 @@ struct HStep {
   uint32_t ndst;
   unsigned long long slot;
   uint32_t local;          // emission index inside its piece (same tree position in every channel)
-  uint32_t pad2;
+  uint32_t dtype;          // payload type of the step's communicator
 };
 
 struct Prim {
@@ -162,6 +162,7 @@ struct hiccl_comm {
   int epochs = 1;
   std::vector<hiccl::Prim> prims;
   enum State { COMPOSING, PLANNED, READY, RUNNING } state = COMPOSING;
+  bool group = false;   // built by hiccl_group from other communicators' plans
   // options
   unsigned long long timeout_ns = 1000000000ull;
   int ctas_per_sm = 2;

@@ -933,7 +933,7 @@ hiccl_status_t dev_upload(hiccl_comm *c) {
     indeg[i] = p.pred_off[i + 1] - p.pred_off[i];
     bool al = true;
     for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k) al = al && (ptrs[st.loc0 + k] % 16 == 0);
-    meta[i] = meta_pack(st.kind, (uint32_t)c->dtype, al ? 1u : 0u, st.nsrc, st.ndst);
+    meta[i] = meta_pack(st.kind, st.dtype, al ? 1u : 0u, st.nsrc, st.ndst);
   }
 
   // one allocation for all read-only arrays
@@ -1032,7 +1032,9 @@ hiccl_status_t hiccl_start(hiccl_comm_t c, void *stream) {
   if (c->state != hiccl_comm::READY || !c->dev) return fail(c, HICCL_ERR_STATE, "start before init");
   DevState *d = c->dev;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  *d->host_err = 0;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaStreamIsCapturing");
+  if (cap == cudaStreamCaptureStatusNone) *d->host_err = 0;
   DevTable t = d->t;
   t.timeout_ns = c->timeout_ns;
   if (t.nitems > 0) {
@@ -1044,6 +1046,10 @@ hiccl_status_t hiccl_start(hiccl_comm_t c, void *stream) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "executor launch");
   }
+  // under stream capture only the launch is recorded: each replay of the
+  // graph is a complete start (counters re-arm themselves on the device);
+  // the caller synchronizes the graph launch on its stream
+  if (cap != cudaStreamCaptureStatusNone) return HICCL_OK;
   cudaError_t e = cudaEventRecord(d->done_ev, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
   c->state = hiccl_comm::RUNNING;
@@ -1142,7 +1148,7 @@ __global__ void hiccl_static_expand(const HStep *steps, const Loc *locs, const u
     nbytes[i] = st.nbytes;
     ptr_off[i] = st.loc0;
     indeg[i] = pred_off[i + 1] - pred_off[i];
-    meta[i] = meta_pack(st.kind, dtype, al ? 1u : 0u, st.nsrc, st.ndst);
+    meta[i] = meta_pack(st.kind, st.dtype, al ? 1u : 0u, st.nsrc, st.ndst);
   }
 }
 

@@ -92,6 +92,7 @@ _SIGS = {
     "hiccl_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong]),
     "hiccl_debug_withhold": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_int]),
     "hiccl_run_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hiccl_group": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "hiccl_get_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_size_t,
                                        ctypes.POINTER(ctypes.c_size_t)]),
     "hiccl_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -261,6 +262,16 @@ def hiccl_get_trace(comm, nitems: int):
     return [tuple(v[i:i + 5]) for i in range(0, len(v), 5)]
 
 
+def hiccl_group(comms: Sequence) -> int:
+    """A communicator running the given planned communicators in one launch."""
+    arr = (ctypes.c_void_p * len(comms))(*[c.handle if isinstance(c, Comm) else c for c in comms])
+    out = ctypes.c_void_p()
+    st = lib().hiccl_group(arr, len(comms), ctypes.byref(out))
+    if st != OK:
+        raise HicclError(st, "hiccl_group")
+    return out.value
+
+
 def hiccl_last_error(comm) -> str:
     return lib().hiccl_last_error(comm).decode()
 
@@ -274,11 +285,16 @@ def hiccl_destroy(comm):
 class Comm:
     """A communicator (the paper's persistent ``Comm<T>``, Listing 2)."""
 
-    def __init__(self, nranks: int, dtype: int | str = "f32"):
+    def __init__(self, nranks: int, dtype: int | str = "f32", _handle=None):
         self.P = int(nranks)
         self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
-        self.handle = hiccl_create(self.P, self.dtype)
+        self.handle = _handle if _handle is not None else hiccl_create(self.P, self.dtype)
         self.nlevels = None
+
+    @classmethod
+    def group(cls, comms: Sequence["Comm"]) -> "Comm":
+        """One communicator executing all of ``comms`` in a single launch."""
+        return cls(comms[0].P, comms[0].dtype, _handle=hiccl_group(comms))
 
     def add_multicast(self, send, recv, count, root, leaves):
         hiccl_add_multicast(self.handle, send, recv, count, root, list(leaves), self.P)
