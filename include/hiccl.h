@@ -135,6 +135,29 @@ hiccl_status_t hiccl_start(hiccl_comm_t comm, void *cuda_stream);
  * HICCL_ERR_CUDA on a CUDA error. */
 hiccl_status_t hiccl_wait(hiccl_comm_t comm);
 
+/* ---- autotuning ------------------------------------------------------------------- */
+
+typedef struct {
+  int stripe;                     /* chosen s                                    */
+  int pipeline;                   /* chosen m                                    */
+  int order;                      /* HICCL_OPT_ORDER value                       */
+  int threads;                    /* HICCL_OPT_THREADS value                     */
+  unsigned long long item_bytes;  /* HICCL_OPT_ITEM_BYTES value                  */
+  float us;                       /* median time of one start, microseconds      */
+  int trials;                     /* configurations timed                        */
+} hiccl_tune_t;
+
+/* Pick the fastest configuration of an initialized communicator by timing it
+ * on `cuda_stream` (each candidate: re-plan, upload, one warm-up and three
+ * timed runs, median of CUDA-event times): executor knobs (work order, item
+ * size) always; with (flags & 1) first the stripe s (its current value, 1,
+ * and the bottom hierarchy factor) and pipeline depth m (1, 2, 4, 8), the
+ * paper's optimization parameters (Sec. 4.1), with the executor defaults.
+ * The communicator ends up initialized with the best configuration, which
+ * *best receives (may be NULL).  The trials execute the collective: receive
+ * buffers are overwritten.  Blocking. */
+hiccl_status_t hiccl_autotune(hiccl_comm_t comm, void *cuda_stream, int flags, hiccl_tune_t *best);
+
 /* ---- batched execution ---------------------------------------------------------- */
 
 /* One communicator whose program is the union of the programs of `n` planned

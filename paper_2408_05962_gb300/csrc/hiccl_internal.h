@@ -178,6 +178,8 @@ struct hiccl_comm {
 
 namespace hiccl {
 hiccl_status_t fail(hiccl_comm *c, hiccl_status_t st, const std::string &msg);
+// factorize c's program again (hiccl_plan.cpp), keeping c's state
+hiccl_status_t replan(hiccl_comm *c, const std::vector<int> &hierarchy, int stripe, int pipeline);
 // runtime entry points (hiccl_runtime.cu)
 hiccl_status_t dev_upload(hiccl_comm *c);
 void dev_release(hiccl_comm *c);

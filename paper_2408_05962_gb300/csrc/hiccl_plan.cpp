@@ -706,6 +706,10 @@ static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevel
   return HICCL_OK;
 }
 
+hiccl_status_t replan(hiccl_comm *c, const std::vector<int> &hierarchy, int stripe, int pipeline) {
+  return build_plan(c, hierarchy.data(), (int)hierarchy.size(), stripe, pipeline);
+}
+
 }  // namespace hiccl
 
 // ============================================================================

@@ -248,6 +248,18 @@ __device__ __forceinline__ void warp_copy(const unsigned long long *ptrs, uint32
     }
     done = nvec << 4;
   }
+  if (!aligned) {   // 4-byte words when every operand allows them
+    bool w4 = (reinterpret_cast<uintptr_t>(src) & 3u) == 0;
+    for (uint32_t k = 0; k < ndst; ++k) w4 = w4 && ((ptrs[1 + k] + lo) & 3u) == 0;
+    if (w4) {
+      const uint32_t nw = n >> 2;
+      for (uint32_t i = lane; i < nw; i += 32) {
+        const unsigned int v = __ldcg(reinterpret_cast<const unsigned int *>(src) + i);
+        for (uint32_t k = 0; k < ndst; ++k) reinterpret_cast<unsigned int *>(reinterpret_cast<char *>(ptrs[1 + k]) + lo)[i] = v;
+      }
+      done = nw << 2;
+    }
+  }
   for (uint32_t b = done + lane; b < n; b += 32) {
     const char v = __ldcg(src + b);
     for (uint32_t k = 0; k < ndst; ++k) (reinterpret_cast<char *>(ptrs[1 + k]) + lo)[b] = v;
@@ -1075,6 +1087,88 @@ hiccl_status_t hiccl_wait(hiccl_comm_t c) {
     if (code == ERR_STALL) return fail(c, HICCL_ERR_TIMEOUT, "an executor pipeline wait timed out");
     return fail(c, HICCL_ERR_CUDA, "executor error " + std::to_string(code));
   }
+  return HICCL_OK;
+}
+
+hiccl_status_t hiccl_autotune(hiccl_comm_t c, void *stream, int flags, hiccl_tune_t *best) {
+  if (!c) return HICCL_ERR_INVALID;
+  if (c->group) return fail(c, HICCL_ERR_UNSUPPORTED, "tune the members, then group them");
+  if (c->state != hiccl_comm::READY || !c->dev) return fail(c, HICCL_ERR_STATE, "needs an idle initialized communicator");
+  const std::vector<int> h = c->plan.hierarchy;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(c, cudaGetLastError(), "cudaEventCreate");
+  }
+  hiccl_tune_t cur{c->plan.stripe, c->plan.pipeline, c->order, c->threads, c->item_bytes, 0.f, 0};
+  hiccl_tune_t top = cur;
+  top.us = 3.4e38f;
+  int trials = 0;
+  // time one configuration; the communicator is left initialized with it
+  auto trial = [&](const hiccl_tune_t &k, float &us) -> hiccl_status_t {
+    c->order = k.order;
+    c->item_bytes = k.item_bytes;
+    c->threads = k.threads;
+    hiccl_status_t st = replan(c, h, k.stripe, k.pipeline);
+    if (st != HICCL_OK) return st;
+    if ((st = dev_upload(c)) != HICCL_OK) return st;
+    c->state = hiccl_comm::READY;
+    float ts[4];
+    for (int r = 0; r < 4; ++r) {
+      cudaEventRecord(e0, s);
+      if ((st = hiccl_start(c, s)) != HICCL_OK) return st;
+      cudaEventRecord(e1, s);
+      if ((st = hiccl_wait(c)) != HICCL_OK) return st;
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ts[r], e0, e1);
+    }
+    std::sort(ts + 1, ts + 4);   // run 0 is the warm-up
+    us = ts[2] * 1000.f;
+    ++trials;
+    return HICCL_OK;
+  };
+  auto consider = [&](hiccl_tune_t k) -> hiccl_status_t {
+    float us = 0.f;
+    hiccl_status_t st = trial(k, us);
+    if (st != HICCL_OK) return st;
+    k.us = us;
+    if (us < top.us) top = k;
+    return HICCL_OK;
+  };
+  hiccl_status_t st = HICCL_OK;
+  if (flags & 1) {   // the paper's stripe and pipeline parameters first
+    std::vector<int> ss{cur.stripe, 1};
+    if (!h.empty() && h.back() > 1 && h.back() <= c->P) ss.push_back(h.back());
+    std::sort(ss.begin(), ss.end());
+    ss.erase(std::unique(ss.begin(), ss.end()), ss.end());
+    for (int sv : ss)
+      for (int mv : {1, 2, 4, 8}) {
+        hiccl_tune_t k = cur;
+        k.stripe = sv;
+        k.pipeline = mv;
+        if (st == HICCL_OK) st = consider(k);
+      }
+  } else if (st == HICCL_OK) {
+    st = consider(cur);
+  }
+  const hiccl_tune_t base = top;
+  for (int order : {1, 0})
+    for (unsigned long long ib : {32768ull, 65536ull, 131072ull}) {
+      hiccl_tune_t k = base;
+      k.order = order;
+      k.item_bytes = ib;
+      if (st == HICCL_OK && !(order == base.order && ib == base.item_bytes)) st = consider(k);
+    }
+  if (st == HICCL_OK) {
+    float us = 0.f;
+    st = trial(top, us);   // leave the communicator on the best configuration
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != HICCL_OK) return st;
+  top.trials = trials;
+  if (best) *best = top;
   return HICCL_OK;
 }
 

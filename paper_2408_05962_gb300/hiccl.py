@@ -55,6 +55,15 @@ class PlanInfo(ctypes.Structure):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("stripe", ctypes.c_int), ("pipeline", ctypes.c_int), ("order", ctypes.c_int),
+                ("threads", ctypes.c_int), ("item_bytes", ctypes.c_ulonglong), ("us", ctypes.c_float),
+                ("trials", ctypes.c_int)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 class StepDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("level", ctypes.c_int), ("nsrc", ctypes.c_int),
                 ("ndst", ctypes.c_int), ("npreds", ctypes.c_int), ("prim", ctypes.c_int),
@@ -92,6 +101,7 @@ _SIGS = {
     "hiccl_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong]),
     "hiccl_debug_withhold": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_int]),
     "hiccl_run_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hiccl_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(TuneResult)]),
     "hiccl_group": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "hiccl_get_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_size_t,
                                        ctypes.POINTER(ctypes.c_size_t)]),
@@ -262,6 +272,14 @@ def hiccl_get_trace(comm, nitems: int):
     return [tuple(v[i:i + 5]) for i in range(0, len(v), 5)]
 
 
+def hiccl_autotune(comm, stream=None, flags: int = 0) -> dict:
+    """Time candidate configurations and keep the fastest (see the header)."""
+    s = _stream_handle(stream)
+    r = TuneResult()
+    _check(comm, lib().hiccl_autotune(comm, ctypes.c_void_p(s) if s else None, int(flags), ctypes.byref(r)))
+    return r.as_dict()
+
+
 def hiccl_group(comms: Sequence) -> int:
     """A communicator running the given planned communicators in one launch."""
     arr = (ctypes.c_void_p * len(comms))(*[c.handle if isinstance(c, Comm) else c for c in comms])
@@ -333,6 +351,9 @@ class Comm:
 
     def steps(self):
         return [self.step(i) for i in range(self.plan_info()["steps"])]
+
+    def autotune(self, stream=None, tune_method: bool = False):
+        return hiccl_autotune(self.handle, stream, 1 if tune_method else 0)
 
     def trace(self):
         return hiccl_get_trace(self.handle, self.plan_info()["items"])

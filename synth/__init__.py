@@ -61,7 +61,8 @@ def batch_mix(n: int = 256, seed: int = 0, min_bytes: int = 4096, max_bytes: int
               ranks=(8, 16, 32), kinds=("allgather", "reducescatter", "allreduce"),
               dtypes=("f32", "bf16")) -> list[dict]:
     """A list of n collective descriptions: kind, P, two-level hierarchy,
-    per-rank bytes (log-uniform, rounded to a multiple of 4*P bytes), dtype."""
+    per-rank bytes (log-uniform, rounded to a multiple of 16*P bytes so that
+    every per-rank chunk starts on a 16-byte boundary), dtype."""
     g = rng(seed)
     out = []
     for _ in range(n):
@@ -69,7 +70,7 @@ def batch_mix(n: int = 256, seed: int = 0, min_bytes: int = 4096, max_bytes: int
         hs = _TWO_LEVEL[P]
         h = hs[int(g.integers(0, len(hs)))]
         b = float(np.exp(g.uniform(np.log(min_bytes), np.log(max_bytes))))
-        quantum = 4 * P
+        quantum = 16 * P
         nbytes = max(quantum, int(b) // quantum * quantum)
         out.append({
             "kind": str(kinds[int(g.integers(0, len(kinds)))]),
@@ -97,7 +98,7 @@ def poisson_requests(rate_hz: float, duration_s: float, seed: int = 0,
             break
         P = int(g.choice(ranks))
         b = float(np.exp(g.uniform(np.log(min_bytes), np.log(max_bytes))))
-        quantum = 4 * P
+        quantum = 16 * P
         nbytes = max(quantum, int(b) // quantum * quantum)
         out.append({
             "t": t,
