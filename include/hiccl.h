@@ -99,6 +99,27 @@ hiccl_status_t hiccl_add_reduction(hiccl_comm_t comm, const void *const *send,
  * write-after-read, write-after-write).  It is not a barrier. */
 hiccl_status_t hiccl_add_fence(hiccl_comm_t comm);
 
+/* Standard collectives of Table 2 (Sec. 3.2-3.3), registered natively as the
+ * primitives the paper composes them from. */
+typedef enum {
+  HICCL_BROADCAST = 0,       /* M(root, U, dp)                          send dp, recv dp */
+  HICCL_REDUCE = 1,          /* R(U, root, dp)                          send dp, recv dp */
+  HICCL_ALLGATHER = 2,       /* sum_i M(i, U, d)                        send d,  recv dp */
+  HICCL_REDUCESCATTER = 3,   /* sum_j R(U, j, d)                        send dp, recv d  */
+  HICCL_ALLREDUCE = 4,       /* Listing 2: RS, fence, in-place AG       send dp, recv dp */
+  HICCL_SCATTER = 5,         /* sum_j R(root, j, d)                     send dp, recv d  */
+  HICCL_GATHER = 6,          /* sum_i M(i, root, d)                     send d,  recv dp */
+  HICCL_ALLTOALL = 7,        /* sum_i sum_j M(i, j, d)                  send dp, recv dp */
+  HICCL_ALLREDUCE_SINGLE = 8 /* sum_j R(U, j, dp) (single step)         send dp, recv dp */
+} hiccl_collective_t;
+
+/* Register collective `kind` over chunk length d (elements; d*P is the largest
+ * per-rank buffer, Sec. 3.2) for per-rank buffers send[r], recv[r] (arrays of
+ * nranks device pointers laid out as in the table above).  Same ownership,
+ * state and error rules as hiccl_add_multicast / hiccl_add_reduction. */
+hiccl_status_t hiccl_add_collective(hiccl_comm_t comm, hiccl_collective_t kind, size_t d,
+                                    const void *const *send, void *const *recv, int root);
+
 /* ---- optimization (Sec. 4) -------------------------------------------------- */
 
 /* Factorize the registered program and upload it to the current device

@@ -821,6 +821,97 @@ hiccl_status_t hiccl_add_fence(hiccl_comm_t c) {
   return HICCL_OK;
 }
 
+hiccl_status_t hiccl_add_collective(hiccl_comm_t c, hiccl_collective_t kind, size_t d, const void *const *send,
+                                    void *const *recv, int root) {
+  if (!c) return HICCL_ERR_INVALID;
+  if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "add after init");
+  if (!send || !recv) return fail(c, HICCL_ERR_INVALID, "null pointer array");
+  const int P = c->P;
+  if (root < 0 || root >= P) return fail(c, HICCL_ERR_INVALID, "root out of range");
+  size_t du = 0;
+  if (!to_units(c, d, du)) return fail(c, HICCL_ERR_INVALID, "FP8 counts must be multiples of 128");
+  const unsigned long long cb = (unsigned long long)du * c->esize;   // bytes of one chunk
+  std::vector<int> all(P), others;
+  for (int r = 0; r < P; ++r) all[r] = r;
+  std::vector<const void *> s(P, nullptr);
+  std::vector<void *> v(P, nullptr);
+  auto sa = [&](int r, unsigned long long k) { return (const void *)((const char *)send[r] + k * cb); };
+  auto ra = [&](int r, unsigned long long k) { return (void *)((char *)recv[r] + k * cb); };
+  auto reset = [&]() {
+    std::fill(s.begin(), s.end(), nullptr);
+    std::fill(v.begin(), v.end(), nullptr);
+  };
+  hiccl_status_t st = HICCL_OK;
+  const size_t dp = d * P;
+  switch (kind) {
+    case HICCL_BROADCAST:
+      return hiccl_add_multicast(c, send, recv, dp, root, all.data(), P);
+    case HICCL_REDUCE:
+      return hiccl_add_reduction(c, send, recv, dp, all.data(), P, root, HICCL_SUM);
+    case HICCL_ALLGATHER:
+      for (int i = 0; i < P && st == HICCL_OK; ++i) {
+        for (int r = 0; r < P; ++r) v[r] = ra(r, i);
+        st = hiccl_add_multicast(c, send, v.data(), d, i, all.data(), P);
+      }
+      return st;
+    case HICCL_REDUCESCATTER:
+      for (int j = 0; j < P && st == HICCL_OK; ++j) {
+        for (int r = 0; r < P; ++r) s[r] = sa(r, j);
+        st = hiccl_add_reduction(c, s.data(), recv, d, all.data(), P, j, HICCL_SUM);
+      }
+      return st;
+    case HICCL_ALLREDUCE_SINGLE:
+      for (int j = 0; j < P && st == HICCL_OK; ++j)
+        st = hiccl_add_reduction(c, send, recv, dp, all.data(), P, j, HICCL_SUM);
+      return st;
+    case HICCL_SCATTER:
+      for (int j = 0; j < P && st == HICCL_OK; ++j) {
+        reset();
+        s[root] = sa(root, j);
+        v[j] = recv[j];
+        st = hiccl_add_reduction(c, s.data(), v.data(), d, &root, 1, j, HICCL_SUM);
+      }
+      return st;
+    case HICCL_GATHER:
+      for (int i = 0; i < P && st == HICCL_OK; ++i) {
+        reset();
+        s[i] = send[i];
+        v[root] = ra(root, i);
+        st = hiccl_add_multicast(c, s.data(), v.data(), d, i, &root, 1);
+      }
+      return st;
+    case HICCL_ALLTOALL:
+      for (int i = 0; i < P && st == HICCL_OK; ++i)
+        for (int j = 0; j < P && st == HICCL_OK; ++j) {
+          reset();
+          s[i] = sa(i, j);
+          v[j] = ra(j, i);
+          st = hiccl_add_multicast(c, s.data(), v.data(), d, i, &j, 1);
+        }
+      return st;
+    case HICCL_ALLREDUCE:
+      for (int j = 0; j < P && st == HICCL_OK; ++j) {
+        reset();
+        for (int r = 0; r < P; ++r) s[r] = sa(r, j);
+        v[j] = ra(j, j);
+        st = hiccl_add_reduction(c, s.data(), v.data(), d, all.data(), P, j, HICCL_SUM);
+      }
+      if (st == HICCL_OK) st = hiccl_add_fence(c);
+      for (int i = 0; i < P && st == HICCL_OK; ++i) {
+        others.clear();
+        for (int r = 0; r < P; ++r)
+          if (r != i) others.push_back(r);
+        for (int r = 0; r < P; ++r) {
+          s[r] = ra(r, i);
+          v[r] = ra(r, i);
+        }
+        st = hiccl_add_multicast(c, s.data(), v.data(), d, i, others.data(), (int)others.size());
+      }
+      return st;
+  }
+  return fail(c, HICCL_ERR_INVALID, "unknown collective");
+}
+
 hiccl_status_t hiccl_plan(hiccl_comm_t c, const int *hierarchy, int nlevels, int stripe, int pipeline) {
   if (!c) return HICCL_ERR_INVALID;
   if (c->state == hiccl_comm::READY || c->state == hiccl_comm::RUNNING)

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cstddef>
 #include <cstring>
 #include <string>
@@ -46,6 +47,8 @@ struct DevState {
   std::vector<uint32_t> indeg;      // host copy, for fault injection
   uint32_t *indeg_dev = nullptr;
   unsigned long long *trace = nullptr;   // [nitems][5] when tracing
+  int err_slot = -1;
+  cudaStream_t upload = nullptr;         // internal stream of the device (not owned)
 };
 
 // ---------------------------------------------------------------------------
@@ -890,6 +893,62 @@ static void exec_launch(int nt, unsigned grid, cudaStream_t s, const DevTable &t
 // host side
 // ---------------------------------------------------------------------------
 
+// ---- process-wide resources, per device -------------------------------------
+// Uploads run on an internal non-blocking stream with stream-ordered
+// allocation, so creating or destroying a communicator never synchronizes the
+// device with kernels other streams are running.  The mapped host error words
+// come from one pinned slab.
+constexpr int MAXDEV = 64;
+struct DeviceRes {
+  std::once_flag once;
+  cudaError_t status = cudaSuccess;
+  cudaStream_t upload = nullptr;
+  int nsm = 0;
+  int occ[4] = {0, 0, 0, 0};
+};
+static DeviceRes g_dev[MAXDEV];
+
+static cudaError_t device_res(int dev, DeviceRes **out) {
+  if (dev < 0 || dev >= MAXDEV) return cudaErrorInvalidDevice;
+  DeviceRes &r = g_dev[dev];
+  std::call_once(r.once, [&]() {
+    cudaError_t e = cudaStreamCreateWithFlags(&r.upload, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&r.nsm, cudaDevAttrMultiProcessorCount, dev);
+    for (int i = 1; i < 4 && e == cudaSuccess; ++i) e = exec_occupancy(64 << i, &r.occ[i]);
+    r.status = e;
+  });
+  *out = &r;
+  return r.status;
+}
+
+constexpr int ERR_SLOTS = 1 << 16;
+static std::mutex g_err_mu;
+static unsigned long long *g_err_host = nullptr, *g_err_dev = nullptr;
+static std::vector<int> g_err_free;
+
+static cudaError_t err_slot(unsigned long long **host, unsigned long long **dev, int *slot) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (!g_err_host) {
+    cudaError_t e = cudaHostAlloc((void **)&g_err_host, ERR_SLOTS * sizeof(unsigned long long), cudaHostAllocMapped);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaHostGetDevicePointer((void **)&g_err_dev, g_err_host, 0)) != cudaSuccess) return e;
+    g_err_free.reserve(ERR_SLOTS);
+    for (int k = ERR_SLOTS - 1; k >= 0; --k) g_err_free.push_back(k);
+  }
+  if (g_err_free.empty()) return cudaErrorMemoryAllocation;
+  *slot = g_err_free.back();
+  g_err_free.pop_back();
+  *host = g_err_host + *slot;
+  *dev = g_err_dev + *slot;
+  **host = 0;
+  return cudaSuccess;
+}
+
+static void err_release(int slot) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (slot >= 0) g_err_free.push_back(slot);
+}
+
 static hiccl_status_t cuda_fail(hiccl_comm *c, cudaError_t e, const char *what) {
   return fail(c, HICCL_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
@@ -899,11 +958,13 @@ void dev_release(hiccl_comm *c) {
   if (!d) return;
   if (c->state == hiccl_comm::RUNNING && d->done_ev) cudaEventSynchronize(d->done_ev);
   if (d->done_ev) cudaEventDestroy(d->done_ev);
-  if (d->table) cudaFree(d->table);
-  if (d->counters) cudaFree(d->counters);
-  if (d->scratch) cudaFree(d->scratch);
-  if (d->host_err) cudaFreeHost(d->host_err);
-  if (d->trace) cudaFree(d->trace);
+  if (d->upload) {   // stream-ordered frees: no device-wide synchronization
+    if (d->table) cudaFreeAsync(d->table, d->upload);
+    if (d->counters) cudaFreeAsync(d->counters, d->upload);
+    if (d->scratch) cudaFreeAsync(d->scratch, d->upload);
+    if (d->trace) cudaFreeAsync(d->trace, d->upload);
+  }
+  err_release(d->err_slot);
   delete d;
   c->dev = nullptr;
 }
@@ -916,20 +977,30 @@ hiccl_status_t dev_upload(hiccl_comm *c) {
   c->dev = d;
   cudaError_t e;
   if ((e = cudaGetDevice(&d->device)) != cudaSuccess) return cuda_fail(c, e, "cudaGetDevice");
-  if ((e = cudaDeviceGetAttribute(&d->nsm, cudaDevAttrMultiProcessorCount, d->device)) != cudaSuccess)
-    return cuda_fail(c, e, "cudaDeviceGetAttribute");
+  DeviceRes *res = nullptr;
+  if ((e = device_res(d->device, &res)) != cudaSuccess) return cuda_fail(c, e, "device set-up");
+  d->nsm = res->nsm;
   for (int i = 1; i < 4; ++i) {
-    if ((e = exec_occupancy(64 << i, &d->occ[i])) != cudaSuccess) return cuda_fail(c, e, "executor occupancy");
+    d->occ[i] = res->occ[i];
     if (d->occ[i] < 1) return fail(c, HICCL_ERR_CUDA, "executor kernel cannot be resident");
   }
+  d->upload = res->upload;
+  cudaStream_t us = d->upload;
+  auto dalloc = [&](void **ptr, size_t bytes, const char *what) -> hiccl_status_t {
+    cudaError_t ee = cudaMallocAsync(ptr, bytes, us);
+    if (ee != cudaSuccess) {
+      cudaGetLastError();
+      *ptr = nullptr;
+      return fail(c, HICCL_ERR_NOMEM, std::string(what) + ": " + cudaGetErrorString(ee));
+    }
+    return HICCL_OK;
+  };
 
   const size_t N = p.steps.size();
   unsigned long long scratch_base = 0;
   if (p.scratch_bytes) {
-    if ((e = cudaMalloc(&d->scratch, p.scratch_bytes)) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(c, HICCL_ERR_NOMEM, "relay buffers: " + std::string(cudaGetErrorString(e)));
-    }
+    hiccl_status_t st = dalloc(&d->scratch, p.scratch_bytes, "relay buffers");
+    if (st != HICCL_OK) return st;
     scratch_base = (unsigned long long)(uintptr_t)d->scratch;
   }
 
@@ -976,24 +1047,22 @@ hiccl_status_t dev_upload(hiccl_comm *c) {
   put(o_item, p.item_off.data(), p.item_off.size() * 4);
   put(o_runs, p.runs.data(), p.runs.size() * sizeof(DevRun));
   put(o_runoff, p.run_off.data(), p.run_off.size() * 4);
-  if ((e = cudaMalloc(&d->table, img.size())) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(c, HICCL_ERR_NOMEM, "step table: " + std::string(cudaGetErrorString(e)));
+  {
+    hiccl_status_t st = dalloc(&d->table, img.size(), "step table");
+    if (st != HICCL_OK) return st;
   }
-  if ((e = cudaMemcpy(d->table, img.data(), img.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((e = cudaMemcpyAsync(d->table, img.data(), img.size(), cudaMemcpyHostToDevice, us)) != cudaSuccess)
     return cuda_fail(c, e, "upload step table");
 
   d->counters_bytes = N * 16 + sizeof(DevCtl);
-  if ((e = cudaMalloc(&d->counters, d->counters_bytes)) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(c, HICCL_ERR_NOMEM, "counters: " + std::string(cudaGetErrorString(e)));
+  {
+    hiccl_status_t st = dalloc(&d->counters, d->counters_bytes, "counters");
+    if (st != HICCL_OK) return st;
   }
-  if ((e = cudaMemset(d->counters, 0, d->counters_bytes)) != cudaSuccess) return cuda_fail(c, e, "cudaMemset");
-  if ((e = cudaHostAlloc((void **)&d->host_err, sizeof(unsigned long long), cudaHostAllocMapped)) != cudaSuccess)
-    return cuda_fail(c, e, "cudaHostAlloc");
-  *d->host_err = 0;
-  if ((e = cudaHostGetDevicePointer((void **)&d->host_err_dev, d->host_err, 0)) != cudaSuccess)
-    return cuda_fail(c, e, "cudaHostGetDevicePointer");
+  if ((e = cudaMemsetAsync(d->counters, 0, d->counters_bytes, us)) != cudaSuccess)
+    return cuda_fail(c, e, "cudaMemsetAsync");
+  if ((e = err_slot(&d->host_err, &d->host_err_dev, &d->err_slot)) != cudaSuccess)
+    return cuda_fail(c, e, "error word");
   if ((e = cudaEventCreateWithFlags(&d->done_ev, cudaEventDisableTiming)) != cudaSuccess)
     return cuda_fail(c, e, "cudaEventCreate");
 
@@ -1021,12 +1090,12 @@ hiccl_status_t dev_upload(hiccl_comm *c) {
   t.seg = p.seg;
   t.trace = nullptr;
   if (c->trace && t.nitems) {
-    if ((e = cudaMalloc(&d->trace, t.nitems * 5 * sizeof(unsigned long long))) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(c, HICCL_ERR_NOMEM, "trace buffer");
-    }
+    hiccl_status_t st = dalloc((void **)&d->trace, t.nitems * 5 * sizeof(unsigned long long), "trace buffer");
+    if (st != HICCL_OK) return st;
     t.trace = d->trace;
   }
+  // the uploads must have landed before the first start (on any stream)
+  if ((e = cudaStreamSynchronize(us)) != cudaSuccess) return cuda_fail(c, e, "upload");
   d->indeg = std::move(indeg);
   d->indeg_dev = reinterpret_cast<uint32_t *>(tb + o_indeg);
   return HICCL_OK;
@@ -1078,7 +1147,8 @@ hiccl_status_t hiccl_wait(hiccl_comm_t c) {
   const unsigned long long err = *(volatile unsigned long long *)d->host_err;
   if (err) {
     // the aborted launch left the counters mid-way: re-arm everything
-    cudaError_t e2 = cudaMemset(d->counters, 0, d->counters_bytes);
+    cudaError_t e2 = cudaMemsetAsync(d->counters, 0, d->counters_bytes, d->upload);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(d->upload);
     if (e2 != cudaSuccess) return cuda_fail(c, e2, "counter reset");
     *d->host_err = 0;
     const unsigned code = (unsigned)(err >> 32), step = (unsigned)(err & 0xffffffffu);
@@ -1193,8 +1263,9 @@ hiccl_status_t hiccl_debug_withhold(hiccl_comm_t c, unsigned long long index, in
   DevState *d = c->dev;
   if (index >= d->indeg.size() || extra < 0 || extra > 1000) return fail(c, HICCL_ERR_INVALID, "bad step or count");
   uint32_t v = d->indeg[index] + (uint32_t)extra;
-  cudaError_t e = cudaMemcpy(d->indeg_dev + index, &v, sizeof(v), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy");
+  cudaError_t e = cudaMemcpyAsync(d->indeg_dev + index, &v, sizeof(v), cudaMemcpyHostToDevice, d->upload);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d->upload);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync");
   return HICCL_OK;
 }
 

@@ -35,6 +35,9 @@ OK, ERR_INVALID, ERR_STATE, ERR_RACE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSU
 STATUS_NAMES = ["OK", "INVALID", "STATE", "RACE", "NOMEM", "CUDA", "TIMEOUT", "UNSUPPORTED", "TOO_LARGE"]
 STATIC_ARENA_BYTES = 16 << 20
 
+COLLECTIVES = {"broadcast": 0, "reduce": 1, "allgather": 2, "reducescatter": 3, "allreduce": 4,
+               "scatter": 5, "gather": 6, "alltoall": 7, "allreduce_single": 8}
+
 OPT_TIMEOUT_NS, OPT_CTAS_PER_SM, OPT_ITEM_BYTES, OPT_ORDER, OPT_THREADS, OPT_TRACE, OPT_SLOT_ITEMS = range(7)
 
 
@@ -83,6 +86,9 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int]),
     "hiccl_add_fence": (ctypes.c_int, [ctypes.c_void_p]),
+    "hiccl_add_collective": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t,
+                                            ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                            ctypes.c_int]),
     "hiccl_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int]),
     "hiccl_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -187,6 +193,12 @@ def hiccl_add_reduction(comm, send, recv, count: int, leaves: Sequence[int], roo
 
 def hiccl_add_fence(comm):
     _check(comm, lib().hiccl_add_fence(comm))
+
+
+def hiccl_add_collective(comm, kind, d: int, send, recv, nranks: int, root: int = 0):
+    k = COLLECTIVES[kind] if isinstance(kind, str) else int(kind)
+    _check(comm, lib().hiccl_add_collective(comm, k, int(d), _ptr_array(send, nranks), _ptr_array(recv, nranks),
+                                            int(root)))
 
 
 def hiccl_init(comm, hierarchy: Sequence[int], stripe: int = 1, pipeline: int = 1):
@@ -322,6 +334,9 @@ class Comm:
 
     def add_fence(self):
         hiccl_add_fence(self.handle)
+
+    def add_collective(self, kind, d, send, recv, root=0):
+        hiccl_add_collective(self.handle, kind, d, send, recv, self.P, root)
 
     def init(self, hierarchy, stripe=1, pipeline=1):
         hiccl_init(self.handle, list(hierarchy), stripe, pipeline)

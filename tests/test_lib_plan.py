@@ -131,3 +131,31 @@ def test_fp8_count_must_be_block_multiple():
     c.add_multicast(a, [0, 0x300000], 256, 0, [1])
     c.plan([2])
     assert c.hbm_bytes() == (2 * 144, 2 * 144)
+
+
+@pytest.mark.parametrize("name", ["broadcast", "reduce", "allgather", "reducescatter", "allreduce", "scatter",
+                                  "gather", "alltoall", "allreduce_single"])
+def test_native_composition_equals_primitive_composition(name):
+    """hiccl_add_collective registers the same program as the Table 2
+    compositions built primitive by primitive (identical plans: step count,
+    HBM and level bytes), and its step table computes the oracle's result."""
+    from paper_2408_05962_gb300 import hiccl as H
+    P, d, h = 8, 13, [2, 4]
+    prog = PR.BUILDERS[name](P, d)
+    fake = FakeAddresses(prog)
+    ref_comm = register(prog, fake.addr)
+    ref_comm.plan(h, 2, 2)
+    comm = H.Comm(P, "f32")
+    recv = [fake.base[("recv", r)] for r in range(P)]
+    send = [fake.base[("send", r)] for r in range(P)]
+    comm.add_collective(name, d, send, recv, root=0)
+    comm.plan(h, 2, 2)
+    assert comm.plan_info()["steps"] == ref_comm.plan_info()["steps"]
+    assert comm.hbm_bytes() == ref_comm.hbm_bytes()
+    assert comm.level_bytes() == ref_comm.level_bytes()
+    mem0 = fill(prog, 4)
+    ref = {k: v.copy() for k, v in mem0.items()}
+    S.run_program(prog, ref, h)
+    got = interpret(comm, fake, {k: v.copy() for k, v in mem0.items()}, prog.dtype)
+    for k in ref:
+        assert np.array_equal(ref[k], got[k]), k
