@@ -574,6 +574,71 @@ def run_batch(args):
         print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Serving workload: Poisson arrivals (synth.poisson_requests seed 0) of the
+    seven collectives, P in {8, 16, 64} ({2,4}, {4,4}, {4,4,4}), per-rank sizes
+    log-uniform 1 KiB .. 256 MiB, fp32 / bf16 / int32, admitted under a 64 GB
+    device-memory budget with continuous batching (serving.Server: 8 launch
+    slots, requests overlapping on the device; and grouped launches of up to
+    16 requests on 2 slots).  The same arrival trace is also served one
+    launch at a time (1 slot).  Reports p50 / p99 latency and the aggregate
+    schedule GB/s of each."""
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist_init("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2408_05962_gb300.serving import Request, Server, latency_stats
+    from synth import poisson_requests
+
+    def serve(descs, slots, max_batch):
+        srv = Server(args.budget_gb << 30, slots=slots, max_batch=max_batch, planners=8)
+        t0 = time.perf_counter()
+        k = 0
+        while k < len(descs) or srv.busy():
+            now = time.perf_counter() - t0
+            while k < len(descs) and descs[k]["t"] <= now:
+                dsc = descs[k]
+                srv.submit(Request(kind=dsc["kind"], P=dsc["P"], hierarchy=dsc["hierarchy"],
+                                   bytes_per_rank=dsc["bytes_per_rank"], dtype=dsc["dtype"],
+                                   t_arrival=t0 + dsc["t"]))
+                k += 1
+            srv.poll()
+        wall = time.perf_counter() - t0
+        srv.close()
+        done = [r for r in srv.done if not r.error]
+        st = latency_stats(done)
+        total = sum(r.hbm_bytes for r in done)
+        return {"requests": len(descs), "completed": len(done), "errors": len(srv.done) - len(done),
+                "wall_s": wall, "achieved_req_per_s": len(done) / wall, "gbs": total / wall / 1e9,
+                "launches": srv.launches, **st}
+
+    out = {}
+    for rate in (args.rate, args.low_rate):
+        descs = poisson_requests(rate, args.duration, seed=0)
+        out[f"{rate:g}/s"] = {"batched": serve(descs, 8, 1), "grouped": serve(descs, 2, 16),
+                              "one_launch_at_a_time": serve(descs, 1, 1)}
+    head = out[f"{args.rate:g}/s"]["batched"]
+    peak, peak_kind = measured_peak()
+    line = {
+        "metric": METRIC, "value": head["gbs"], "unit": "GB/s", "n_gpus": world, "steps": 1, "warmup": 0,
+        "ms_per_step": head["wall_s"] * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+bf16+i32", "data": "synthetic",
+        "config": {"workload": f"serving: Poisson {args.rate:g} requests/s for {args.duration:g} s of the seven "
+                               "collectives, P in {8,16,64}, 1 KiB..256 MiB per rank, fp32/bf16/int32, "
+                               f"{args.budget_gb} GB budget, continuous batching", "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "hbm", "achieved": head["gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": head["gbs"] / peak, "peak_source": peak_kind, "traffic": None,
+                     "kernel": "hiccl_exec_kernel"},
+        "serving": out, "p50_ms": head.get("p50_ms"), "p99_ms": head.get("p99_ms"),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -585,7 +650,11 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--item-bytes", type=int, default=0, help="executor work-item size (0: library default)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="executor CTAs per SM (0: library default)")
-    ap.add_argument("--workload", default="seven", choices=sorted(WORKLOADS) + ["batch256"])
+    ap.add_argument("--workload", default="seven", choices=sorted(WORKLOADS) + ["batch256", "serve"])
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: offered requests per second")
+    ap.add_argument("--low-rate", type=float, default=100.0, help="serve: a sub-saturating rate")
+    ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
+    ap.add_argument("--budget-gb", type=int, default=64, help="serve: device-memory budget")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8"],
                     help="payload of the allreduce64 workload (accumulation is FP32)")
     ap.add_argument("--kinds", default="", help="comma-separated subset of the seven collectives (profiling)")
@@ -596,6 +665,8 @@ def main(argv=None):
         run_reference(args)
     elif args.workload == "batch256":
         run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 
