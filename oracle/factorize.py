@@ -72,6 +72,7 @@ class Op:
     epoch: int = 0
     branch: int = 0
     channel: int = 0
+    op: str = "sum"           # combining operation of a reduce
 
 
 @dataclass
@@ -147,12 +148,13 @@ class Factorizer:
         self.ops: list = []
         self.scratch: dict = {}
         self._cur = None            # (prim, epoch, branch, channel)
+        self._op = "sum"
 
     # ---- helpers -------------------------------------------------------------
     def _emit(self, kind, srcs, dsts, n, level, deps) -> int:
         prim, epoch, b, c = self._cur
         self.ops.append(Op(kind, srcs, dsts, n, level, sorted(set(d for d in deps if d is not None)),
-                           prim, epoch, b, c))
+                           prim, epoch, b, c, self._op))
         return len(self.ops) - 1
 
     def _new_scratch(self, n: int) -> Ref:
@@ -298,8 +300,10 @@ class Factorizer:
             for p in epoch:
                 self._cur = (pid, e, 0, 0)
                 if isinstance(p, Multicast):
+                    self._op = "sum"
                     self._multicast(p)
                 else:
+                    self._op = p.op
                     self._reduction(p)
                 pid += 1
             if e > 0:

@@ -62,6 +62,7 @@ class Reduction:
     count: int
     srcs: dict                    # leaf rank -> Ref of its source range
     dst: Ref                      # the root's destination range
+    op: str = "sum"               # sum | max | min | lor
 
     kind = "reduction"
 
@@ -82,9 +83,9 @@ class Program:
         self.epochs[-1].append(Multicast(int(root), tuple(sorted(int(j) for j in leaves)),
                                          int(count), src, dict(dsts)))
 
-    def reduction(self, leaves, root: int, count: int, srcs: dict, dst: Ref) -> None:
+    def reduction(self, leaves, root: int, count: int, srcs: dict, dst: Ref, op: str = "sum") -> None:
         self.epochs[-1].append(Reduction(tuple(sorted(int(i) for i in leaves)), int(root),
-                                         int(count), dict(srcs), dst))
+                                         int(count), dict(srcs), dst, op))
 
     def fence(self) -> None:
         self.epochs.append([])

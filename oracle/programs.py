@@ -36,11 +36,11 @@ def broadcast(P, d, root=0, dtype="f32"):
     return prog
 
 
-def reduce(P, d, root=0, dtype="f32"):
-    """R(U, j, dp, sum)."""
+def reduce(P, d, root=0, dtype="f32", op="sum"):
+    """R(U, j, dp, op)."""
     prog = Program(P, dtype)
     send, recv = _bufs(prog, P, d * P, d * P)
-    prog.reduction(_all(P), root, d * P, {r: send[r] for r in range(P)}, recv[root])
+    prog.reduction(_all(P), root, d * P, {r: send[r] for r in range(P)}, recv[root], op)
     return prog
 
 
@@ -101,13 +101,13 @@ def alltoall(P, d, dtype="f32"):
 
 # ---- Listing 2 ------------------------------------------------------------------
 
-def allreduce(P, d, dtype="f32"):
+def allreduce(P, d, dtype="f32", op="sum"):
     """Reduce-scatter, fence, in-place All-gather (Listing 2, Fig. 4)."""
     prog = Program(P, dtype)
     send, recv = _bufs(prog, P, d * P, d * P)
     for j in range(P):
         prog.reduction(_all(P), j, d, {r: send[r].shift(j * d) for r in range(P)},
-                       recv[j].shift(j * d))
+                       recv[j].shift(j * d), op)
     prog.fence()
     for i in range(P):
         others = [r for r in range(P) if r != i]

@@ -30,7 +30,23 @@ from .model import Multicast, Program, Reduction
 # the fixed-order sum
 # ---------------------------------------------------------------------------
 
-def nested_fold(values: dict, hierarchy, dtype: str | None = None) -> np.ndarray:
+def combine(a: np.ndarray, b: np.ndarray, op: str = "sum") -> np.ndarray:
+    """One step of a reduction's fold (Sec. 3.1: sum, max, logical or, ...).
+    sum: the arrays' own arithmetic; max / min: IEEE maxNum / minNum for
+    floats (a NaN operand yields the other), plain for int32; lor (int32): 1
+    where either operand is nonzero, else 0."""
+    if op == "sum":
+        return a + b
+    if op == "max":
+        return np.fmax(a, b) if a.dtype.kind == "f" else np.maximum(a, b)
+    if op == "min":
+        return np.fmin(a, b) if a.dtype.kind == "f" else np.minimum(a, b)
+    if op == "lor":
+        return ((a != 0) | (b != 0)).astype(a.dtype)
+    raise ValueError(op)
+
+
+def nested_fold(values: dict, hierarchy, dtype: str | None = None, op: str = "sum") -> np.ndarray:
     """Hierarchical nested fold of ``values`` (rank -> array) over ``hierarchy``.
 
     S(rank r) = values[r]; S(group) = the left fold over the S(subgroup) of
@@ -40,7 +56,8 @@ def nested_fold(values: dict, hierarchy, dtype: str | None = None) -> np.ndarray
     precision payloads ("bf16", "fp8") the subgroup values are decoded to
     binary32, folded with binary32 adds and the group's result encoded once
     (lowprec); a group with a single contributing subgroup passes its value
-    through unchanged.
+    through unchanged (Sec. 3.1: with one leaf the operation is omitted).
+    ``op`` selects the combining operation (``combine``).
     """
     if not values:
         raise ValueError("empty leaf set")
@@ -64,11 +81,11 @@ def nested_fold(values: dict, hierarchy, dtype: str | None = None) -> np.ndarray
         if not low:
             acc = parts[0].copy()
             for p in parts[1:]:
-                acc = acc + p
+                acc = combine(acc, p, op)
             return acc
         acc = to_acc(parts[0], dtype).copy()
         for p in parts[1:]:
-            acc = (acc + to_acc(p, dtype)).astype(np.float32)
+            acc = combine(acc, to_acc(p, dtype), op).astype(np.float32)
         return from_acc(acc, dtype)
 
     return S(0, 0, ranks)
@@ -103,7 +120,7 @@ def apply_reduction(p: Reduction, mem: dict, hierarchy, dtype: str | None = None
     if p.count == 0:
         return
     vals = {i: _view(mem, p.srcs[i], p.count).copy() for i in p.leaves}
-    _view(mem, p.dst, p.count)[...] = nested_fold(vals, hierarchy, dtype)
+    _view(mem, p.dst, p.count)[...] = nested_fold(vals, hierarchy, dtype, p.op)
 
 
 def run_program(prog: Program, mem: dict, hierarchy) -> dict:

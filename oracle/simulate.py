@@ -11,6 +11,7 @@ import numpy as np
 from .factorize import Plan
 from .lowprec import from_acc, to_acc
 from .model import DTYPES
+from .semantics import combine
 
 
 def _view(mem, ref, n):
@@ -28,12 +29,12 @@ def execute_op(op, mem: dict, dtype: str | None = None) -> None:
     if dtype in ("bf16", "fp8"):
         acc = to_acc(_view(mem, op.srcs[0][1], op.n), dtype).copy()
         for _, s in op.srcs[1:]:
-            acc = (acc + to_acc(_view(mem, s, op.n), dtype)).astype(np.float32)
+            acc = combine(acc, to_acc(_view(mem, s, op.n), dtype), op.op).astype(np.float32)
         _view(mem, op.dsts[0][1], op.n)[...] = from_acc(acc, dtype)
         return
     acc = _view(mem, op.srcs[0][1], op.n).copy()
     for _, s in op.srcs[1:]:
-        acc = acc + _view(mem, s, op.n)
+        acc = combine(acc, _view(mem, s, op.n), op.op)
     _view(mem, op.dsts[0][1], op.n)[...] = acc
 
 

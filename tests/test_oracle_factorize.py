@@ -270,3 +270,28 @@ def test_collectives_simulated(name, P, h, s, m):
     simulate(plan, got, order_seed=P + s + m)
     for k in ref:
         assert np.array_equal(ref[k], got[k]), (name, k)
+
+
+
+@pytest.mark.parametrize("op,dtype", [("max", "f32"), ("min", "i32"), ("lor", "i32"), ("max", "bf16")])
+@pytest.mark.parametrize("P,h,s,m", [(8, [2, 4], 1, 1), (8, [2, 4], 4, 2), (12, [2, 2, 3], 3, 2)])
+def test_other_ops_simulated(op, dtype, P, h, s, m):
+    d = 24
+    for prog in (PR.allreduce(P, d, dtype=dtype, op=op), PR.reduce(P, d, root=P - 1, dtype=dtype, op=op)):
+        mem0 = _init_ops(prog, 3)
+        ref = {k: v.copy() for k, v in mem0.items()}
+        S.run_program(prog, ref, h)
+        got = {k: v.copy() for k, v in mem0.items()}
+        simulate(factorize(prog, h, s, m), got, order_seed=s + m)
+        for k in ref:
+            assert np.array_equal(ref[k].view(np.uint8), got[k].view(np.uint8)), k
+
+
+def _init_ops(prog, seed):
+    from tests._cases import fill
+    mem = fill(prog, seed)
+    if prog.dtype == "i32":                      # small values with zeros, for lor
+        g = np.random.Generator(np.random.PCG64(seed))
+        for v in mem.values():
+            v[...] = g.integers(-2, 3, size=v.shape)
+    return mem

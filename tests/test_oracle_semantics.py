@@ -255,3 +255,34 @@ def test_race_detection():
     prog3.multicast(0, [1], 4, b[0], {1: b[1]})
     prog3.multicast(1, [2], 4, b[1], {2: b[2]})
     assert S.find_race(prog3) is not None
+
+
+# ---------------------------------------------------------------------------
+# other reduction operators (Sec. 3.1: sum, max, logical or, ...)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("op", ["max", "min", "lor"])
+@pytest.mark.parametrize("P,h", [(4, [2, 2]), (8, [2, 4]), (6, [3, 2]), (5, [5])])
+def test_other_ops_bruteforce(op, P, h):
+    """max / min are order-free: the fold equals the plain elementwise max /
+    min over ranks (brute force); logical or of two or more contributions is
+    1 exactly where some rank is nonzero."""
+    g = np.random.Generator(np.random.PCG64(P))
+    xi = g.integers(-3, 4, size=(P, 40)).astype(np.int32)        # many zeros for lor
+    xi[:, :5] = 0
+    got = S.nested_fold({r: xi[r] for r in range(P)}, h, None, op)
+    for k in range(40):
+        col = [int(xi[r, k]) for r in range(P)]
+        want = {"max": max(col), "min": min(col), "lor": int(any(v != 0 for v in col))}[op]
+        assert int(got[k]) == want
+    if op != "lor":
+        xf = uniform_ranks(P, 40, seed=P)
+        gotf = S.nested_fold({r: xf[r] for r in range(P)}, h, None, op)
+        assert np.array_equal(gotf, xf.max(axis=0) if op == "max" else xf.min(axis=0))
+
+
+def test_single_leaf_reduction_omits_the_operation():
+    """Sec. 3.1: a reduction with one leaf is point-to-point; the operation
+    is omitted (a logical or of one nonzero value is the value itself)."""
+    x = {3: np.array([5, 0, -2], np.int32)}
+    assert list(S.nested_fold(x, [2, 2], None, "lor")) == [5, 0, -2]
