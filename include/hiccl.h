@@ -42,8 +42,13 @@ typedef enum {
   HICCL_FP8E4M3 = 3
 } hiccl_dtype_t;
 
-/* Reduction operator (Sec. 3.1 lists sum, max, logical or; sum is provided). */
-typedef enum { HICCL_SUM = 0 } hiccl_op_t;
+/* Reduction operator (Sec. 3.1: "sum, max, logical or, etc.").
+ *   SUM: see hiccl_add_reduction (all payloads).
+ *   MAX / MIN: F32 IEEE maxNum / minNum (a NaN operand yields the other),
+ *              I32, BF16 (exact: the result is one of the inputs); not FP8.
+ *   LOR: I32 only; 1 where some contribution is nonzero, else 0.
+ * A reduction with a single leaf is a copy: the operator is omitted (Sec. 3.1). */
+typedef enum { HICCL_SUM = 0, HICCL_MAX = 1, HICCL_MIN = 2, HICCL_LOR = 3 } hiccl_op_t;
 
 typedef enum {
   HICCL_OK = 0,
@@ -115,10 +120,13 @@ typedef enum {
 
 /* Register collective `kind` over chunk length d (elements; d*P is the largest
  * per-rank buffer, Sec. 3.2) for per-rank buffers send[r], recv[r] (arrays of
- * nranks device pointers laid out as in the table above).  Same ownership,
- * state and error rules as hiccl_add_multicast / hiccl_add_reduction. */
+ * nranks device pointers laid out as in the table above).  The reductions of
+ * REDUCE, REDUCESCATTER, ALLREDUCE and ALLREDUCE_SINGLE combine with `op`
+ * (other kinds ignore it).  Same ownership, state and error rules as
+ * hiccl_add_multicast / hiccl_add_reduction. */
 hiccl_status_t hiccl_add_collective(hiccl_comm_t comm, hiccl_collective_t kind, size_t d,
-                                    const void *const *send, void *const *recv, int root);
+                                    const void *const *send, void *const *recv, int root,
+                                    hiccl_op_t op);
 
 /* ---- optimization (Sec. 4) -------------------------------------------------- */
 
@@ -232,6 +240,7 @@ hiccl_status_t hiccl_plan_info(hiccl_comm_t comm, hiccl_plan_info_t *out);
 
 /* One step of the plan, for inspection and host-side checking.
  *   kind: 0 copy, 1 reduce.  level: hierarchy level crossed, -1 local.
+ *   op: the reduce's hiccl_op_t (0 for copies).
  *   src_addr/dst_addr: device addresses, or byte offsets into the relay
  *   arena where the matching *_scratch flag is 1.  preds: indices of the
  *   steps this one depends on.  Arrays must hold nsrc, ndst and npreds
@@ -245,6 +254,8 @@ typedef struct {
   int prim;
   int branch;
   int channel;
+  int op;
+  int reserved;
   unsigned long long nbytes;
   unsigned long long slot;
 } hiccl_step_desc_t;

@@ -53,21 +53,21 @@ def allgather(P, d, dtype="f32"):
     return prog
 
 
-def reducescatter(P, d, dtype="f32"):
-    """sum_j R(U, j, d, sum)."""
+def reducescatter(P, d, dtype="f32", op="sum"):
+    """sum_j R(U, j, d, op)."""
     prog = Program(P, dtype)
     send, recv = _bufs(prog, P, d * P, d)
     for j in range(P):
-        prog.reduction(_all(P), j, d, {r: send[r].shift(j * d) for r in range(P)}, recv[j])
+        prog.reduction(_all(P), j, d, {r: send[r].shift(j * d) for r in range(P)}, recv[j], op)
     return prog
 
 
-def allreduce_single(P, d, dtype="f32"):
-    """sum_j R(U, j, dp, sum) -- moves d*p^2 data (Sec. 3.2)."""
+def allreduce_single(P, d, dtype="f32", op="sum"):
+    """sum_j R(U, j, dp, op) -- moves d*p^2 data (Sec. 3.2)."""
     prog = Program(P, dtype)
     send, recv = _bufs(prog, P, d * P, d * P)
     for j in range(P):
-        prog.reduction(_all(P), j, d * P, {r: send[r] for r in range(P)}, recv[j])
+        prog.reduction(_all(P), j, d * P, {r: send[r] for r in range(P)}, recv[j], op)
     return prog
 
 

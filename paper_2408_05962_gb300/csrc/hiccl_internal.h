@@ -33,15 +33,18 @@ constexpr uint32_t TMA_MAX_FANIN = 8;   // reduce inputs folded in shared memory
 
 enum : uint32_t { OP_COPY = 0, OP_REDUCE = 1 };
 
-// meta word of a step: op | dtype << 2 | aligned16 << 6 | nsrc << 8 (12 bits) | ndst << 20 (12 bits)
-HICCL_HD inline uint32_t meta_pack(uint32_t op, uint32_t dt, uint32_t al, uint32_t nsrc, uint32_t ndst) {
-  return op | (dt << 2) | (al << 6) | (nsrc << 8) | (ndst << 20);
+// meta word of a step: op (2 bits) | dtype (4) | aligned16 (1) | reduction
+// operator (3) | nsrc (11) | ndst (11)
+HICCL_HD inline uint32_t meta_pack(uint32_t op, uint32_t dt, uint32_t al, uint32_t nsrc, uint32_t ndst,
+                                   uint32_t rop = 0) {
+  return op | (dt << 2) | (al << 6) | (rop << 7) | (nsrc << 10) | (ndst << 21);
 }
 HICCL_HD inline uint32_t meta_op(uint32_t m) { return m & 3u; }
 HICCL_HD inline uint32_t meta_dtype(uint32_t m) { return (m >> 2) & 15u; }
 HICCL_HD inline uint32_t meta_aligned(uint32_t m) { return (m >> 6) & 1u; }
-HICCL_HD inline uint32_t meta_nsrc(uint32_t m) { return (m >> 8) & 4095u; }
-HICCL_HD inline uint32_t meta_ndst(uint32_t m) { return (m >> 20) & 4095u; }
+HICCL_HD inline uint32_t meta_rop(uint32_t m) { return (m >> 7) & 7u; }
+HICCL_HD inline uint32_t meta_nsrc(uint32_t m) { return (m >> 10) & 2047u; }
+HICCL_HD inline uint32_t meta_ndst(uint32_t m) { return (m >> 21) & 2047u; }
 
 // one contiguous run of a step's segments inside a work item
 struct DevEntry {
@@ -119,10 +122,13 @@ struct HStep {
   unsigned long long slot;
   uint32_t local;          // emission index inside its piece (same tree position in every channel)
   uint32_t dtype;          // payload type of the step's communicator
+  uint32_t rop;            // reduction operator (hiccl_op_t) of a reduce
+  uint32_t pad3;
 };
 
 struct Prim {
   int kind;                                // 0 multicast, 1 reduction
+  int op = 0;                              // hiccl_op_t of a reduction
   int root;
   std::vector<int> leaves;                 // sorted, distinct
   size_t count;

@@ -122,6 +122,7 @@ struct Builder {
     st.nbytes = cur_n;
     st.local = cur_local++;
     st.dtype = (uint32_t)c.dtype;
+    st.rop = p ? (uint32_t)p->op : 0u;
     st.loc0 = (uint32_t)locs.size();
     st.nsrc = (uint32_t)srcs.size();
     st.ndst = (uint32_t)dsts.size();
@@ -788,10 +789,16 @@ hiccl_status_t hiccl_add_reduction(hiccl_comm_t c, const void *const *send, void
   if (!c) return HICCL_ERR_INVALID;
   if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "add after init");
   if (!send || !recv) return fail(c, HICCL_ERR_INVALID, "null pointer array");
-  if (op != HICCL_SUM) return fail(c, HICCL_ERR_UNSUPPORTED, "only HICCL_SUM is implemented");
+  if (op != HICCL_SUM && op != HICCL_MAX && op != HICCL_MIN && op != HICCL_LOR)
+    return fail(c, HICCL_ERR_INVALID, "unknown reduction operator");
+  if (op != HICCL_SUM && c->dtype == HICCL_FP8E4M3)
+    return fail(c, HICCL_ERR_UNSUPPORTED, "FP8 payloads reduce with HICCL_SUM only");
+  if (op == HICCL_LOR && c->dtype != HICCL_I32)
+    return fail(c, HICCL_ERR_UNSUPPORTED, "HICCL_LOR needs HICCL_I32 payloads");
   if (root < 0 || root >= c->P) return fail(c, HICCL_ERR_INVALID, "root out of range");
   Prim p;
   p.kind = 1;
+  p.op = (int)op;
   p.root = root;
   if (!to_units(c, count, p.count)) return fail(c, HICCL_ERR_INVALID, "FP8 counts must be multiples of 128");
   p.epoch = c->epochs - 1;
@@ -822,7 +829,7 @@ hiccl_status_t hiccl_add_fence(hiccl_comm_t c) {
 }
 
 hiccl_status_t hiccl_add_collective(hiccl_comm_t c, hiccl_collective_t kind, size_t d, const void *const *send,
-                                    void *const *recv, int root) {
+                                    void *const *recv, int root, hiccl_op_t op) {
   if (!c) return HICCL_ERR_INVALID;
   if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "add after init");
   if (!send || !recv) return fail(c, HICCL_ERR_INVALID, "null pointer array");
@@ -847,7 +854,7 @@ hiccl_status_t hiccl_add_collective(hiccl_comm_t c, hiccl_collective_t kind, siz
     case HICCL_BROADCAST:
       return hiccl_add_multicast(c, send, recv, dp, root, all.data(), P);
     case HICCL_REDUCE:
-      return hiccl_add_reduction(c, send, recv, dp, all.data(), P, root, HICCL_SUM);
+      return hiccl_add_reduction(c, send, recv, dp, all.data(), P, root, op);
     case HICCL_ALLGATHER:
       for (int i = 0; i < P && st == HICCL_OK; ++i) {
         for (int r = 0; r < P; ++r) v[r] = ra(r, i);
@@ -857,12 +864,12 @@ hiccl_status_t hiccl_add_collective(hiccl_comm_t c, hiccl_collective_t kind, siz
     case HICCL_REDUCESCATTER:
       for (int j = 0; j < P && st == HICCL_OK; ++j) {
         for (int r = 0; r < P; ++r) s[r] = sa(r, j);
-        st = hiccl_add_reduction(c, s.data(), recv, d, all.data(), P, j, HICCL_SUM);
+        st = hiccl_add_reduction(c, s.data(), recv, d, all.data(), P, j, op);
       }
       return st;
     case HICCL_ALLREDUCE_SINGLE:
       for (int j = 0; j < P && st == HICCL_OK; ++j)
-        st = hiccl_add_reduction(c, send, recv, dp, all.data(), P, j, HICCL_SUM);
+        st = hiccl_add_reduction(c, send, recv, dp, all.data(), P, j, op);
       return st;
     case HICCL_SCATTER:
       for (int j = 0; j < P && st == HICCL_OK; ++j) {
@@ -894,7 +901,7 @@ hiccl_status_t hiccl_add_collective(hiccl_comm_t c, hiccl_collective_t kind, siz
         reset();
         for (int r = 0; r < P; ++r) s[r] = sa(r, j);
         v[j] = ra(j, j);
-        st = hiccl_add_reduction(c, s.data(), v.data(), d, all.data(), P, j, HICCL_SUM);
+        st = hiccl_add_reduction(c, s.data(), v.data(), d, all.data(), P, j, op);
       }
       if (st == HICCL_OK) st = hiccl_add_fence(c);
       for (int i = 0; i < P && st == HICCL_OK; ++i) {
@@ -1092,6 +1099,8 @@ hiccl_status_t hiccl_get_step(hiccl_comm_t c, unsigned long long index, hiccl_st
   d->prim = st.prim;
   d->branch = st.branch;
   d->channel = st.channel;
+  d->op = st.kind == 1 ? (int)st.rop : 0;
+  d->reserved = 0;
   d->nbytes = st.nbytes;
   d->slot = st.slot;
   for (uint32_t k = 0; k < st.nsrc; ++k) {

@@ -101,17 +101,37 @@ __device__ __forceinline__ T ldg_ro(const T *p) { return __ldg(p); }
 __device__ __forceinline__ uint4 ld16(const char *p) { return __ldcg(reinterpret_cast<const uint4 *>(p)); }
 __device__ __forceinline__ void st16(char *p, uint4 v) { *reinterpret_cast<uint4 *>(p) = v; }
 
-__device__ __forceinline__ uint4 add4(uint4 a, uint4 b, uint32_t dt) {
-  if (dt == HICCL_F32) {
+// one step of a fold on 32-bit lanes: f32 (IEEE RNE add, maxNum, minNum) or
+// i32 (wrapping add, max, min, logical or)
+__device__ __forceinline__ float comb_f(float a, float b, uint32_t rop) {
+  return rop == HICCL_SUM ? __fadd_rn(a, b) : rop == HICCL_MAX ? fmaxf(a, b) : fminf(a, b);
+}
+__device__ __forceinline__ uint32_t comb32(uint32_t a, uint32_t b, uint32_t dt, uint32_t rop) {
+  if (dt == HICCL_F32) return __float_as_uint(comb_f(__uint_as_float(a), __uint_as_float(b), rop));
+  const int x = (int)a, y = (int)b;
+  switch (rop) {
+    case HICCL_SUM: return a + b;
+    case HICCL_MAX: return (uint32_t)(x > y ? x : y);
+    case HICCL_MIN: return (uint32_t)(x < y ? x : y);
+    default: return (x != 0 || y != 0) ? 1u : 0u;
+  }
+}
+__device__ __forceinline__ uint4 add4(uint4 a, uint4 b, uint32_t dt, uint32_t rop = 0) {
+  if (rop == HICCL_SUM && dt == HICCL_F32) {
     a.x = __float_as_uint(__fadd_rn(__uint_as_float(a.x), __uint_as_float(b.x)));
     a.y = __float_as_uint(__fadd_rn(__uint_as_float(a.y), __uint_as_float(b.y)));
     a.z = __float_as_uint(__fadd_rn(__uint_as_float(a.z), __uint_as_float(b.z)));
     a.w = __float_as_uint(__fadd_rn(__uint_as_float(a.w), __uint_as_float(b.w)));
-  } else {   // int32, wrapping
+  } else if (rop == HICCL_SUM) {   // int32, wrapping
     a.x += b.x;
     a.y += b.y;
     a.z += b.z;
     a.w += b.w;
+  } else {
+    a.x = comb32(a.x, b.x, dt, rop);
+    a.y = comb32(a.y, b.y, dt, rop);
+    a.z = comb32(a.z, b.z, dt, rop);
+    a.w = comb32(a.w, b.w, dt, rop);
   }
   return a;
 }
@@ -147,10 +167,10 @@ __device__ __forceinline__ uint32_t f32x2_to_e4m3x2(float lo, float hi) {
 // vector: f32 / i32 natively (add4), BF16 decoded to binary32, folded in
 // order and rounded once
 template <typename LD>
-__device__ __forceinline__ uint4 fold16(LD ld, uint32_t f, uint32_t dt) {
+__device__ __forceinline__ uint4 fold16(LD ld, uint32_t f, uint32_t dt, uint32_t rop = 0) {
   uint4 v = ld(0);
   if (dt != HICCL_BF16) {
-    for (uint32_t q = 1; q < f; ++q) v = add4(v, ld(q), dt);
+    for (uint32_t q = 1; q < f; ++q) v = add4(v, ld(q), dt, rop);
     return v;
   }
   float a[8];
@@ -165,8 +185,8 @@ __device__ __forceinline__ uint4 fold16(LD ld, uint32_t f, uint32_t dt) {
     const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      a[2 * i] = __fadd_rn(a[2 * i], __uint_as_float(w[i] << 16));
-      a[2 * i + 1] = __fadd_rn(a[2 * i + 1], __uint_as_float(w[i] & 0xffff0000u));
+      a[2 * i] = comb_f(a[2 * i], __uint_as_float(w[i] << 16), rop);
+      a[2 * i + 1] = comb_f(a[2 * i + 1], __uint_as_float(w[i] & 0xffff0000u), rop);
     }
   }
   uint4 r;
@@ -271,7 +291,8 @@ __device__ __forceinline__ void warp_copy(const unsigned long long *ptrs, uint32
 
 // out[lo, lo + n) = in_0 + in_1 + ... (left fold, fixed order; n <= SEG_BYTES)
 __device__ __forceinline__ void warp_reduce(const unsigned long long *ptrs, uint32_t nsrc, uint32_t dt,
-                                            unsigned long long lo, uint32_t n, bool aligned, int lane) {
+                                            unsigned long long lo, uint32_t n, bool aligned, int lane,
+                                            uint32_t rop = 0) {
   char *dst = reinterpret_cast<char *>(ptrs[nsrc]) + lo;
   if (dt == HICCL_FP8E4M3) {   // whole 144-byte blocks, four per warp pass
     const uint32_t nblk = n / FP8_BLOCK_BYTES, grp = lane >> 3, sub = lane & 7;
@@ -305,7 +326,7 @@ __device__ __forceinline__ void warp_reduce(const unsigned long long *ptrs, uint
           if (i < nvec) v[u] = ld16(sq + (i << 4));
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) acc[u] = add4(acc[u], v[u], dt);
+        for (int u = 0; u < U; ++u) acc[u] = add4(acc[u], v[u], dt, rop);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -318,7 +339,8 @@ __device__ __forceinline__ void warp_reduce(const unsigned long long *ptrs, uint
     const uint32_t nvec = n >> 4;
     for (uint32_t i = lane; i < nvec; i += 32)
       st16(dst + (i << 4),
-           fold16([&](uint32_t q) { return ld16(reinterpret_cast<const char *>(ptrs[q]) + lo + (i << 4)); }, nsrc, dt));
+           fold16([&](uint32_t q) { return ld16(reinterpret_cast<const char *>(ptrs[q]) + lo + (i << 4)); }, nsrc, dt,
+                  rop));
     done = nvec << 4;
   }
   // element tail (or the whole unaligned range)
@@ -327,8 +349,9 @@ __device__ __forceinline__ void warp_reduce(const unsigned long long *ptrs, uint
       float acc = __uint_as_float((uint32_t)__ldcg(reinterpret_cast<const unsigned short *>(
                                       reinterpret_cast<const char *>(ptrs[0]) + lo + b)) << 16);
       for (uint32_t q = 1; q < nsrc; ++q)
-        acc = __fadd_rn(acc, __uint_as_float((uint32_t)__ldcg(reinterpret_cast<const unsigned short *>(
-                                                 reinterpret_cast<const char *>(ptrs[q]) + lo + b)) << 16));
+        acc = comb_f(acc, __uint_as_float((uint32_t)__ldcg(reinterpret_cast<const unsigned short *>(
+                                              reinterpret_cast<const char *>(ptrs[q]) + lo + b)) << 16),
+                     rop);
       *reinterpret_cast<unsigned short *>(dst + b) = (unsigned short)f32_to_bf16_rn(acc);
     }
     return;
@@ -337,10 +360,7 @@ __device__ __forceinline__ void warp_reduce(const unsigned long long *ptrs, uint
     uint32_t acc = __ldcg(reinterpret_cast<const unsigned int *>(reinterpret_cast<const char *>(ptrs[0]) + lo + b));
     for (uint32_t q = 1; q < nsrc; ++q) {
       const uint32_t v = __ldcg(reinterpret_cast<const unsigned int *>(reinterpret_cast<const char *>(ptrs[q]) + lo + b));
-      if (dt == HICCL_F32)
-        acc = __float_as_uint(__fadd_rn(__uint_as_float(acc), __uint_as_float(v)));
-      else
-        acc += v;
+      acc = comb32(acc, v, dt, rop);
     }
     *reinterpret_cast<uint32_t *>(dst + b) = acc;
   }
@@ -795,7 +815,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
             } else {
               for (uint32_t v = lane; v < len / 16; v += 32)
                 *reinterpret_cast<uint4 *>(my_stage + v * 16) = fold16(
-                    [&](uint32_t q) { return *reinterpret_cast<const uint4 *>(my_stage + q * chunk + v * 16); }, f, dt);
+                    [&](uint32_t q) { return *reinterpret_cast<const uint4 *>(my_stage + q * chunk + v * 16); }, f, dt,
+                    meta_rop(meta));
             }
             fence_proxy_async_smem();   // the folded chunk is read by the bulk store
             __syncwarp();
@@ -810,15 +831,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
             float acc = __uint_as_float((uint32_t)__ldcg(reinterpret_cast<const unsigned short *>(
                                             reinterpret_cast<const char *>(ptrs[0]) + b)) << 16);
             for (uint32_t q = 1; q < f; ++q)
-              acc = __fadd_rn(acc, __uint_as_float((uint32_t)__ldcg(reinterpret_cast<const unsigned short *>(
-                                                       reinterpret_cast<const char *>(ptrs[q]) + b)) << 16));
+              acc = comb_f(acc, __uint_as_float((uint32_t)__ldcg(reinterpret_cast<const unsigned short *>(
+                                                    reinterpret_cast<const char *>(ptrs[q]) + b)) << 16),
+                           meta_rop(meta));
             *reinterpret_cast<unsigned short *>(reinterpret_cast<char *>(ptrs[f]) + b) = (unsigned short)f32_to_bf16_rn(acc);
           } else if (!stalled && n16 != g.n && dt != HICCL_BF16 && lane < (int)((g.n - n16) / 4)) {
             const unsigned long long b = g.lo + n16 + 4 * lane;
             uint32_t acc = __ldcg(reinterpret_cast<const unsigned int *>(reinterpret_cast<const char *>(ptrs[0]) + b));
             for (uint32_t q = 1; q < f; ++q) {
               const uint32_t v = __ldcg(reinterpret_cast<const unsigned int *>(reinterpret_cast<const char *>(ptrs[q]) + b));
-              acc = dt == HICCL_F32 ? __float_as_uint(__fadd_rn(__uint_as_float(acc), __uint_as_float(v))) : acc + v;
+              acc = comb32(acc, v, dt, meta_rop(meta));
             }
             *reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(ptrs[f]) + b) = acc;
           }
@@ -839,7 +861,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
           if (meta_op(meta) == OP_COPY)
             warp_copy(ptrs, meta_ndst(meta), g.lo, g.n, meta_aligned(meta), lane);
           else
-            warp_reduce(ptrs, meta_nsrc(meta), meta_dtype(meta), g.lo, g.n, meta_aligned(meta), lane);
+            warp_reduce(ptrs, meta_nsrc(meta), meta_dtype(meta), g.lo, g.n, meta_aligned(meta), lane, meta_rop(meta));
         }
       }
       mbar_arrive(&done_bar[b]);
@@ -1016,7 +1038,7 @@ hiccl_status_t dev_upload(hiccl_comm *c) {
     indeg[i] = p.pred_off[i + 1] - p.pred_off[i];
     bool al = true;
     for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k) al = al && (ptrs[st.loc0 + k] % 16 == 0);
-    meta[i] = meta_pack(st.kind, st.dtype, al ? 1u : 0u, st.nsrc, st.ndst);
+    meta[i] = meta_pack(st.kind, st.dtype, al ? 1u : 0u, st.nsrc, st.ndst, st.rop);
   }
 
   // one allocation for all read-only arrays
@@ -1313,7 +1335,7 @@ __global__ void hiccl_static_expand(const HStep *steps, const Loc *locs, const u
     nbytes[i] = st.nbytes;
     ptr_off[i] = st.loc0;
     indeg[i] = pred_off[i + 1] - pred_off[i];
-    meta[i] = meta_pack(st.kind, st.dtype, al ? 1u : 0u, st.nsrc, st.ndst);
+    meta[i] = meta_pack(st.kind, st.dtype, al ? 1u : 0u, st.nsrc, st.ndst, st.rop);
   }
 }
 

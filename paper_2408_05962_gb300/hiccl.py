@@ -29,7 +29,9 @@ def nbytes(dtype: int, elems: int) -> int:
             raise ValueError("FP8 counts must be multiples of 128")
         return elems // FP8_BLOCK * FP8_BLOCK_BYTES
     return elems * ESIZE[dtype]
-SUM = 0
+SUM, MAX, MIN, LOR = 0, 1, 2, 3
+OPS = {"sum": SUM, "max": MAX, "min": MIN, "lor": LOR}
+OP_NAMES = {v: k for k, v in OPS.items()}
 
 OK, ERR_INVALID, ERR_STATE, ERR_RACE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_TOO_LARGE = range(9)
 STATUS_NAMES = ["OK", "INVALID", "STATE", "RACE", "NOMEM", "CUDA", "TIMEOUT", "UNSUPPORTED", "TOO_LARGE"]
@@ -70,8 +72,8 @@ class TuneResult(ctypes.Structure):
 class StepDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("level", ctypes.c_int), ("nsrc", ctypes.c_int),
                 ("ndst", ctypes.c_int), ("npreds", ctypes.c_int), ("prim", ctypes.c_int),
-                ("branch", ctypes.c_int), ("channel", ctypes.c_int),
-                ("nbytes", ctypes.c_ulonglong), ("slot", ctypes.c_ulonglong)]
+                ("branch", ctypes.c_int), ("channel", ctypes.c_int), ("op", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("nbytes", ctypes.c_ulonglong), ("slot", ctypes.c_ulonglong)]
 
 
 _lib = None
@@ -88,7 +90,7 @@ _SIGS = {
     "hiccl_add_fence": (ctypes.c_int, [ctypes.c_void_p]),
     "hiccl_add_collective": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t,
                                             ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
-                                            ctypes.c_int]),
+                                            ctypes.c_int, ctypes.c_int]),
     "hiccl_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int]),
     "hiccl_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -195,10 +197,11 @@ def hiccl_add_fence(comm):
     _check(comm, lib().hiccl_add_fence(comm))
 
 
-def hiccl_add_collective(comm, kind, d: int, send, recv, nranks: int, root: int = 0):
+def hiccl_add_collective(comm, kind, d: int, send, recv, nranks: int, root: int = 0, op=SUM):
     k = COLLECTIVES[kind] if isinstance(kind, str) else int(kind)
+    o = OPS[op] if isinstance(op, str) else int(op)
     _check(comm, lib().hiccl_add_collective(comm, k, int(d), _ptr_array(send, nranks), _ptr_array(recv, nranks),
-                                            int(root)))
+                                            int(root), o))
 
 
 def hiccl_init(comm, hierarchy: Sequence[int], stripe: int = 1, pipeline: int = 1):
@@ -250,6 +253,7 @@ def hiccl_get_step(comm, index: int) -> dict:
     return {
         "kind": "copy" if d.kind == 0 else "reduce", "level": d.level, "nbytes": int(d.nbytes),
         "prim": d.prim, "branch": d.branch, "channel": d.channel, "slot": int(d.slot),
+        "op": OP_NAMES[d.op],
         "srcs": [(int(sr[k]), int(sa[k]), bool(ss[k])) for k in range(ns)],
         "dsts": [(int(dr[k]), int(da[k]), bool(ds[k])) for k in range(nd)],
         "preds": [int(pr[k]) for k in range(npd)],
@@ -329,14 +333,15 @@ class Comm:
     def add_multicast(self, send, recv, count, root, leaves):
         hiccl_add_multicast(self.handle, send, recv, count, root, list(leaves), self.P)
 
-    def add_reduction(self, send, recv, count, leaves, root):
-        hiccl_add_reduction(self.handle, send, recv, count, list(leaves), root, self.P)
+    def add_reduction(self, send, recv, count, leaves, root, op="sum"):
+        hiccl_add_reduction(self.handle, send, recv, count, list(leaves), root, self.P,
+                            OPS[op] if isinstance(op, str) else int(op))
 
     def add_fence(self):
         hiccl_add_fence(self.handle)
 
-    def add_collective(self, kind, d, send, recv, root=0):
-        hiccl_add_collective(self.handle, kind, d, send, recv, self.P, root)
+    def add_collective(self, kind, d, send, recv, root=0, op="sum"):
+        hiccl_add_collective(self.handle, kind, d, send, recv, self.P, root, op)
 
     def init(self, hierarchy, stripe=1, pipeline=1):
         hiccl_init(self.handle, list(hierarchy), stripe, pipeline)

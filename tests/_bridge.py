@@ -13,6 +13,7 @@ from __future__ import annotations
 import numpy as np
 
 from oracle.lowprec import from_acc, to_acc
+from oracle.semantics import combine
 from oracle.model import DTYPES, Multicast
 from paper_2408_05962_gb300 import hiccl as H
 
@@ -66,13 +67,14 @@ def register(prog, addr_of, dtype=None) -> H.Comm:
                 for i in p.leaves:
                     send[i] = addr_of(p.srcs[i])
                 recv[p.root] = addr_of(p.dst)
-                comm.add_reduction(send, recv, p.count * k, p.leaves, p.root)
+                comm.add_reduction(send, recv, p.count * k, p.leaves, p.root, p.op)
     return comm
 
 
 def interpret(comm: H.Comm, fake: FakeAddresses, mem: dict, dtype: str) -> dict:
     """Run the library's step table, in table order, on the NumPy buffers
-    ``mem`` (keyed like the program's buffers)."""
+    ``mem`` (keyed like the program's buffers); a reduce step combines with
+    the operator the table gives it."""
     info = comm.plan_info()
     dt = DTYPES[dtype]
     byte_views = {k: v.view(np.uint8) for k, v in mem.items()}
@@ -89,6 +91,7 @@ def interpret(comm: H.Comm, fake: FakeAddresses, mem: dict, dtype: str) -> dict:
         st = comm.step(i)
         assert all(q < i for q in st["preds"]), "table order must be topological"
         n = st["nbytes"]
+        op = st["op"]
         if st["kind"] == "copy":
             src = view(st["srcs"][0], n).copy()
             for d in st["dsts"]:
@@ -96,11 +99,11 @@ def interpret(comm: H.Comm, fake: FakeAddresses, mem: dict, dtype: str) -> dict:
         elif dtype in ("bf16", "fp8"):
             acc = to_acc(view(st["srcs"][0], n).copy().view(dt), dtype).copy()
             for s in st["srcs"][1:]:
-                acc = (acc + to_acc(view(s, n).copy().view(dt), dtype)).astype(np.float32)
+                acc = combine(acc, to_acc(view(s, n).copy().view(dt), dtype), op).astype(np.float32)
             view(st["dsts"][0], n)[...] = from_acc(acc, dtype).view(np.uint8)
         else:
             acc = view(st["srcs"][0], n).copy().view(dt)
             for s in st["srcs"][1:]:
-                acc = acc + view(s, n).copy().view(dt)
+                acc = combine(acc, view(s, n).copy().view(dt), op)
             view(st["dsts"][0], n)[...] = acc.view(np.uint8)
     return mem

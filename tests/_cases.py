@@ -36,9 +36,11 @@ def random_program(P: int, seed: int, dtype: str = "f32", chunks: int = 3, max_n
     return prog
 
 
-def fill(prog: Program, seed: int) -> dict:
+def fill(prog: Program, seed: int, zero_frac: float = 0.0) -> dict:
     """Random contents for every buffer of ``prog`` (NumPy): uniform[-1, 1]
-    values (encoded for BF16 / FP8 payloads), full-range int32."""
+    values (encoded for BF16 / FP8 payloads), full-range int32; with
+    ``zero_frac`` a random fraction of the elements (f32, i32, bf16) is then
+    set to +0, so that logical-or and max / min see zeros and ties."""
     from oracle.lowprec import encode
     mem = prog.allocate()
     g = np.random.Generator(np.random.PCG64(seed))
@@ -51,4 +53,8 @@ def fill(prog: Program, seed: int) -> dict:
             v[...] = encode(g.uniform(-1, 1, size=v.shape).astype(np.float32), "bf16")
         else:   # fp8 blocks of 128 values
             v[...] = encode(g.uniform(-1, 1, size=v.shape[0] * 128).astype(np.float32), "fp8")
+    if zero_frac > 0 and prog.dtype != "fp8":
+        z = np.random.Generator(np.random.PCG64(seed + 7919))
+        for v in mem.values():
+            v[z.random(v.shape) < zero_frac] = 0
     return mem

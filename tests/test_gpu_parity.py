@@ -21,8 +21,8 @@ def built():
     __graft_entry__.build()
 
 
-def _parity(prog, h, s, m, seed=0, repeats=1, **kw):
-    mem0 = fill(prog, seed)
+def _parity(prog, h, s, m, seed=0, repeats=1, zero_frac=0.0, **kw):
+    mem0 = fill(prog, seed, zero_frac)
     ref = {k: v.copy() for k, v in mem0.items()}
     S.run_program(prog, ref, h)
     outs, comm = run_on_gpu(prog, h, s, m, mem0, repeats=repeats, **kw)
@@ -115,3 +115,18 @@ def test_options_do_not_change_results():
     for opts in ({H.OPT_ORDER: 1}, {H.OPT_ITEM_BYTES: 4096}, {H.OPT_ITEM_BYTES: 1 << 20},
                  {H.OPT_CTAS_PER_SM: 1}):
         _parity(prog, [4, 4], 4, 4, options=opts)
+
+
+OPS_CASES = [(op, dt) for op in ("max", "min") for dt in ("f32", "i32", "bf16")] + [("lor", "i32")]
+
+
+@pytest.mark.parametrize("op,dtype", OPS_CASES)
+@pytest.mark.parametrize("name", ["allreduce", "reduce", "reducescatter"])
+@pytest.mark.parametrize("P,h,s,m,d,mis", [(8, [2, 4], 4, 3, 2053, 0), (16, [16], 2, 2, 1031, 0),
+                                           (12, [2, 2, 3], 3, 2, 999, 1)])
+def test_reduction_operators(op, dtype, name, P, h, s, m, d, mis):
+    """Max, min and logical or (Sec. 3.1) through every fold path: shared-memory
+    folds (fan-in <= 8, aligned), vector-load folds (fan-in 16) and the
+    element path (buffers one element off 16-byte alignment)."""
+    _parity(PR.BUILDERS[name](P, d, dtype=dtype, op=op), h, s, m, seed=P + s + m, zero_frac=0.25,
+            misalign_elems=mis)

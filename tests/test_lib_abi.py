@@ -92,12 +92,24 @@ def test_race_rejected():
     c2.plan([2, 2])
 
 
-def test_unsupported_op():
+def test_reduction_operators_checked():
     c = _comm(2)
     a = [0x1000, 0x2000]
     with pytest.raises(H.HicclError) as e:
-        H.hiccl_add_reduction(c.handle, a, a, 4, [0, 1], 0, 2, op=3)
+        H.hiccl_add_reduction(c.handle, a, a, 4, [0, 1], 0, 2, op=7)
+    assert e.value.status == H.ERR_INVALID
+    with pytest.raises(H.HicclError) as e:           # logical or on floats
+        H.hiccl_add_reduction(c.handle, a, a, 4, [0, 1], 0, 2, op=H.LOR)
     assert e.value.status == H.ERR_UNSUPPORTED
+    for op in (H.SUM, H.MAX, H.MIN):
+        H.hiccl_add_reduction(c.handle, a, a, 4, [0, 1], 0, 2, op=op)
+        c.add_fence()
+    f8 = H.Comm(2, "fp8")
+    with pytest.raises(H.HicclError) as e:
+        H.hiccl_add_reduction(f8.handle, a, a, 128, [0, 1], 0, 2, op=H.MAX)
+    assert e.value.status == H.ERR_UNSUPPORTED
+    i32 = H.Comm(2, "i32")
+    H.hiccl_add_reduction(i32.handle, a, a, 4, [0, 1], 0, 2, op=H.LOR)
 
 
 def test_options():

@@ -23,7 +23,7 @@ def built():
     B.build()
 
 
-def _check(prog, h, s, m, seed=0, interpret_steps=True):
+def _check(prog, h, s, m, seed=0, interpret_steps=True, zero_frac=0.0):
     fake = FakeAddresses(prog)
     comm = register(prog, fake.addr)
     comm.plan(h, s, m)
@@ -34,7 +34,7 @@ def _check(prog, h, s, m, seed=0, interpret_steps=True):
     assert info["stages"] == plan.stages()
     assert info["steps"] == len(plan.ops)
     if interpret_steps:
-        mem0 = fill(prog, seed)
+        mem0 = fill(prog, seed, zero_frac)
         ref = {k: v.copy() for k, v in mem0.items()}
         S.run_program(prog, ref, h)
         got = interpret(comm, fake, {k: v.copy() for k, v in mem0.items()}, prog.dtype)
@@ -154,6 +154,42 @@ def test_native_composition_equals_primitive_composition(name):
     assert comm.hbm_bytes() == ref_comm.hbm_bytes()
     assert comm.level_bytes() == ref_comm.level_bytes()
     mem0 = fill(prog, 4)
+    ref = {k: v.copy() for k, v in mem0.items()}
+    S.run_program(prog, ref, h)
+    got = interpret(comm, fake, {k: v.copy() for k, v in mem0.items()}, prog.dtype)
+    for k in ref:
+        assert np.array_equal(ref[k], got[k]), k
+
+
+OPS_CASES = [(op, dt) for op in ("max", "min") for dt in ("f32", "i32", "bf16")] + [("lor", "i32")]
+
+
+@pytest.mark.parametrize("op,dtype", OPS_CASES)
+@pytest.mark.parametrize("name", ["reduce", "reducescatter", "allreduce", "allreduce_single"])
+@pytest.mark.parametrize("P,h,s,m", [(8, [2, 4], 1, 1), (8, [2, 4], 4, 3), (12, [2, 2, 3], 3, 2)])
+def test_reduction_operators(op, dtype, name, P, h, s, m):
+    """Max, min and logical or (Sec. 3.1): the step table carries the
+    operator of each reduce and reproduces the oracle bit for bit (inputs
+    with a quarter zeros, so that logical or sees both outcomes)."""
+    prog = PR.BUILDERS[name](P, 29, dtype=dtype, op=op)
+    comm = _check(prog, h, s, m, seed=P + s, zero_frac=0.25)
+    ops = {st["op"] for st in comm.steps() if st["kind"] == "reduce"}
+    assert ops == {op}
+
+
+@pytest.mark.parametrize("name,op", [("allreduce", "max"), ("reducescatter", "min"), ("reduce", "max"),
+                                     ("allreduce_single", "min")])
+def test_native_composition_operator(name, op):
+    """hiccl_add_collective passes its operator to every reduction it registers."""
+    from paper_2408_05962_gb300 import hiccl as H
+    P, d, h = 8, 13, [2, 4]
+    prog = PR.BUILDERS[name](P, d, op=op)
+    fake = FakeAddresses(prog)
+    comm = H.Comm(P, "f32")
+    comm.add_collective(name, d, [fake.base[("send", r)] for r in range(P)],
+                        [fake.base[("recv", r)] for r in range(P)], root=0, op=op)
+    comm.plan(h, 2, 2)
+    mem0 = fill(prog, 5)
     ref = {k: v.copy() for k, v in mem0.items()}
     S.run_program(prog, ref, h)
     got = interpret(comm, fake, {k: v.copy() for k, v in mem0.items()}, prog.dtype)
