@@ -1,8 +1,8 @@
 """The optimizer of paper Sec. 4: striping, tree factorization, pipelining.
 
-Each primitive is factorized, in the paper's order (Sec. 4.4: striping first,
-then the tree; the ring is not used, i.e. ``ring(1)``), into point-to-point
-operations within one level of the hierarchy:
+Each primitive is factorized, in the paper's order (Sec. 4.4: striping, then
+the ring, then the tree), into point-to-point operations within one level of
+the hierarchy:
 
 * a *copy* moves n elements from one rank to one or more ranks -- one
   multicast hop of a tree node (the holder forwards to the representatives
@@ -44,6 +44,17 @@ Readings (the paper is silent or ambiguous; each is stated once):
    later epoch follows exactly the earlier-epoch operations whose user-buffer
    ranges it reads after they write, writes after they read, or writes after
    they write.
+6. Ring (Sec. 4.4).  ``ring(n)`` chains the n nodes -- the groups of P/n
+   ranks, which must be the groups of one hierarchy level
+   (``hierarchy.ring_level``) -- starting at the node of the branch's stripe
+   rank and going up cyclically; nodes without leaves are skipped.  The rank
+   entering a node is chosen like a representative (reading 1) from the
+   previous node's entry rank.  A multicast hops node to node and each entry
+   rank multicasts inside its node with the tree; a reduction mirrors it:
+   the last node's tree fold travels backwards, and every other entry rank
+   folds its node's subgroup partials followed by the incoming partial in
+   one reduce (the ring order of ``semantics``).  With n > 1 the stripe may
+   not exceed the node size, so that all branches start in the root's node.
 
 Byte accounting.  ``level_bytes[l]``: for every copy destination, and every
 reduce input, that sits on another rank, n elements cross the level of the
@@ -56,7 +67,7 @@ import bisect
 from dataclasses import dataclass, field
 from math import ceil
 
-from .hierarchy import check, group_sizes, level_of
+from .hierarchy import check, group_sizes, level_of, ring_level
 from .model import DTYPES, QUANTUM, Multicast, Program, Ref
 
 
@@ -85,6 +96,7 @@ class Plan:
     ops: list
     scratch: dict             # key -> length
     esize: int
+    ring: int = 1
 
     # ---- accounting -------------------------------------------------------
     def level_bytes(self) -> list:
@@ -136,13 +148,17 @@ def piece_bounds(count: int, parts: int, quantum: int) -> list:
 
 
 class Factorizer:
-    def __init__(self, prog: Program, hierarchy, stripe: int = 1, pipeline: int = 1):
+    def __init__(self, prog: Program, hierarchy, stripe: int = 1, pipeline: int = 1, ring: int = 1):
         self.prog = prog
         self.h = check(hierarchy, prog.P)
         self.L = len(self.h)
         self.G = group_sizes(self.h)
         if stripe < 1 or stripe > prog.P or pipeline < 1:
             raise ValueError("stripe must be in [1, P] and pipeline >= 1")
+        self.ring = int(ring)
+        self.lr = ring_level(self.h, self.ring)      # level of the ring's nodes
+        if self.ring > 1 and stripe > self.G[self.lr]:
+            raise ValueError("with a ring, the stripe may not exceed the node size")
         self.s = stripe
         self.m = pipeline
         self.ops: list = []
@@ -233,6 +249,84 @@ class Factorizer:
                         [o for _, _, o in inputs])
         return out, op
 
+    # ---- ring across nodes (Sec. 4.4), tree inside them ----------------------------
+    def _node_leaves(self, a, leaves):
+        N = self.G[self.lr]
+        return [r for r in leaves if a * N <= r < (a + 1) * N]
+
+    def _mcast_ring(self, holder, src: Ref, src_op, leaves, dst_of, n):
+        if self.ring == 1:
+            self._mcast_tree(0, 0, holder, src, src_op, leaves, dst_of, n)
+            return
+        N = self.G[self.lr]
+        a0 = holder // N
+        self._mcast_tree(self.lr, a0 * N, holder, src, src_op, self._node_leaves(a0, leaves), dst_of, n)
+        for i in range(1, self.ring):
+            a = (a0 + i) % self.ring
+            nl = self._node_leaves(a, leaves)
+            if not nl:
+                continue
+            e = self._rep(a * N, N, holder, nl)
+            hop = self._emit("copy", [(holder, src)], [(e, dst_of(e))], n, self._lvl(holder, e), [src_op])
+            self._mcast_tree(self.lr, a * N, e, dst_of(e), hop, [r for r in nl if r != e], dst_of, n)
+            holder, src, src_op = e, dst_of(e), hop
+
+    def _red_ring(self, target, leaves, src_of, out, n):
+        """The ring-order fold of ``leaves`` at ``target`` (semantics, ring
+        order); returns (Ref, producing op or None) like ``_red_tree``."""
+        if self.ring == 1:
+            return self._red_tree(0, 0, target, leaves, src_of, out, n)
+        N = self.G[self.lr]
+        a0 = target // N
+        chain = []
+        prev = target
+        for i in range(self.ring):
+            a = (a0 + i) % self.ring
+            nl = self._node_leaves(a, leaves)
+            if not nl:
+                continue
+            e = target if a == a0 else self._rep(a * N, N, prev, nl)
+            chain.append((a, nl, e))
+            prev = e
+        inc = None
+        for idx in range(len(chain) - 1, -1, -1):
+            a, nl, e = chain[idx]
+            o = out if (idx == 0 and e == target) else None
+            if inc is None:
+                ref, op = self._red_tree(self.lr, a * N, e, nl, src_of, o, n)
+            else:
+                ref, op = self._red_node(a, e, nl, src_of, o, n, inc)
+            inc = (e, ref, op)
+        e, ref, op = inc
+        if e == target:
+            return ref, op
+        dst = out if out is not None else self._new_scratch(n)
+        return dst, self._emit("copy", [(e, ref)], [(target, dst)], n, self._lvl(e, target), [op])
+
+    def _red_node(self, a, target, nl, src_of, out, n, inc):
+        """One ring node that is not the chain's last: fold the node's
+        subgroup partials, then the partial ``inc`` = (rank, Ref, op) received
+        from the next node, into one reduce at ``target``."""
+        if self.lr == self.L:
+            inputs = [(target, src_of(target), None)]
+        else:
+            sub = self.G[self.lr + 1]
+            inputs = []
+            for q in range(self.h[self.lr]):
+                qb = a * self.G[self.lr] + q * sub
+                ql = [r for r in nl if qb <= r < qb + sub]
+                if not ql:
+                    continue
+                rep = target if qb <= target < qb + sub else self._rep(qb, sub, target, ql)
+                inputs.append((rep,) + self._red_tree(self.lr + 1, qb, rep, ql, src_of, None, n))
+        inputs.append(inc)
+        if out is None:
+            out = self._new_scratch(n)
+        level = min(lv for lv in (self._lvl(r, target) for r, _, _ in inputs) if lv is not None)
+        op = self._emit("reduce", [(r, ref) for r, ref, _ in inputs], [(target, out)], n, level,
+                        [o for _, _, o in inputs])
+        return out, op
+
     # ---- one primitive -----------------------------------------------------------
     def _multicast(self, p: Multicast):
         if p.count == 0:
@@ -266,8 +360,7 @@ class Factorizer:
                     holder_op = self._emit("copy", [(p.root, src)], [(k, dst)], n, self._lvl(p.root, k), [])
                     holder_src = dst
                     branch = sorted(j for j in leaves_k if j != k)
-                self._mcast_tree(0, 0, k, holder_src, holder_op, branch,
-                                 lambda r, lo=lo: p.dsts[r].shift(lo), n)
+                self._mcast_ring(k, holder_src, holder_op, branch, lambda r, lo=lo: p.dsts[r].shift(lo), n)
 
     def _reduction(self, p):
         if p.count == 0:
@@ -286,9 +379,9 @@ class Factorizer:
                 k = ks[b]
                 src_of = (lambda r, lo=lo: p.srcs[r].shift(lo))
                 if k == p.root:
-                    self._red_tree(0, 0, k, list(p.leaves), src_of, final, n)
+                    self._red_ring(k, list(p.leaves), src_of, final, n)
                 else:
-                    ref, op = self._red_tree(0, 0, k, list(p.leaves), src_of, None, n)
+                    ref, op = self._red_ring(k, list(p.leaves), src_of, None, n)
                     self._emit("copy", [(k, ref)], [(p.root, final)], n, self._lvl(k, p.root),
                                [op])
 
@@ -309,7 +402,7 @@ class Factorizer:
             if e > 0:
                 self._fence_deps(first)
         return Plan(self.prog.P, self.h, self.s, self.m, self.prog.dtype, self.ops,
-                    dict(self.scratch), DTYPES[self.prog.dtype].itemsize)
+                    dict(self.scratch), DTYPES[self.prog.dtype].itemsize, self.ring)
 
     def _fence_deps(self, first: int):
         """Reading 5: dependencies of the ops emitted from ``first`` on (one
@@ -351,5 +444,5 @@ def _op_accesses(op: Op):
     return out
 
 
-def factorize(prog: Program, hierarchy, stripe: int = 1, pipeline: int = 1) -> Plan:
-    return Factorizer(prog, hierarchy, stripe, pipeline).run()
+def factorize(prog: Program, hierarchy, stripe: int = 1, pipeline: int = 1, ring: int = 1) -> Plan:
+    return Factorizer(prog, hierarchy, stripe, pipeline, ring).run()

@@ -41,6 +41,21 @@ def level_of(a: int, b: int, hierarchy) -> int | None:
     raise AssertionError("unreachable")
 
 
+def ring_level(hierarchy, ring: int) -> int:
+    """Level whose groups are the conceptual nodes of ``ring(n)`` (Sec. 4.4).
+
+    Reading: the ring chains the n groups of P/n ranks, which must be the
+    groups of one level of the hierarchy, i.e. n = f_0 * ... * f_{l-1} for
+    some l; the ring replaces the tree above that level and the tree
+    factorizes inside each node.  ``ring(1)`` is the plain tree (l = 0)."""
+    G = group_sizes(hierarchy)
+    n = int(ring)
+    for l, g in enumerate(G):
+        if n >= 1 and g * n == G[0]:
+            return l
+    raise ValueError(f"ring({ring}) does not match a level of hierarchy {list(hierarchy)}")
+
+
 def all_factorizations(P: int, max_levels: int = 4) -> list[list[int]]:
     """Every ordered factorization of P into factors >= 2 (plus [P] itself)."""
     out = []

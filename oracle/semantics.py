@@ -16,12 +16,20 @@ Readings (the paper is silent on these; each is stated once here):
 * A multicast whose root is also a leaf delivers to the root's own
   destination (nothing to do when source and destination coincide, the
   "dashed edges" of Fig. 4).
+* Ring order (Sec. 4.4).  With ``ring(n)`` the n nodes (the groups of P/n
+  ranks) form a chain that starts at the root's node and visits the nodes in
+  ascending order, cyclically; nodes without leaves are skipped.  Partial
+  results travel the chain backwards, so the reduction is a right fold over
+  the chain: the last node contributes its nested fold; every earlier node
+  folds its own subgroups' contributions and then the partial received from
+  its successor (one reduce step, encoded once).  The result depends on the
+  root's node; it equals the tree's for order-free arithmetic (int32).
 """
 from __future__ import annotations
 
 import numpy as np
 
-from .hierarchy import check, group_sizes
+from .hierarchy import check, group_sizes, ring_level
 from .lowprec import from_acc, to_acc
 from .model import Multicast, Program, Reduction
 
@@ -46,7 +54,8 @@ def combine(a: np.ndarray, b: np.ndarray, op: str = "sum") -> np.ndarray:
     raise ValueError(op)
 
 
-def nested_fold(values: dict, hierarchy, dtype: str | None = None, op: str = "sum") -> np.ndarray:
+def nested_fold(values: dict, hierarchy, dtype: str | None = None, op: str = "sum", ring: int = 1,
+                root: int = 0) -> np.ndarray:
     """Hierarchical nested fold of ``values`` (rank -> array) over ``hierarchy``.
 
     S(rank r) = values[r]; S(group) = the left fold over the S(subgroup) of
@@ -57,7 +66,9 @@ def nested_fold(values: dict, hierarchy, dtype: str | None = None, op: str = "su
     binary32, folded with binary32 adds and the group's result encoded once
     (lowprec); a group with a single contributing subgroup passes its value
     through unchanged (Sec. 3.1: with one leaf the operation is omitted).
-    ``op`` selects the combining operation (``combine``).
+    ``op`` selects the combining operation (``combine``).  With ``ring`` > 1
+    the levels above the ring's nodes are folded along the chain that starts
+    at ``root``'s node (ring order, above) instead.
     """
     if not values:
         raise ValueError("empty leaf set")
@@ -78,6 +89,9 @@ def nested_fold(values: dict, hierarchy, dtype: str | None = None, op: str = "su
                 parts.append(S(level + 1, lo, inside))
         if len(parts) == 1:
             return parts[0].copy()
+        return fold(parts)
+
+    def fold(parts):
         if not low:
             acc = parts[0].copy()
             for p in parts[1:]:
@@ -88,7 +102,39 @@ def nested_fold(values: dict, hierarchy, dtype: str | None = None, op: str = "su
             acc = combine(acc, to_acc(p, dtype), op).astype(np.float32)
         return from_acc(acc, dtype)
 
-    return S(0, 0, ranks)
+    if ring == 1:
+        return S(0, 0, ranks)
+    lr = ring_level(h, ring)
+    N = G[lr]
+    a0 = root // N
+    chain = []
+    for i in range(ring):
+        a = (a0 + i) % ring
+        inside = [r for r in ranks if a * N <= r < (a + 1) * N]
+        if inside:
+            chain.append((a, inside))
+
+    def node_parts(a, members):
+        """Contributions the node folds: its non-empty subgroups (the node's
+        own value when a node is a single rank)."""
+        if lr == len(h):
+            return [values[a]]
+        sub = G[lr + 1]
+        out = []
+        for q in range(h[lr]):
+            lo = a * N + q * sub
+            inside = [r for r in members if lo <= r < lo + sub]
+            if inside:
+                out.append(S(lr + 1, lo, inside))
+        return out
+
+    acc = None
+    for a, members in reversed(chain):
+        if acc is None:
+            acc = S(lr, a * N, members)
+        else:
+            acc = fold(node_parts(a, members) + [acc])
+    return acc
 
 
 def fsum64(values: list) -> np.ndarray:
@@ -114,26 +160,27 @@ def apply_multicast(p: Multicast, mem: dict) -> None:
         _view(mem, p.dsts[j], p.count)[...] = src
 
 
-def apply_reduction(p: Reduction, mem: dict, hierarchy, dtype: str | None = None) -> None:
-    """R(i, j, d, sum): the root's destination receives the fixed-order sum of
+def apply_reduction(p: Reduction, mem: dict, hierarchy, dtype: str | None = None, ring: int = 1) -> None:
+    """R(i, j, d, op): the root's destination receives the fixed-order fold of
     the leaves' d elements (Sec. 3.1)."""
     if p.count == 0:
         return
     vals = {i: _view(mem, p.srcs[i], p.count).copy() for i in p.leaves}
-    _view(mem, p.dst, p.count)[...] = nested_fold(vals, hierarchy, dtype, p.op)
+    _view(mem, p.dst, p.count)[...] = nested_fold(vals, hierarchy, dtype, p.op, ring, p.root)
 
 
-def run_program(prog: Program, mem: dict, hierarchy) -> dict:
+def run_program(prog: Program, mem: dict, hierarchy, ring: int = 1) -> dict:
     """Execute the program's epochs in order; inside an epoch the (race-free)
     primitives are applied in registration order, which Sec. 3.2 makes
-    irrelevant."""
+    irrelevant.  ``ring`` selects the ring order of the sums (Sec. 4.4)."""
     check(hierarchy, prog.P)
+    ring_level(hierarchy, ring)
     for epoch in prog.epochs:
         for p in epoch:
             if isinstance(p, Multicast):
                 apply_multicast(p, mem)
             else:
-                apply_reduction(p, mem, hierarchy, prog.dtype)
+                apply_reduction(p, mem, hierarchy, prog.dtype, ring)
     return mem
 
 

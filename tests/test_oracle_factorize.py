@@ -66,6 +66,58 @@ def test_golden_fig1_direct_vs_hierarchical():
         assert n == int(crossing)
 
 
+def test_golden_ring_4x3():
+    """Sec. 4.4: ring(4) with stripe(3) over {4,3}: the inter-node hops of each
+    stripe form the chain N0 -> N1 -> N2 -> N3, and five stages."""
+    rows = _read_golden("ring_4x3.txt")
+    prog = PR.broadcast(12, 6, root=0)
+    for r in rows:
+        if r[0] == "stages":
+            ring, stripe, n = int(r[1]), int(r[2]), int(r[3])
+            assert factorize(prog, [4, 3], stripe=stripe, ring=ring).stages() == n
+    plan = factorize(prog, [4, 3], stripe=3, ring=4)
+    inter = {(a, b) for lv, a, b in _hops(plan) if lv == 0}
+    want = set()
+    for r in rows:
+        if r[0] == "chain":
+            ranks = [int(v) for v in r[1:]]
+            want |= set(zip(ranks, ranks[1:]))
+    assert inter == want
+    # the tree on the same machine: one top-level hop per stripe into every node
+    tree = factorize(prog, [4, 3], stripe=3)
+    assert {(a, b) for lv, a, b in _hops(tree) if lv == 0} == {(k, k + 3 * i) for k in range(3) for i in (1, 2, 3)}
+    assert tree.stages() == 3          # stage 0, the top level, inside the nodes
+
+
+def test_ring_level_volumes_and_chain_start():
+    """A ring over all nodes from node 0 crosses each level as often as the
+    tree (consecutive nodes a, a+1 first differ at level l for
+    prod(f_0..f_{l-1}) * (f_l - 1) values of a); from another node the chain
+    wraps: for {2,2,3} from node 1 it runs N1->N2 (level 0), N2->N3 (level 1),
+    N3->N0 (level 0)."""
+    d, e = 8, 4
+    for h, ring in (([2, 2, 3], 4), ([4, 3], 4), ([2, 3, 2], 2), ([2, 3, 2], 6), ([3, 2, 2], 12)):
+        P = prod(h)
+        G = group_sizes(h)
+        b = d * P * e
+        closed = [prod(h[:l]) * (h[l] - 1) * b for l in range(len(h))]
+        assert factorize(PR.broadcast(P, d, root=0), h, ring=ring).level_bytes() == closed
+        assert factorize(PR.reduce(P, d, root=0), h, ring=ring).level_bytes() == closed
+    plan = factorize(PR.broadcast(12, d, root=4), [2, 2, 3], ring=4)
+    inter = sorted((lv, a, b) for lv, a, b in _hops(plan) if lv < 2)
+    assert inter == [(0, 4, 7), (0, 10, 1), (1, 7, 10)]
+
+
+def test_ring_rejects_bad_shapes():
+    prog = PR.broadcast(12, 2)
+    with pytest.raises(ValueError):
+        factorize(prog, [4, 3], ring=3)            # 4-rank nodes are not a level of {4,3}
+    with pytest.raises(ValueError):
+        factorize(prog, [4, 3], stripe=4, ring=4)  # stripe beyond the node
+    factorize(prog, [4, 3], stripe=3, ring=4)
+    factorize(prog, [4, 3], stripe=4, ring=1)
+
+
 def test_striped_tree_is_multi_rail():
     """Sec. 4.3: with stripe(3) on {2,2,3} every GPU of the root node sends one
     piece across the top level (g0, g1, g2 -> g6, g7, g8)."""
@@ -250,6 +302,39 @@ def test_simulator_matches_semantics(P):
                         assert np.array_equal(ref[k], got[k]), (h, s, m, dtype, k)
                     cases += 1
     assert cases > 0
+
+
+def _rings(h):
+    """Every ring(n) that matches a level of h: n = f_0 * ... * f_{l-1}."""
+    return sorted({prod(h[:l]) for l in range(len(h) + 1)})
+
+
+@pytest.mark.parametrize("P", [2, 4, 6, 8, 12])
+def test_ring_simulator_matches_semantics(P):
+    """Every ring of every hierarchy: the simulated schedule (random
+    dependency-respecting order) reproduces the ring-order semantics bit for
+    bit, for random programs, roots and leaf sets."""
+    cases = 0
+    for h in all_factorizations(P, max_levels=3):
+        node_sizes = group_sizes(h)
+        for ring in _rings(h):
+            N = P // ring
+            for s in sorted({1, 2, N} & set(range(1, (N if ring > 1 else P) + 1))):
+                for m in (1, 2):
+                    dtype = ("f32", "i32", "bf16")[(P + ring + s + m) % 3]
+                    seed = hash((P, tuple(h), ring, s, m)) % 100000
+                    prog = _random_program(P, seed, dtype)
+                    if S.find_race(prog) is not None:
+                        continue
+                    mem0 = _init(prog, seed)
+                    ref = {k: v.copy() for k, v in mem0.items()}
+                    S.run_program(prog, ref, h, ring)
+                    got = {k: v.copy() for k, v in mem0.items()}
+                    simulate(factorize(prog, h, s, m, ring), got, order_seed=seed)
+                    for k in ref:
+                        assert np.array_equal(ref[k].view(np.uint8), got[k].view(np.uint8)), (h, ring, s, m, k)
+                    cases += 1
+    assert cases > 0 and node_sizes
 
 
 @pytest.mark.parametrize("name", PR.SEVEN + ("reduce", "allreduce_single"))

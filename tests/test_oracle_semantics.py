@@ -286,3 +286,32 @@ def test_single_leaf_reduction_omits_the_operation():
     is omitted (a logical or of one nonzero value is the value itself)."""
     x = {3: np.array([5, 0, -2], np.int32)}
     assert list(S.nested_fold(x, [2, 2], None, "lor")) == [5, 0, -2]
+
+
+def test_ring_order_fold():
+    """Sec. 4.4 ring order on three single-rank nodes (hierarchy {3},
+    ring(3)) with x = (1e8, -1e8, 1) in binary32, where -1e8 + 1 and 1 + 1e8
+    round back to -1e8 and 1e8: the chain from the root's node folds from its
+    far end backwards.  Root 0: x0 + (x1 + x2) = 0; root 1: x1 + (x2 + x0) = 0;
+    root 2: x2 + (x0 + x1) = 1; the tree (ring(1)) gives (x0 + x1) + x2 = 1."""
+    x = {0: np.array([1e8], np.float32), 1: np.array([-1e8], np.float32), 2: np.array([1.0], np.float32)}
+    assert float(S.nested_fold(x, [3])[0]) == 1.0
+    assert [float(S.nested_fold(x, [3], ring=3, root=r)[0]) for r in range(3)] == [0.0, 0.0, 1.0]
+    # nodes of two ranks ({2,2}, ring(2)), root in node 1: (x2 + x3) + (x0 + x1)
+    y = {0: np.array([1.0], np.float32), 1: np.array([1e8], np.float32),
+         2: np.array([-1e8], np.float32), 3: np.array([1.0], np.float32)}
+    assert float(S.nested_fold(y, [2, 2], ring=2, root=3)[0]) == 0.0      # -1e8 + 1e8
+    assert float(S.nested_fold(y, [2, 2], ring=2, root=0)[0]) == 0.0      # 1e8 + -1e8
+    # a node with one contributing subgroup still folds the incoming partial
+    z = {1: np.array([3.0], np.float32), 2: np.array([4.0], np.float32)}
+    assert float(S.nested_fold(z, [2, 2], ring=2, root=0)[0]) == 7.0
+
+
+@pytest.mark.parametrize("h,ring", [([2, 4], 2), ([2, 2, 2], 4), ([4, 2], 8), ([2, 3], 2)])
+def test_ring_fold_int32_equals_tree(h, ring):
+    """Wrapping int32 addition is order-free: every ring order gives the tree's sum."""
+    P = int(np.prod(h))
+    x = int_ranks(P, 64, seed=ring)
+    for root in range(P):
+        vals = {r: x[r] for r in range(P)}
+        assert np.array_equal(S.nested_fold(vals, h, ring=ring, root=root), S.nested_fold(vals, h))
