@@ -349,6 +349,8 @@ def run_ours(args):
             comm.set_option(H.OPT_CTAS_PER_SM, args.ctas_per_sm)
         if args.threads:
             comm.set_option(H.OPT_THREADS, args.threads)
+        if args.ring > 1:
+            comm.set_option(H.OPT_RING, args.ring)
         C.compose(comm, kind, d, b.send_ptrs(), b.recv_ptrs())
         comm.init(hier, stripe, pipe)
         rd, wr = comm.hbm_bytes()
@@ -437,8 +439,9 @@ def run_ours(args):
         "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": statistics.mean(step_ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
-        "data": "synthetic", "config": workload_config({"parallelism": f"replicas{world}", "payload": dtype},
-                                                       args.workload),
+        "data": "synthetic", "config": workload_config(
+            {"parallelism": f"replicas{world}", "payload": dtype, **({"ring": args.ring} if args.ring > 1 else {})},
+            args.workload),
         "roofline": {"bound": "hbm", "achieved": gbs / world, "peak": peak, "unit": "GB/s",
                      "frac": gbs / world / peak, "peak_source": peak_kind,
                      "traffic": traffic, "kernel": "hiccl_exec_kernel"},
@@ -660,6 +663,7 @@ def main(argv=None):
     ap.add_argument("--kinds", default="", help="comma-separated subset of the seven collectives (profiling)")
     ap.add_argument("--threads", type=int, default=0, help="executor threads per CTA (0: library default)")
     ap.add_argument("--order", type=int, default=None, help="work order: 0 pipeline slots, 1 stage depth")
+    ap.add_argument("--ring", type=int, default=1, help="ring(n) of the hybrid ring+tree topology (1: tree)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         run_reference(args)

@@ -181,7 +181,9 @@ typedef struct {
  * timed runs, median of CUDA-event times): executor knobs (work order, item
  * size) always; with (flags & 1) first the stripe s (its current value, 1,
  * and the bottom hierarchy factor) and pipeline depth m (1, 2, 4, 8), the
- * paper's optimization parameters (Sec. 4.1), with the executor defaults.
+ * paper's optimization parameters (Sec. 4.1), with the executor defaults;
+ * with a ring (HICCL_OPT_RING > 1) only stripes up to the node size.  None of
+ * these changes a result bit; the ring, which does, is not tuned.
  * The communicator ends up initialized with the best configuration, which
  * *best receives (may be NULL).  The trials execute the collective: receive
  * buffers are overwritten.  Blocking. */
@@ -276,13 +278,24 @@ typedef enum {
   HICCL_OPT_ORDER = 3,        /* work order: 0 pipeline slots, 1 stage depth (default)    */
   HICCL_OPT_THREADS = 4,      /* threads per executor CTA: 128, 256 (default), 512       */
   HICCL_OPT_TRACE = 5,        /* 1: record per-item timestamps (hiccl_get_trace); default 0 */
-  HICCL_OPT_SLOT_ITEMS = 6    /* items a pipeline slot is spread over (default 1024)      */
+  HICCL_OPT_SLOT_ITEMS = 6,   /* items a pipeline slot is spread over (default 1024)      */
+  HICCL_OPT_RING = 7          /* ring(n) of Sec. 4.4: n nodes chained (default 1, tree)    */
 } hiccl_option_t;
 
 /* Set an option.  TIMEOUT_NS, CTAS_PER_SM and THREADS apply to the next start;
- * ITEM_BYTES, ORDER and SLOT_ITEMS must be set before hiccl_init / hiccl_plan,
- * TRACE before hiccl_init.  A work item holds at most
- * max(4096, min(ITEM_BYTES, bytes of its slot / SLOT_ITEMS)) bytes of steps. */
+ * ITEM_BYTES, ORDER, SLOT_ITEMS and RING must be set before hiccl_init /
+ * hiccl_plan, TRACE before hiccl_init.  A work item holds at most
+ * max(4096, min(ITEM_BYTES, bytes of its slot / SLOT_ITEMS)) bytes of steps.
+ * RING = n (Sec. 4.4, hybrid ring+tree): the n nodes of P/n ranks, which must
+ * be the groups of one hierarchy level (n = f_0 * ... * f_{l-1}; checked at
+ * planning, HICCL_ERR_INVALID otherwise), are chained starting at the root's
+ * node and in ascending node order, cyclically, skipping nodes without
+ * leaves; the tree factorizes inside each node.  A multicast hops node to
+ * node; a reduction folds along the chain backwards: the last node's tree
+ * fold is sent to the previous node, whose entry rank folds its own
+ * subgroups' partials followed by the incoming partial, and so on back to the
+ * root's node -- so with n > 1 the floating-point sum order depends on the
+ * root's node.  The stripe may not exceed P/n when n > 1. */
 hiccl_status_t hiccl_set_option(hiccl_comm_t comm, hiccl_option_t opt, long long value);
 
 /* Executor trace of the last start (HICCL_OPT_TRACE set before hiccl_init).

@@ -177,6 +177,7 @@ struct hiccl_comm {
   int order = 1;
   unsigned long long slot_items = 1024;
   int trace = 0;
+  int ring = 1;                       // ring(n) of Sec. 4.4; 1 = tree only
   hiccl::Plan plan;
   hiccl::DevState *dev = nullptr;
   std::string err;

@@ -79,6 +79,7 @@ struct Builder {
   std::vector<long long> G;   // G[l] = prod h[l..]
   int L;
   int s, m;
+  int ring = 1, lr = 0;       // ring(n) and the level of its nodes
   std::vector<HStep> steps;
   std::vector<Loc> locs;
   std::vector<std::pair<uint32_t, uint32_t>> edges;   // (pred, succ) in emission order
@@ -271,6 +272,90 @@ struct Builder {
     return {o, st};
   }
 
+  // ---- ring across the nodes of level lr (Sec. 4.4), tree inside them ----------
+  // chain order: the holder's node first, then ascending node index, cyclically
+  std::vector<int> node_leaves(long long a, const std::vector<int> &leaves) const {
+    return inside(leaves, a * G[lr], (a + 1) * G[lr]);
+  }
+
+  void mcast_ring(int holder, Loc src, int src_step, const std::vector<int> &leaves) {
+    if (ring == 1) {
+      mcast_tree(0, 0, holder, src, src_step, leaves);
+      return;
+    }
+    const long long N = G[lr], a0 = holder / N;
+    mcast_tree(lr, a0 * N, holder, src, src_step, node_leaves(a0, leaves));
+    for (int i = 1; i < ring; ++i) {
+      const long long a = (a0 + i) % ring;
+      std::vector<int> nl = node_leaves(a, leaves);
+      if (nl.empty()) continue;
+      const int e = pick_rep(a * N, N, holder, nl);
+      const int hop = emit(OP_COPY, {src}, {recv_loc(e)}, level_of(holder, e), {src_step});
+      std::vector<int> rest;
+      for (int r : nl)
+        if (r != e) rest.push_back(r);
+      mcast_tree(lr, a * N, e, recv_loc(e), hop, rest);
+      holder = e;
+      src = recv_loc(e);
+      src_step = hop;
+    }
+  }
+
+  // the fold along the chain: the last node's tree fold travels back, each
+  // earlier entry rank folds its node's partials and then the incoming one
+  std::pair<Loc, int> red_ring(int target, const std::vector<int> &leaves, const Loc *out) {
+    if (ring == 1) return red_tree(0, 0, target, leaves, out);
+    const long long N = G[lr], a0 = target / N;
+    struct Node { long long a; std::vector<int> nl; int e; };
+    std::vector<Node> chain;
+    int prev = target;
+    for (int i = 0; i < ring; ++i) {
+      const long long a = (a0 + i) % ring;
+      std::vector<int> nl = node_leaves(a, leaves);
+      if (nl.empty()) continue;
+      const int e = a == a0 ? target : pick_rep(a * N, N, prev, nl);
+      chain.push_back(Node{a, std::move(nl), e});
+      prev = e;
+    }
+    std::pair<Loc, int> inc{};
+    int inc_rank = -1;
+    for (size_t k = chain.size(); k-- > 0;) {
+      const Node &nd = chain[k];
+      const Loc *o = (k == 0 && nd.e == target) ? out : nullptr;
+      if (inc_rank < 0) {
+        inc = red_tree(lr, nd.a * N, nd.e, nd.nl, o);
+      } else {
+        std::vector<Loc> ins;
+        std::vector<int> producers;
+        int lvl = level_of(inc_rank, nd.e);
+        if (lr == L) {
+          ins.push_back(send_loc(nd.e));
+        } else {
+          const long long sub = G[lr + 1];
+          for (int q = 0; q < h[lr]; ++q) {
+            const long long qb = nd.a * N + q * sub;
+            std::vector<int> ql = inside(nd.nl, qb, qb + sub);
+            if (ql.empty()) continue;
+            const int rep = (nd.e >= qb && nd.e < qb + sub) ? nd.e : pick_rep(qb, sub, nd.e, ql);
+            auto r = red_tree(lr + 1, qb, rep, ql, nullptr);
+            ins.push_back(r.first);
+            producers.push_back(r.second);
+            const int lv = level_of(rep, nd.e);
+            if (lv >= 0 && lv < lvl) lvl = lv;
+          }
+        }
+        ins.push_back(inc.first);
+        producers.push_back(inc.second);
+        const Loc dst = o ? *o : scratch_loc(nd.e);
+        inc = {dst, emit(OP_REDUCE, ins, {dst}, lvl, producers)};
+      }
+      inc_rank = nd.e;
+    }
+    if (inc_rank == target) return inc;
+    const Loc dst = out ? *out : scratch_loc(target);
+    return {dst, emit(OP_COPY, {inc.first}, {dst}, level_of(inc_rank, target), {inc.second})};
+  }
+
   std::vector<unsigned long long> bounds(size_t count, int parts) const {
     unsigned long long q = quantum_of(c.dtype);
     std::vector<unsigned long long> b(parts + 1);
@@ -301,7 +386,7 @@ struct Builder {
         Loc src = send_loc(pr.root);
         if (k == pr.root) {
           if (self_copy) emit(OP_COPY, {src}, {recv_loc(pr.root)}, -1, {});
-          mcast_tree(0, 0, k, src, -1, others);
+          mcast_ring(k, src, -1, others);
         } else {
           bool k_leaf = std::binary_search(pr.leaves.begin(), pr.leaves.end(), k);
           Loc dst = k_leaf ? recv_loc(k) : scratch_loc(k);
@@ -310,7 +395,7 @@ struct Builder {
           for (int j : others)
             if (j != k) branch.push_back(j);
           if (self_copy) branch.insert(std::lower_bound(branch.begin(), branch.end(), pr.root), pr.root);
-          mcast_tree(0, 0, k, dst, s0, branch);
+          mcast_ring(k, dst, s0, branch);
         }
       }
     }
@@ -328,9 +413,9 @@ struct Builder {
         int k = ks[b];
         Loc fin = recv_loc(pr.root);
         if (k == pr.root) {
-          red_tree(0, 0, k, pr.leaves, &fin);
+          red_ring(k, pr.leaves, &fin);
         } else {
-          auto r = red_tree(0, 0, k, pr.leaves, nullptr);
+          auto r = red_ring(k, pr.leaves, nullptr);
           emit(OP_COPY, {r.first}, {fin}, level_of(k, pr.root), {r.second});
         }
       }
@@ -447,10 +532,26 @@ static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevel
                                           ") != nranks (" + std::to_string(c->P) + ")");
   if (stripe < 1 || stripe > c->P) return fail(c, HICCL_ERR_INVALID, "stripe must be in [1, nranks]");
   if (pipeline < 1 || pipeline > 65536) return fail(c, HICCL_ERR_INVALID, "pipeline must be in [1, 65536]");
+  // ring(n): its nodes must be the groups of one level (Sec. 4.4)
+  int ring_lvl = -1;
+  {
+    long long g = c->P;
+    for (int l = 0; l <= nlevels; ++l) {
+      if (g * c->ring == c->P) { ring_lvl = l; break; }
+      if (l < nlevels) g /= h[l];
+    }
+  }
+  if (ring_lvl < 0)
+    return fail(c, HICCL_ERR_INVALID, "ring(" + std::to_string(c->ring) +
+                                          ") is not a product of the top hierarchy factors");
+  if (c->ring > 1 && stripe > c->P / c->ring)
+    return fail(c, HICCL_ERR_INVALID, "with a ring the stripe may not exceed the node size");
   std::string msg;
   if (find_race(*c, msg)) return fail(c, HICCL_ERR_RACE, "race: " + msg);
 
   Builder B(*c, h, stripe, pipeline);
+  B.ring = c->ring;
+  B.lr = ring_lvl;
   std::vector<uint32_t> epoch_first(c->epochs + 1, 0);
   int e_seen = 0;
   for (size_t i = 0; i < c->prims.size(); ++i) {
@@ -1150,6 +1251,11 @@ hiccl_status_t hiccl_set_option(hiccl_comm_t c, hiccl_option_t opt, long long va
       if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "set before planning");
       if (value < (long long)SEG_BYTES || value > (1ll << 30)) return fail(c, HICCL_ERR_INVALID, "item bytes out of range");
       c->item_bytes = (unsigned long long)value;
+      return HICCL_OK;
+    case HICCL_OPT_RING:
+      if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "set before planning");
+      if (value < 1 || value > c->P) return fail(c, HICCL_ERR_INVALID, "ring must be in [1, nranks]");
+      c->ring = (int)value;
       return HICCL_OK;
     case HICCL_OPT_ORDER:
       if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "set before planning");

@@ -1234,6 +1234,8 @@ hiccl_status_t hiccl_autotune(hiccl_comm_t c, void *stream, int flags, hiccl_tun
     if (!h.empty() && h.back() > 1 && h.back() <= c->P) ss.push_back(h.back());
     std::sort(ss.begin(), ss.end());
     ss.erase(std::unique(ss.begin(), ss.end()), ss.end());
+    if (c->ring > 1)   // a ring keeps the stripe inside one node
+      ss.erase(std::remove_if(ss.begin(), ss.end(), [&](int v) { return v > c->P / c->ring; }), ss.end());
     for (int sv : ss)
       for (int mv : {1, 2, 4, 8}) {
         hiccl_tune_t k = cur;

@@ -40,7 +40,8 @@ STATIC_ARENA_BYTES = 16 << 20
 COLLECTIVES = {"broadcast": 0, "reduce": 1, "allgather": 2, "reducescatter": 3, "allreduce": 4,
                "scatter": 5, "gather": 6, "alltoall": 7, "allreduce_single": 8}
 
-OPT_TIMEOUT_NS, OPT_CTAS_PER_SM, OPT_ITEM_BYTES, OPT_ORDER, OPT_THREADS, OPT_TRACE, OPT_SLOT_ITEMS = range(7)
+(OPT_TIMEOUT_NS, OPT_CTAS_PER_SM, OPT_ITEM_BYTES, OPT_ORDER, OPT_THREADS, OPT_TRACE, OPT_SLOT_ITEMS,
+ OPT_RING) = range(8)
 
 
 class HicclError(RuntimeError):

@@ -130,3 +130,22 @@ def test_reduction_operators(op, dtype, name, P, h, s, m, d, mis):
     element path (buffers one element off 16-byte alignment)."""
     _parity(PR.BUILDERS[name](P, d, dtype=dtype, op=op), h, s, m, seed=P + s + m, zero_frac=0.25,
             misalign_elems=mis)
+
+
+RING_GPU = [(12, [4, 3], 4, 3, 6, 1500), (12, [2, 2, 3], 4, 3, 8, 2053), (16, [4, 4], 16, 1, 4, 999),
+            (64, [4, 4, 4], 4, 4, 8, 4096)]
+
+
+@pytest.mark.parametrize("name", ["allreduce", "reducescatter", "reduce", "broadcast", "allgather", "alltoall"])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("P,h,ring,s,m,d", RING_GPU)
+def test_ring(name, dtype, P, h, ring, s, m, d):
+    """Hybrid ring+tree (Sec. 4.4): the executor reproduces the ring-order
+    semantics bit for bit, up to the 64-rank three-level machine."""
+    from paper_2408_05962_gb300 import hiccl as H
+    prog = PR.BUILDERS[name](P, d, dtype=dtype)
+    mem0 = fill(prog, P + ring)
+    ref = {k: v.copy() for k, v in mem0.items()}
+    S.run_program(prog, ref, h, ring)
+    outs, _ = run_on_gpu(prog, h, s, m, mem0, options={H.OPT_RING: ring})
+    assert_bit_equal(ref, outs[0])

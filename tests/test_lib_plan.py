@@ -23,11 +23,14 @@ def built():
     B.build()
 
 
-def _check(prog, h, s, m, seed=0, interpret_steps=True, zero_frac=0.0):
+def _check(prog, h, s, m, seed=0, interpret_steps=True, zero_frac=0.0, ring=1):
     fake = FakeAddresses(prog)
     comm = register(prog, fake.addr)
+    if ring != 1:
+        from paper_2408_05962_gb300 import hiccl as H
+        comm.set_option(H.OPT_RING, ring)
     comm.plan(h, s, m)
-    plan = factorize(prog, h, s, m)
+    plan = factorize(prog, h, s, m, ring)
     assert comm.level_bytes() == plan.level_bytes()
     assert comm.hbm_bytes() == plan.hbm_bytes()
     info = comm.plan_info()
@@ -36,10 +39,10 @@ def _check(prog, h, s, m, seed=0, interpret_steps=True, zero_frac=0.0):
     if interpret_steps:
         mem0 = fill(prog, seed, zero_frac)
         ref = {k: v.copy() for k, v in mem0.items()}
-        S.run_program(prog, ref, h)
+        S.run_program(prog, ref, h, ring)
         got = interpret(comm, fake, {k: v.copy() for k, v in mem0.items()}, prog.dtype)
         for k in ref:
-            assert np.array_equal(ref[k], got[k]), k
+            assert np.array_equal(ref[k].view(np.uint8), got[k].view(np.uint8)), k
     return comm
 
 
@@ -195,3 +198,52 @@ def test_native_composition_operator(name, op):
     got = interpret(comm, fake, {k: v.copy() for k, v in mem0.items()}, prog.dtype)
     for k in ref:
         assert np.array_equal(ref[k], got[k]), k
+
+
+RING_CASES = [(12, [4, 3], 4, 3, 2), (12, [2, 2, 3], 4, 3, 3), (12, [2, 2, 3], 2, 1, 2), (8, [2, 2, 2], 8, 1, 2),
+              (16, [4, 4], 4, 4, 4), (12, [3, 2, 2], 6, 2, 1)]
+
+
+@pytest.mark.parametrize("name", COLL)
+@pytest.mark.parametrize("P,h,ring,s,m", RING_CASES)
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_ring_collectives(name, P, h, ring, s, m, dtype):
+    """ring(n) (Sec. 4.4): the library's plan has the oracle's level bytes,
+    HBM bytes and stage count, and its step table reproduces the ring-order
+    semantics bit for bit."""
+    _check(PR.BUILDERS[name](P, 19, dtype=dtype), h, s, m, seed=P + ring + s, ring=ring)
+
+
+@pytest.mark.parametrize("P", [4, 6, 8, 12])
+def test_ring_random_programs(P):
+    from oracle.hierarchy import group_sizes
+    n = 0
+    for h in all_factorizations(P, max_levels=3):
+        for l in range(1, len(h) + 1):
+            ring = int(np.prod(h[:l]))
+            node = P // ring
+            for s in sorted({1, node}):
+                prog = random_program(P, P * 31 + l + s, ("f32", "i32")[l % 2])
+                if S.find_race(prog) is not None:
+                    continue
+                _check(prog, h, s, 2, seed=l, ring=ring)
+                n += 1
+    assert n > 0 and group_sizes
+
+
+def test_ring_validation():
+    from paper_2408_05962_gb300 import hiccl as H
+    prog = PR.broadcast(12, 4)
+    fake = FakeAddresses(prog)
+    for ring, s, ok in ((3, 1, False), (4, 4, False), (4, 3, True), (12, 1, True), (1, 12, True)):
+        comm = register(prog, fake.addr)
+        comm.set_option(H.OPT_RING, ring)
+        if ok:
+            comm.plan([4, 3], s, 1)
+        else:
+            with pytest.raises(H.HicclError) as e:
+                comm.plan([4, 3], s, 1)
+            assert e.value.status == H.ERR_INVALID
+    comm = register(prog, fake.addr)
+    with pytest.raises(H.HicclError):
+        comm.set_option(H.OPT_RING, 13)
