@@ -65,6 +65,38 @@ struct DevRun {
   unsigned long long bytes;
 };
 
+// ---- work-item records ----------------------------------------------------
+// Everything the control warp stages for one work item lies in one contiguous,
+// 16-byte aligned record, brought into shared memory by bulk copies in a
+// single round trip: the entries (step, meta word, pointer offset, dependency
+// count), the prefix sums of the runs' segment counts, the runs, and the
+// operand pointers of the entries' steps.  A pointer offset with PTR_GLOBAL
+// set indexes the global pointer array instead (steps with many operands, or
+// an item whose inline pointer area is full).
+constexpr uint32_t PTR_CAP = 384;              // inline pointers per item
+constexpr uint32_t PTR_STEP_MAX = 64;          // a step with more operands keeps them global
+constexpr uint32_t PTR_GLOBAL = 0x80000000u;
+struct RecEnt {
+  uint32_t step;
+  uint32_t meta;
+  uint32_t poff;    // inline pointer index, or PTR_GLOBAL | global pointer index
+  uint32_t indeg;   // dependency count of the step
+};
+struct DevItem {
+  uint32_t rec;     // record offset in 16-byte units
+  uint32_t nent;
+  uint32_t nrun;
+  uint32_t nptr;    // inline pointers
+};
+static_assert(sizeof(RecEnt) == 16 && sizeof(DevItem) == 16 && sizeof(DevRun) == 24, "record layout");
+HICCL_HD inline uint32_t rec_ent_bytes(uint32_t nent) { return nent * 16u; }
+HICCL_HD inline uint32_t rec_rpre_bytes(uint32_t nrun) { return ((nrun + 1u) * 4u + 15u) & ~15u; }
+HICCL_HD inline uint32_t rec_run_bytes(uint32_t nrun) { return (nrun * 24u + 15u) & ~15u; }
+HICCL_HD inline uint32_t rec_ptr_bytes(uint32_t nptr) { return (nptr * 8u + 15u) & ~15u; }
+HICCL_HD inline uint32_t rec_bytes(const DevItem &it) {
+  return rec_ent_bytes(it.nent) + rec_rpre_bytes(it.nrun) + rec_run_bytes(it.nrun) + rec_ptr_bytes(it.nptr);
+}
+
 // per-launch control block (device memory, zeroed at upload)
 struct DevCtl {
   unsigned long long ticket;   // next work item to claim
@@ -74,18 +106,12 @@ struct DevCtl {
 };
 
 struct DevTable {
-  const unsigned long long *nbytes;   // [nsteps]
-  const uint32_t *meta;               // [nsteps]
-  const uint32_t *ptr_off;            // [nsteps] first of nsrc source then ndst destination pointers
-  const uint32_t *indeg;              // [nsteps] dependency count
+  const unsigned char *recs;          // work-item records (16-byte aligned)
+  const DevItem *items;               // [nitems] record descriptors, in ticket order
   const uint32_t *nent;               // [nsteps] entries covering the step (completion target)
   const uint32_t *succ_off;           // [nsteps + 1]
   const uint32_t *succ;               // [nedges]
-  const unsigned long long *ptrs;     // [nptrs] device addresses
-  const DevEntry *entries;            // [nentries]
-  const uint32_t *item_off;           // [nitems + 1] entry ranges of the work items
-  const DevRun *runs;                 // [nruns] data ranges of the work items
-  const uint32_t *run_off;            // [nitems + 1] run ranges of the work items
+  const unsigned long long *ptrs;     // [nptrs] device addresses (nsrc sources then ndst destinations per step)
   unsigned long long *dep;            // [nsteps] arrivals of predecessors (cumulative over launches)
   unsigned long long *done;           // [nsteps] finished entries (cumulative over launches)
   DevCtl *ctl;
@@ -158,6 +184,16 @@ struct Plan {
   unsigned long long stages = 0, slots = 0;
   bool valid = false;
 };
+
+// Host image of the executor's read-only arrays for a plan whose relay
+// offsets resolve against relay_base (hiccl_plan.cpp, build_image).
+struct TableImage {
+  std::vector<unsigned long long> ptrs;   // every location, resolved
+  std::vector<uint32_t> indeg;            // per step
+  std::vector<unsigned char> recs;        // work-item records
+  std::vector<DevItem> items;             // per work item
+};
+void build_image(const Plan &p, unsigned long long relay_base, TableImage &im);
 
 }  // namespace hiccl
 

@@ -517,6 +517,66 @@ bool find_race(const hiccl_comm &c, std::string &msg) {
 
 }  // namespace
 
+// Work-item records (the executor's staging unit): per item its entries
+// with their steps' meta words and dependency counts, the runs and the
+// prefix sums of their segment counts, and the entries' operand pointers
+// inline while they fit.  Meta words carry the 16-byte alignment of every
+// resolved operand.
+void build_image(const Plan &p, unsigned long long relay_base, TableImage &im) {
+  const size_t N = p.steps.size();
+  im.ptrs.resize(p.locs.size());
+  for (size_t k = 0; k < p.locs.size(); ++k)
+    im.ptrs[k] = p.locs[k].scratch ? relay_base + p.locs[k].addr : p.locs[k].addr;
+  std::vector<uint32_t> meta(N);
+  im.indeg.resize(N);
+  for (size_t i = 0; i < N; ++i) {
+    const HStep &st = p.steps[i];
+    im.indeg[i] = p.pred_off[i + 1] - p.pred_off[i];
+    bool al = true;
+    for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k) al = al && (im.ptrs[st.loc0 + k] % 16 == 0);
+    meta[i] = meta_pack(st.kind, st.dtype, al ? 1u : 0u, st.nsrc, st.ndst, st.rop);
+  }
+  const size_t NI = p.item_off.empty() ? 0 : p.item_off.size() - 1;
+  im.items.assign(NI, DevItem{});
+  im.recs.clear();
+  std::vector<RecEnt> ents;
+  std::vector<unsigned long long> iptr;
+  std::vector<uint32_t> rpre;
+  for (size_t i = 0; i < NI; ++i) {
+    const uint32_t e0 = p.item_off[i], e1 = p.item_off[i + 1];
+    const uint32_t r0 = p.run_off[i], r1 = p.run_off[i + 1];
+    ents.clear();
+    iptr.clear();
+    for (uint32_t e = e0; e < e1; ++e) {
+      const uint32_t s = p.entries[e].step;
+      const HStep &st = p.steps[s];
+      const uint32_t np = st.nsrc + st.ndst;
+      RecEnt re{s, meta[s], PTR_GLOBAL | st.loc0, im.indeg[s]};
+      if (np <= PTR_STEP_MAX && iptr.size() + np <= PTR_CAP) {
+        re.poff = (uint32_t)iptr.size();
+        iptr.insert(iptr.end(), im.ptrs.begin() + st.loc0, im.ptrs.begin() + st.loc0 + np);
+      }
+      ents.push_back(re);
+    }
+    rpre.assign(1, 0u);
+    for (uint32_t r = r0; r < r1; ++r)
+      rpre.push_back(rpre.back() + (uint32_t)((p.runs[r].bytes + p.seg - 1) / p.seg));
+    DevItem it{(uint32_t)(im.recs.size() / 16), e1 - e0, r1 - r0, (uint32_t)iptr.size()};
+    const size_t at = im.recs.size();
+    im.recs.resize(at + rec_bytes(it), 0);
+    unsigned char *q = im.recs.data() + at;
+    std::memcpy(q, ents.data(), ents.size() * sizeof(RecEnt));
+    q += rec_ent_bytes(it.nent);
+    std::memcpy(q, rpre.data(), rpre.size() * 4);
+    q += rec_rpre_bytes(it.nrun);
+    if (r1 > r0) std::memcpy(q, &p.runs[r0], (r1 - r0) * sizeof(DevRun));
+    q += rec_run_bytes(it.nrun);
+    if (!iptr.empty()) std::memcpy(q, iptr.data(), iptr.size() * 8);
+    im.items[i] = it;
+  }
+}
+
+
 static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevels, int stripe,
                                  int pipeline) {
   if (!hierarchy || nlevels < 1 || nlevels > 64) return fail(c, HICCL_ERR_INVALID, "bad hierarchy");
@@ -1177,9 +1237,10 @@ hiccl_status_t hiccl_plan_info(hiccl_comm_t c, hiccl_plan_info_t *out) {
   out->runs = p.runs.size();
   out->scratch_bytes = p.scratch_bytes;
   unsigned long long N = p.steps.size();
-  out->table_bytes = N * (8 + 4 * 5 + 16) + 4 + p.succ.size() * 4 + p.locs.size() * 8 +
-                     p.entries.size() * sizeof(DevEntry) + p.item_off.size() * 8 +
-                     p.runs.size() * sizeof(DevRun) + sizeof(DevCtl);
+  TableImage im;
+  build_image(p, 0, im);
+  out->table_bytes = im.recs.size() + im.items.size() * sizeof(DevItem) + N * (4 + 4 + 16) + 4 +
+                     p.succ.size() * 4 + im.ptrs.size() * 8 + sizeof(DevCtl);
   return HICCL_OK;
 }
 

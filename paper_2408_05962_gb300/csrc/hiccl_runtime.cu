@@ -44,8 +44,9 @@ struct DevState {
   unsigned long long *host_err_dev = nullptr;
   cudaEvent_t done_ev = nullptr;
   DevTable t{};
-  std::vector<uint32_t> indeg;      // host copy, for fault injection
-  uint32_t *indeg_dev = nullptr;
+  std::vector<uint32_t> indeg;      // host copies, for fault injection
+  std::vector<DevItem> items;
+  char *recs_dev = nullptr;
   unsigned long long *trace = nullptr;   // [nitems][5] when tracing
   int err_slot = -1;
   cudaStream_t upload = nullptr;         // internal stream of the device (not owned)
@@ -80,6 +81,9 @@ __device__ __forceinline__ unsigned long long atom_relaxed_add(unsigned long lon
   unsigned long long old;
   asm volatile("atom.relaxed.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
   return old;
+}
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -366,24 +370,31 @@ __device__ __forceinline__ void warp_reduce(const unsigned long long *ptrs, uint
   }
 }
 
-constexpr int PMAX = 6;   // pointers of a step staged in shared memory (more: read from global)
 constexpr int NBUF = 3;   // work items staged ahead of the data warps
 
 // one staged work item: its entries, their steps' descriptors and pointers
-struct ItemBuf {
-  DevEntry ent[MAX_ENTRIES_PER_ITEM];
-  uint32_t pre[MAX_ENTRIES_PER_ITEM + 1];   // prefix sums of the entries' segment counts
-  uint32_t meta[MAX_ENTRIES_PER_ITEM];
-  uint32_t poff[MAX_ENTRIES_PER_ITEM];
-  unsigned long long nb[MAX_ENTRIES_PER_ITEM];
-  unsigned long long ptr[MAX_ENTRIES_PER_ITEM][PMAX];
-  uint32_t nent;
-  uint32_t end;                             // no more items: leave the loop
-  unsigned long long item;                  // ticket of the staged item
+// A staged work item: the sections of its record at fixed offsets (each
+// filled by one bulk copy), then the control fields.
+struct __align__(16) ItemBuf {
+  RecEnt ent[MAX_ENTRIES_PER_ITEM];
+  uint32_t rpre[MAX_ENTRIES_PER_ITEM + 4];  // prefix sums of the runs' segment counts
   DevRun run[MAX_ENTRIES_PER_ITEM];         // data ranges (runs of contiguous entries)
-  uint32_t rpre[MAX_ENTRIES_PER_ITEM + 1];  // prefix sums of the runs' segment counts
+  unsigned long long ptr[PTR_CAP];          // inline operand pointers
+  uint32_t nent;
   uint32_t nrun;
+  uint32_t end;                             // no more items: leave the loop
+  uint32_t pad;
+  unsigned long long item;                  // ticket of the staged item
 };
+static_assert(offsetof(ItemBuf, rpre) % 16 == 0 && offsetof(ItemBuf, run) % 16 == 0 &&
+                  offsetof(ItemBuf, ptr) % 16 == 0 && sizeof(ItemBuf) % 16 == 0,
+              "bulk-copy destinations must be 16-byte aligned");
+
+// operand pointers of entry k of a staged item
+__device__ __forceinline__ const unsigned long long *ent_ptrs(const ItemBuf &X, uint32_t k, const DevTable &T) {
+  const uint32_t po = X.ent[k].poff;
+  return (po & PTR_GLOBAL) ? T.ptrs + (po & ~PTR_GLOBAL) : X.ptr + po;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -482,7 +493,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
   constexpr int NS = ExecShape<NT>::NS;   // staging slots per data warp
   static_assert(D >= 1, "need at least one data warp");
   __shared__ ItemBuf buf[NBUF];
-  __shared__ __align__(8) unsigned long long full_bar[NBUF], done_bar[NBUF], empty_bar[NBUF];
+  __shared__ __align__(8) unsigned long long full_bar[NBUF], done_bar[NBUF], empty_bar[NBUF], rec_bar[NBUF];
   __shared__ __align__(8) unsigned long long ld_bar[D][NS];
   __shared__ __align__(8) unsigned long long red_bar[D];
   extern __shared__ __align__(128) unsigned char stage[];   // D x NS x SEG_BYTES
@@ -495,6 +506,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
       mbar_init(&full_bar[b], 32);
       mbar_init(&done_bar[b], D * 32);
       mbar_init(&empty_bar[b], 32);
+      mbar_init(&rec_bar[b], 1);
     }
     for (int w = 0; w < D; ++w) {
       for (int k = 0; k < NS; ++k) mbar_init(&ld_bar[w][k], 1);
@@ -505,6 +517,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
 
   if (warp == 0) {
     // ---- control: claim, stage, wait for predecessors ----
+    // The ticket of the next item is claimed, and its record descriptor read
+    // and its record prefetched into L2, while the current item's record is
+    // in flight and its predecessors are awaited.
+    unsigned long long nxt = 0;
+    DevItem nd{0, 0, 0, 0};
+    if (lane == 0) nxt = atomicAdd(&T.ctl->ticket, 1ull);
+    nxt = __shfl_sync(0xffffffffu, nxt, 0);
+    if (nxt < T.nitems) nd = T.items[nxt];
     for (uint32_t r = 0;; ++r) {
       const int b = r % NBUF;
       const uint32_t ph = (r / NBUF) & 1u;
@@ -514,100 +534,54 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         if (lane == 0) raise_error(T, (unsigned long long)ERR_STALL << 32);
         stop = true;
       }
-      unsigned long long item = 0;
       const unsigned long long t_claim = T.trace ? global_ns() : 0ull;
+      const unsigned long long item = nxt;
+      const DevItem it = nd;
+      if (!stop) stop = item >= T.nitems || ld_relaxed(&T.ctl->err) != 0ull;
       if (!stop) {
-        if (lane == 0) item = atomicAdd(&T.ctl->ticket, 1ull);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        stop = item >= T.nitems || ld_relaxed(&T.ctl->err) != 0ull;
+        if (lane == 0) {
+          const unsigned char *src = T.recs + (size_t)it.rec * 16;
+          const uint32_t be = rec_ent_bytes(it.nent), br = rec_rpre_bytes(it.nrun), bu = rec_run_bytes(it.nrun),
+                         bp = rec_ptr_bytes(it.nptr);
+          mbar_expect_tx(&rec_bar[b], be + br + bu + bp);
+          bulk_g2s(B.ent, src, be, &rec_bar[b]);
+          bulk_g2s(B.rpre, src + be, br, &rec_bar[b]);
+          if (bu) bulk_g2s(B.run, src + be + br, bu, &rec_bar[b]);
+          if (bp) bulk_g2s(B.ptr, src + be + br + bu, bp, &rec_bar[b]);
+          B.nent = it.nent;
+          B.nrun = it.nrun;
+          nxt = atomicAdd(&T.ctl->ticket, 1ull);
+        }
+        nxt = __shfl_sync(0xffffffffu, nxt, 0);
+        if (nxt < T.nitems) {
+          nd = T.items[nxt];
+          const unsigned char *q = T.recs + (size_t)nd.rec * 16;
+          const uint32_t nb = rec_bytes(nd);
+          for (uint32_t o = (uint32_t)lane * 128u; o < nb; o += 32u * 128u) prefetch_l2(q + o);
+        }
+        if (!mbar_wait(&rec_bar[b], ph, limit)) {
+          if (lane == 0) raise_error(T, (unsigned long long)ERR_STALL << 32);
+          stop = true;
+        }
       }
       if (!stop) {
-        const uint32_t e0 = ldg_ro(T.item_off + item), e1 = ldg_ro(T.item_off + item + 1);
-        const uint32_t ne = e1 - e0;
-        uint32_t cnt[2] = {0, 0}, sv[2] = {0, 0};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t x = lane + 32 * h;
-          if (x < ne) {
-            const DevEntry e = T.entries[e0 + x];
-            const uint32_t s = e.step;
-            sv[h] = s;
-            const uint32_t meta = ldg_ro(T.meta + s), po = ldg_ro(T.ptr_off + s);
-            B.ent[x] = e;
-            B.meta[x] = meta;
-            B.poff[x] = po;
-            B.nb[x] = ldg_ro(T.nbytes + s);
-            const uint32_t np = meta_nsrc(meta) + meta_ndst(meta);
-            if (np <= PMAX)
-              for (uint32_t q = 0; q < np; ++q) B.ptr[x][q] = ldg_ro(T.ptrs + po + q);
-            cnt[h] = e.seg_hi - e.seg_lo;
-          }
-        }
-        // inclusive warp scans of the segment counts of entries 0..31 and 32..63
-        uint32_t inc0 = cnt[0], inc1 = cnt[1];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t v0 = __shfl_up_sync(0xffffffffu, inc0, o);
-          const uint32_t v1 = __shfl_up_sync(0xffffffffu, inc1, o);
-          if (lane >= o) {
-            inc0 += v0;
-            inc1 += v1;
-          }
-        }
-        const uint32_t half = __shfl_sync(0xffffffffu, inc0, 31);
-        if (lane < (int)ne) B.pre[lane + 1] = inc0;
-        if (lane + 32 < (int)ne) B.pre[lane + 33] = half + inc1;
-        if (lane == 0) {
-          B.pre[0] = 0;
-          B.nent = ne;
-        }
-        {   // the item's runs and the prefix sums of their segment counts
-          const uint32_t r0 = ldg_ro(T.run_off + item), nr = ldg_ro(T.run_off + item + 1) - r0;
-          uint32_t rc[2] = {0, 0};
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const uint32_t x = lane + 32 * h;
-            if (x < nr) {
-              const DevRun rn = T.runs[r0 + x];
-              B.run[x] = rn;
-              rc[h] = (uint32_t)((rn.bytes + T.seg - 1) / T.seg);
-            }
-          }
-          uint32_t i0 = rc[0], i1 = rc[1];
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v0 = __shfl_up_sync(0xffffffffu, i0, o);
-            const uint32_t v1 = __shfl_up_sync(0xffffffffu, i1, o);
-            if (lane >= o) {
-              i0 += v0;
-              i1 += v1;
-            }
-          }
-          const uint32_t hf = __shfl_sync(0xffffffffu, i0, 31);
-          if (lane < (int)nr) B.rpre[lane + 1] = i0;
-          if (lane + 32 < (int)nr) B.rpre[lane + 33] = hf + i1;
-          if (lane == 0) {
-            B.rpre[0] = 0;
-            B.nrun = nr;
-          }
-        }
         bool bad = false;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const uint32_t x = lane + 32 * h;
-          if (x < ne && !bad) {
-            const uint32_t s = sv[h];
-            const unsigned long long target = (unsigned long long)ldg_ro(T.indeg + s) * epoch;
-            if (target && ld_acquire(T.dep + s) < target) {
+          if (x < it.nent && !bad) {
+            const RecEnt e = B.ent[x];
+            const unsigned long long target = (unsigned long long)e.indeg * epoch;
+            if (target && ld_acquire(T.dep + e.step) < target) {
               const unsigned long long t0 = global_ns();
               unsigned ns = 32;
-              while (ld_acquire(T.dep + s) < target) {
+              while (ld_acquire(T.dep + e.step) < target) {
                 if (ld_relaxed(&T.ctl->err)) {
                   bad = true;
                   break;
                 }
                 if (global_ns() - t0 > T.timeout_ns) {
-                  raise_error(T, ((unsigned long long)ERR_TIMEOUT << 32) | s);
+                  raise_error(T, ((unsigned long long)ERR_TIMEOUT << 32) | e.step);
                   bad = true;
                   break;
                 }
@@ -645,7 +619,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         break;
       }
       if (B.end) break;
-      if (!mbar_wait(&done_bar[b], ph, limit)) {
+      if (!mbar_wait(&rec_bar[b], ph, limit) || !mbar_wait(&done_bar[b], ph, limit)) {
         if (lane == 0) raise_error(T, (unsigned long long)ERR_STALL << 32);
         break;
       }
@@ -678,9 +652,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
     uint32_t seq = 0;        // bulk loads issued by this warp (slot = seq % NS, phase = seq / NS)
     uint32_t pre_issued = 0; // loads of the current item issued early (during the previous item)
     uint32_t rseq = 0;       // completed phases of this warp's reduce barrier
-    auto is_tma = [](const ItemBuf &X) { return meta_op(X.meta[0]) == OP_COPY && meta_aligned(X.meta[0]) != 0; };
+    auto is_tma = [](const ItemBuf &X) { return meta_op(X.ent[0].meta) == OP_COPY && meta_aligned(X.ent[0].meta) != 0; };
     auto is_tma_reduce = [](const ItemBuf &X) {
-      return meta_op(X.meta[0]) == OP_REDUCE && meta_aligned(X.meta[0]) != 0 && meta_nsrc(X.meta[0]) <= TMA_MAX_FANIN;
+      const uint32_t m = X.ent[0].meta;
+      return meta_op(m) == OP_REDUCE && meta_aligned(m) != 0 && meta_nsrc(m) <= TMA_MAX_FANIN;
     };
     auto mine = [&](const ItemBuf &X) {
       const uint32_t total = X.rpre[X.nrun];
@@ -688,8 +663,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
     };
     auto issue = [&](const ItemBuf &X, uint32_t i, uint32_t at) {   // segment i of X into load number `at`
       const SegRef g = seg_of(X, dw + i * D, T.seg);
-      const uint32_t np = meta_nsrc(X.meta[g.k]) + meta_ndst(X.meta[g.k]);
-      const unsigned long long *ptrs = np <= PMAX ? X.ptr[g.k] : T.ptrs + X.poff[g.k];
+      const unsigned long long *ptrs = ent_ptrs(X, g.k, T);
       const uint32_t slot = at % NS;
       const uint32_t n16 = g.n & ~15u;
       mbar_expect_tx(&ld_bar[dw][slot], n16);
@@ -705,6 +679,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         break;
       }
       if (B.end) break;
+      if (!mbar_wait(&rec_bar[b], ph, limit)) {   // the record's bulk copies are visible to this warp
+        if (lane == 0) raise_error(T, (unsigned long long)ERR_STALL << 32);
+        break;
+      }
       if (is_tma(B)) {
         const uint32_t nm = mine(B);
         bool stalled = false;
@@ -721,9 +699,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
                 break;
               }
               const SegRef g = seg_of(B, dw + i * D, T.seg);
-              const uint32_t meta = B.meta[g.k];
-              const uint32_t np = meta_nsrc(meta) + meta_ndst(meta);
-              const unsigned long long *ptrs = np <= PMAX ? B.ptr[g.k] : T.ptrs + B.poff[g.k];
+              const uint32_t meta = B.ent[g.k].meta;
+              const unsigned long long *ptrs = ent_ptrs(B, g.k, T);
               const uint32_t n16 = g.n & ~15u;
               if (n16) {
                 for (uint32_t q = 0; q < meta_ndst(meta); ++q)
@@ -744,7 +721,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
             bulk_wait_read_all();
             const int b2 = (r + 1) % NBUF;
             const ItemBuf &B2 = buf[b2];
-            if (mbar_try_wait(&full_bar[b2], ((r + 1) / NBUF) & 1u) && !B2.end && is_tma(B2)) {
+            if (mbar_try_wait(&full_bar[b2], ((r + 1) / NBUF) & 1u) && !B2.end &&
+                mbar_try_wait(&rec_bar[b2], ((r + 1) / NBUF) & 1u) && is_tma(B2)) {
               const uint32_t nm2 = mine(B2);
               const uint32_t pro2 = nm2 < (uint32_t)NS ? nm2 : (uint32_t)NS;
               fence_proxy_async_global();
@@ -762,9 +740,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
           const SegRef g = seg_of(B, dw + i * D, T.seg);
           const uint32_t n16 = g.n & ~15u;
           if (n16 == g.n) continue;
-          const uint32_t meta = B.meta[g.k];
-          const uint32_t np = meta_nsrc(meta) + meta_ndst(meta);
-          const unsigned long long *ptrs = np <= PMAX ? B.ptr[g.k] : T.ptrs + B.poff[g.k];
+          const uint32_t meta = B.ent[g.k].meta;
+          const unsigned long long *ptrs = ent_ptrs(B, g.k, T);
           if (lane < (int)(g.n - n16)) {
             const char v = __ldcg(reinterpret_cast<const char *>(ptrs[0]) + g.lo + n16 + lane);
             for (uint32_t q = 0; q < meta_ndst(meta); ++q)
@@ -782,9 +759,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         const uint32_t nm = mine(B);
         for (uint32_t i = 0; i < nm && !stalled; ++i) {
           const SegRef g = seg_of(B, dw + i * D, T.seg);
-          const uint32_t meta = B.meta[g.k];
+          const uint32_t meta = B.ent[g.k].meta;
           const uint32_t f = meta_nsrc(meta);
-          const unsigned long long *ptrs = (f + 1) <= PMAX ? B.ptr[g.k] : T.ptrs + B.poff[g.k];
+          const unsigned long long *ptrs = ent_ptrs(B, g.k, T);
           const uint32_t n16 = g.n & ~15u;
           const uint32_t dt = meta_dtype(meta);
           const uint32_t chunk = dt == HICCL_FP8E4M3 ? (AREA / f) / FP8_BLOCK_BYTES * FP8_BLOCK_BYTES
@@ -855,9 +832,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         const uint32_t rtotal = B.rpre[B.nrun];
         for (uint32_t j = dw; j < rtotal; j += D) {
           const SegRef g = seg_of(B, j, T.seg);
-          const uint32_t meta = B.meta[g.k];
-          const uint32_t np = meta_nsrc(meta) + meta_ndst(meta);
-          const unsigned long long *ptrs = np <= PMAX ? B.ptr[g.k] : T.ptrs + B.poff[g.k];
+          const uint32_t meta = B.ent[g.k].meta;
+          const unsigned long long *ptrs = ent_ptrs(B, g.k, T);
           if (meta_op(meta) == OP_COPY)
             warp_copy(ptrs, meta_ndst(meta), g.lo, g.n, meta_aligned(meta), lane);
           else
@@ -1026,49 +1002,28 @@ hiccl_status_t dev_upload(hiccl_comm *c) {
     scratch_base = (unsigned long long)(uintptr_t)d->scratch;
   }
 
-  // host images of the device arrays
-  std::vector<unsigned long long> nbytes(N), ptrs(p.locs.size());
-  std::vector<uint32_t> meta(N), ptr_off(N), indeg(N);
-  for (size_t k = 0; k < p.locs.size(); ++k)
-    ptrs[k] = p.locs[k].scratch ? scratch_base + p.locs[k].addr : p.locs[k].addr;
-  for (size_t i = 0; i < N; ++i) {
-    const HStep &st = p.steps[i];
-    nbytes[i] = st.nbytes;
-    ptr_off[i] = st.loc0;
-    indeg[i] = p.pred_off[i + 1] - p.pred_off[i];
-    bool al = true;
-    for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k) al = al && (ptrs[st.loc0 + k] % 16 == 0);
-    meta[i] = meta_pack(st.kind, st.dtype, al ? 1u : 0u, st.nsrc, st.ndst, st.rop);
-  }
-
-  // one allocation for all read-only arrays
+  // host image of the read-only arrays, in one allocation
+  TableImage im;
+  build_image(p, scratch_base, im);
   size_t off = 0;
   auto place = [&](size_t bytes) {
     size_t o = off;
     off = (off + bytes + 255) & ~size_t(255);
     return o;
   };
-  const size_t o_nbytes = place(N * 8), o_meta = place(N * 4), o_ptroff = place(N * 4), o_indeg = place(N * 4),
+  const size_t o_recs = place(im.recs.size()), o_items = place(im.items.size() * sizeof(DevItem)),
                o_nent = place(N * 4), o_succoff = place((N + 1) * 4), o_succ = place(p.succ.size() * 4),
-               o_ptrs = place(ptrs.size() * 8), o_ent = place(p.entries.size() * sizeof(DevEntry)),
-               o_item = place(p.item_off.size() * 4), o_runs = place(p.runs.size() * sizeof(DevRun)),
-               o_runoff = place(p.run_off.size() * 4);
+               o_ptrs = place(im.ptrs.size() * 8);
   std::vector<char> img(std::max<size_t>(off, 256), 0);
   auto put = [&](size_t o, const void *src, size_t bytes) {
     if (bytes) std::memcpy(img.data() + o, src, bytes);
   };
-  put(o_nbytes, nbytes.data(), N * 8);
-  put(o_meta, meta.data(), N * 4);
-  put(o_ptroff, ptr_off.data(), N * 4);
-  put(o_indeg, indeg.data(), N * 4);
+  put(o_recs, im.recs.data(), im.recs.size());
+  put(o_items, im.items.data(), im.items.size() * sizeof(DevItem));
   put(o_nent, p.nent.data(), N * 4);
   put(o_succoff, p.succ_off.data(), (N + 1) * 4);
   put(o_succ, p.succ.data(), p.succ.size() * 4);
-  put(o_ptrs, ptrs.data(), ptrs.size() * 8);
-  put(o_ent, p.entries.data(), p.entries.size() * sizeof(DevEntry));
-  put(o_item, p.item_off.data(), p.item_off.size() * 4);
-  put(o_runs, p.runs.data(), p.runs.size() * sizeof(DevRun));
-  put(o_runoff, p.run_off.data(), p.run_off.size() * 4);
+  put(o_ptrs, im.ptrs.data(), im.ptrs.size() * 8);
   {
     hiccl_status_t st = dalloc(&d->table, img.size(), "step table");
     if (st != HICCL_OK) return st;
@@ -1091,18 +1046,12 @@ hiccl_status_t dev_upload(hiccl_comm *c) {
   char *tb = static_cast<char *>(d->table);
   char *cb = static_cast<char *>(d->counters);
   DevTable &t = d->t;
-  t.nbytes = reinterpret_cast<const unsigned long long *>(tb + o_nbytes);
-  t.meta = reinterpret_cast<const uint32_t *>(tb + o_meta);
-  t.ptr_off = reinterpret_cast<const uint32_t *>(tb + o_ptroff);
-  t.indeg = reinterpret_cast<const uint32_t *>(tb + o_indeg);
+  t.recs = reinterpret_cast<const unsigned char *>(tb + o_recs);
+  t.items = reinterpret_cast<const DevItem *>(tb + o_items);
   t.nent = reinterpret_cast<const uint32_t *>(tb + o_nent);
   t.succ_off = reinterpret_cast<const uint32_t *>(tb + o_succoff);
   t.succ = reinterpret_cast<const uint32_t *>(tb + o_succ);
   t.ptrs = reinterpret_cast<const unsigned long long *>(tb + o_ptrs);
-  t.entries = reinterpret_cast<const DevEntry *>(tb + o_ent);
-  t.item_off = reinterpret_cast<const uint32_t *>(tb + o_item);
-  t.runs = reinterpret_cast<const DevRun *>(tb + o_runs);
-  t.run_off = reinterpret_cast<const uint32_t *>(tb + o_runoff);
   t.dep = reinterpret_cast<unsigned long long *>(cb);
   t.done = reinterpret_cast<unsigned long long *>(cb + N * 8);
   t.ctl = reinterpret_cast<DevCtl *>(cb + N * 16);
@@ -1118,8 +1067,9 @@ hiccl_status_t dev_upload(hiccl_comm *c) {
   }
   // the uploads must have landed before the first start (on any stream)
   if ((e = cudaStreamSynchronize(us)) != cudaSuccess) return cuda_fail(c, e, "upload");
-  d->indeg = std::move(indeg);
-  d->indeg_dev = reinterpret_cast<uint32_t *>(tb + o_indeg);
+  d->indeg = std::move(im.indeg);
+  d->items = std::move(im.items);
+  d->recs_dev = tb + o_recs;
   return HICCL_OK;
 }
 
@@ -1286,8 +1236,17 @@ hiccl_status_t hiccl_debug_withhold(hiccl_comm_t c, unsigned long long index, in
   if (c->state != hiccl_comm::READY || !c->dev) return fail(c, HICCL_ERR_STATE, "needs an idle initialized communicator");
   DevState *d = c->dev;
   if (index >= d->indeg.size() || extra < 0 || extra > 1000) return fail(c, HICCL_ERR_INVALID, "bad step or count");
-  uint32_t v = d->indeg[index] + (uint32_t)extra;
-  cudaError_t e = cudaMemcpyAsync(d->indeg_dev + index, &v, sizeof(v), cudaMemcpyHostToDevice, d->upload);
+  // the dependency count is stored in every record entry of the step
+  uint32_t v[1] = {d->indeg[index] + (uint32_t)extra};
+  const Plan &p = c->plan;
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < d->items.size() && e == cudaSuccess; ++i)
+    for (uint32_t k = p.item_off[i]; k < p.item_off[i + 1] && e == cudaSuccess; ++k)
+      if (p.entries[k].step == index) {
+        char *at = d->recs_dev + (size_t)d->items[i].rec * 16 + (size_t)(k - p.item_off[i]) * sizeof(RecEnt) +
+                   offsetof(RecEnt, indeg);
+        e = cudaMemcpyAsync(at, v, sizeof(uint32_t), cudaMemcpyHostToDevice, d->upload);
+      }
   if (e == cudaSuccess) e = cudaStreamSynchronize(d->upload);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync");
   return HICCL_OK;
@@ -1315,32 +1274,6 @@ static __device__ __align__(256) unsigned char g_static_arena[HICCL_STATIC_ARENA
 constexpr int MAX_STATIC_DEVICES = 64;
 static void *g_static_addr[MAX_STATIC_DEVICES];   // device address of the arena, per device
 
-// Expands the raw plan (steps, locations, predecessor offsets) copied into the
-// arena into the executor's table arrays; relay offsets become arena addresses.
-__global__ void hiccl_static_expand(const HStep *steps, const Loc *locs, const uint32_t *pred_off,
-                                    unsigned long long nsteps, unsigned long long nlocs, uint32_t dtype,
-                                    unsigned long long relay_base, unsigned long long *nbytes,
-                                    uint32_t *meta, uint32_t *ptr_off, uint32_t *indeg,
-                                    unsigned long long *ptrs) {
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  const unsigned long long t0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  for (unsigned long long k = t0; k < nlocs; k += stride)
-    ptrs[k] = locs[k].scratch ? relay_base + locs[k].addr : locs[k].addr;
-  for (unsigned long long i = t0; i < nsteps; i += stride) {
-    const HStep st = steps[i];
-    bool al = true;
-    for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k) {
-      const Loc l = locs[st.loc0 + k];
-      const unsigned long long a = l.scratch ? relay_base + l.addr : l.addr;
-      al = al && (a % 16 == 0);
-    }
-    nbytes[i] = st.nbytes;
-    ptr_off[i] = st.loc0;
-    indeg[i] = pred_off[i + 1] - pred_off[i];
-    meta[i] = meta_pack(st.kind, st.dtype, al ? 1u : 0u, st.nsrc, st.ndst, st.rop);
-  }
-}
-
 }  // namespace hiccl
 
 extern "C" hiccl_status_t hiccl_run_static(hiccl_comm_t c, void *stream) {
@@ -1348,22 +1281,8 @@ extern "C" hiccl_status_t hiccl_run_static(hiccl_comm_t c, void *stream) {
   if (!c->plan.valid) return HICCL_ERR_STATE;
   const Plan &p = c->plan;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const unsigned long long N = p.steps.size(), NL = p.locs.size(), NE = p.entries.size();
+  const unsigned long long N = p.steps.size();
   const unsigned long long NI = p.item_off.size() ? p.item_off.size() - 1 : 0, NS = p.succ.size();
-  unsigned long long off = 0;
-  auto place = [&](unsigned long long bytes) {
-    const unsigned long long o = off;
-    off = (off + bytes + 255) & ~255ull;
-    return o;
-  };
-  const unsigned long long o_steps = place(N * sizeof(HStep)), o_locs = place(NL * sizeof(Loc)),
-                           o_predoff = place((N + 1) * 4), o_nbytes = place(N * 8), o_meta = place(N * 4),
-                           o_ptroff = place(N * 4), o_indeg = place(N * 4), o_nent = place(N * 4),
-                           o_succoff = place((N + 1) * 4), o_succ = place(NS * 4), o_ptrs = place(NL * 8),
-                           o_ent = place(NE * sizeof(DevEntry)), o_item = place((NI + 1) * 4),
-                           o_runs = place(p.runs.size() * sizeof(DevRun)), o_runoff = place((NI + 1) * 4),
-                           o_ctr = place(N * 16 + sizeof(DevCtl) + 8), o_relay = place(p.scratch_bytes);
-  if (off > HICCL_STATIC_ARENA_BYTES) return HICCL_ERR_TOO_LARGE;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return HICCL_ERR_CUDA;
@@ -1377,47 +1296,45 @@ extern "C" hiccl_status_t hiccl_run_static(hiccl_comm_t c, void *stream) {
     g_static_addr[dev] = addr;
   }
   char *base = static_cast<char *>(g_static_addr[dev]);
+
+  // arena layout: relay buffers first (their addresses go into the records),
+  // then the read-only arrays, then the counters
+  unsigned long long off = 0;
+  auto place = [&](unsigned long long bytes) {
+    const unsigned long long o = off;
+    off = (off + bytes + 255) & ~255ull;
+    return o;
+  };
+  const unsigned long long o_relay = place(p.scratch_bytes);
+  TableImage im;
+  build_image(p, (unsigned long long)(uintptr_t)(base + o_relay), im);
+  const unsigned long long o_recs = place(im.recs.size()), o_items = place(im.items.size() * sizeof(DevItem)),
+                           o_nent = place(N * 4), o_succoff = place((N + 1) * 4), o_succ = place(NS * 4),
+                           o_ptrs = place(im.ptrs.size() * 8), o_ctr = place(N * 16 + sizeof(DevCtl) + 8);
+  if (off > HICCL_STATIC_ARENA_BYTES) return HICCL_ERR_TOO_LARGE;
   if (N == 0) return HICCL_OK;
 
   auto h2d = [&](unsigned long long o, const void *src, unsigned long long bytes) {
     return bytes ? cudaMemcpyAsync(base + o, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
   };
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = h2d(o_steps, p.steps.data(), N * sizeof(HStep));
-  if (e == cudaSuccess) e = h2d(o_locs, p.locs.data(), NL * sizeof(Loc));
-  if (e == cudaSuccess) e = h2d(o_predoff, p.pred_off.data(), (N + 1) * 4);
+  if (e == cudaSuccess) e = h2d(o_recs, im.recs.data(), im.recs.size());
+  if (e == cudaSuccess) e = h2d(o_items, im.items.data(), im.items.size() * sizeof(DevItem));
   if (e == cudaSuccess) e = h2d(o_nent, p.nent.data(), N * 4);
   if (e == cudaSuccess) e = h2d(o_succoff, p.succ_off.data(), (N + 1) * 4);
   if (e == cudaSuccess) e = h2d(o_succ, p.succ.data(), NS * 4);
-  if (e == cudaSuccess) e = h2d(o_ent, p.entries.data(), NE * sizeof(DevEntry));
-  if (e == cudaSuccess) e = h2d(o_item, p.item_off.data(), (NI + 1) * 4);
-  if (e == cudaSuccess) e = h2d(o_runs, p.runs.data(), p.runs.size() * sizeof(DevRun));
-  if (e == cudaSuccess) e = h2d(o_runoff, p.run_off.data(), (NI + 1) * 4);
+  if (e == cudaSuccess) e = h2d(o_ptrs, im.ptrs.data(), im.ptrs.size() * 8);
   // every call starts from zeroed counters: the arena keeps the last call's contents
   if (e == cudaSuccess) e = cudaMemsetAsync(base + o_ctr, 0, N * 16 + sizeof(DevCtl) + 8, s);
   if (e != cudaSuccess) return HICCL_ERR_CUDA;
 
-  hiccl_static_expand<<<(unsigned)std::min<unsigned long long>((N + NL + 255) / 256, 1024), 256, 0, s>>>(
-      reinterpret_cast<const HStep *>(base + o_steps), reinterpret_cast<const Loc *>(base + o_locs),
-      reinterpret_cast<const uint32_t *>(base + o_predoff), N, NL, (uint32_t)c->dtype,
-      (unsigned long long)(uintptr_t)(base + o_relay), reinterpret_cast<unsigned long long *>(base + o_nbytes),
-      reinterpret_cast<uint32_t *>(base + o_meta), reinterpret_cast<uint32_t *>(base + o_ptroff),
-      reinterpret_cast<uint32_t *>(base + o_indeg), reinterpret_cast<unsigned long long *>(base + o_ptrs));
-  if (cudaGetLastError() != cudaSuccess) return HICCL_ERR_CUDA;
-
   DevTable t{};
-  t.nbytes = reinterpret_cast<const unsigned long long *>(base + o_nbytes);
-  t.meta = reinterpret_cast<const uint32_t *>(base + o_meta);
-  t.ptr_off = reinterpret_cast<const uint32_t *>(base + o_ptroff);
-  t.indeg = reinterpret_cast<const uint32_t *>(base + o_indeg);
+  t.recs = reinterpret_cast<const unsigned char *>(base + o_recs);
+  t.items = reinterpret_cast<const DevItem *>(base + o_items);
   t.nent = reinterpret_cast<const uint32_t *>(base + o_nent);
   t.succ_off = reinterpret_cast<const uint32_t *>(base + o_succoff);
   t.succ = reinterpret_cast<const uint32_t *>(base + o_succ);
   t.ptrs = reinterpret_cast<const unsigned long long *>(base + o_ptrs);
-  t.entries = reinterpret_cast<const DevEntry *>(base + o_ent);
-  t.item_off = reinterpret_cast<const uint32_t *>(base + o_item);
-  t.runs = reinterpret_cast<const DevRun *>(base + o_runs);
-  t.run_off = reinterpret_cast<const uint32_t *>(base + o_runoff);
   t.dep = reinterpret_cast<unsigned long long *>(base + o_ctr);
   t.done = reinterpret_cast<unsigned long long *>(base + o_ctr + N * 8);
   t.ctl = reinterpret_cast<DevCtl *>(base + o_ctr + N * 16);
