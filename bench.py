@@ -360,6 +360,10 @@ def run_ours(args):
     step_bytes = sum(nbytes.values())
 
     def one_step(evs=None):
+        """All collectives back to back on one stream.  With ``evs`` (one
+        event per collective plus one) each launch is bracketed; without,
+        consecutive launches overlap their launch latency (programmatic
+        dependent launch)."""
         for i, kind in enumerate(kinds):
             if evs is not None:
                 evs[i].record(stream)
@@ -373,26 +377,31 @@ def run_ours(args):
         one_step()
     torch.cuda.synchronize(device)
 
+    # per-collective breakdown (untimed pass, events between the launches)
+    per_kind = {kind: [] for kind in kinds}
+    for _ in range(min(args.steps, 10)):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(kinds) + 1)]
+        one_step(evs)
+        torch.cuda.synchronize(device)
+        for i, kind in enumerate(kinds):
+            per_kind[kind].append(evs[i].elapsed_time(evs[i + 1]))
+
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    all_evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(kinds) + 1)] for _ in range(args.steps)]
+    step_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier(device)
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
     for k in range(args.steps):
-        one_step(all_evs[k])
+        step_evs[k][0].record(stream)
+        one_step()
+        step_evs[k][1].record(stream)
     torch.cuda.synchronize(device)
     wall = time.perf_counter() - t0
     barrier(device)
     clk = clocks.stop()
-
-    per_kind = {kind: [] for kind in kinds}
-    step_ms = []
-    for evs in all_evs:
-        for i, kind in enumerate(kinds):
-            per_kind[kind].append(evs[i].elapsed_time(evs[i + 1]))
-        step_ms.append(evs[0].elapsed_time(evs[len(kinds)]))
+    step_ms = [a.elapsed_time(b) for a, b in step_evs]
     dev_s = sum(step_ms) / 1e3
     tot_bytes, tot_s = aggregate(step_bytes * args.steps, dev_s, device)
     gbs = tot_bytes / tot_s / 1e9

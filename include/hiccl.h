@@ -299,11 +299,12 @@ typedef enum {
 hiccl_status_t hiccl_set_option(hiccl_comm_t comm, hiccl_option_t opt, long long value);
 
 /* Executor trace of the last start (HICCL_OPT_TRACE set before hiccl_init).
- * For every work item, in ticket order, 5 values: the %globaltimer time (ns)
+ * For every work item, in ticket order, 6 values: the %globaltimer time (ns)
  * its staging began, the time its predecessors were satisfied and it was
  * handed to the data warps, the time its data movement ended, the time its
- * successors were released, and the SM that ran it.  `out` receives
- * min(capacity, 5 * items) values; *written gets that count.  Call after
+ * successors were released, the SM that ran it, and the index of its first
+ * step (hiccl_get_step).  `out` receives min(capacity, 6 * items) values;
+ * *written gets that count.  Call after
  * hiccl_wait.  HICCL_ERR_STATE if tracing was not enabled. */
 hiccl_status_t hiccl_get_trace(hiccl_comm_t comm, unsigned long long *out, size_t capacity, size_t *written);
 

@@ -119,7 +119,7 @@ struct DevTable {
   unsigned long long nitems;
   unsigned long long timeout_ns;
   unsigned long long seg;             // segment bytes of this plan
-  unsigned long long *trace;          // [nitems][4] timestamps, or null (see hiccl_get_trace)
+  unsigned long long *trace;          // [nitems][6] timestamps, SM, first step; or null (see hiccl_get_trace)
 };
 
 enum : uint32_t { ERR_TIMEOUT = 1, ERR_BADSTEP = 2, ERR_STALL = 3 };

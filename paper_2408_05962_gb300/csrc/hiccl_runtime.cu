@@ -47,7 +47,7 @@ struct DevState {
   std::vector<uint32_t> indeg;      // host copies, for fault injection
   std::vector<DevItem> items;
   char *recs_dev = nullptr;
-  unsigned long long *trace = nullptr;   // [nitems][5] when tracing
+  unsigned long long *trace = nullptr;   // [nitems][6] when tracing
   int err_slot = -1;
   cudaStream_t upload = nullptr;         // internal stream of the device (not owned)
 };
@@ -370,7 +370,13 @@ __device__ __forceinline__ void warp_reduce(const unsigned long long *ptrs, uint
   }
 }
 
-constexpr int NBUF = 3;   // work items staged ahead of the data warps
+#ifndef HICCL_NBUF
+#define HICCL_NBUF 3
+#endif
+#ifndef HICCL_PDL
+#define HICCL_PDL 1
+#endif
+constexpr int NBUF = HICCL_NBUF;   // work items staged ahead of the data warps
 
 // one staged work item: its entries, their steps' descriptors and pointers
 // A staged work item: the sections of its record at fixed offsets (each
@@ -499,7 +505,6 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
   extern __shared__ __align__(128) unsigned char stage[];   // D x NS x SEG_BYTES
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned long long epoch = ld_relaxed(&T.ctl->epoch) + 1;   // this launch
   const unsigned long long limit = 2 * T.timeout_ns + 1000000ull;    // bound of the in-CTA waits
   if (tid == 0) {
     for (int b = 0; b < NBUF; ++b) {
@@ -514,6 +519,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
     }
   }
   __syncthreads();
+  // the previous kernel of the stream has completed and its writes are visible
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const unsigned long long epoch = ld_relaxed(&T.ctl->epoch) + 1;   // this launch
 
   if (warp == 0) {
     // ---- control: claim, stage, wait for predecessors ----
@@ -537,7 +545,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
       const unsigned long long t_claim = T.trace ? global_ns() : 0ull;
       const unsigned long long item = nxt;
       const DevItem it = nd;
-      if (!stop) stop = item >= T.nitems || ld_relaxed(&T.ctl->err) != 0ull;
+      if (!stop && item >= T.nitems) {
+        stop = true;
+        // no more items for this CTA: the next kernel of the stream may start
+        // its launch (it waits for this grid's completion before any access)
+        if (lane == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+      }
+      if (!stop) stop = ld_relaxed(&T.ctl->err) != 0ull;
       if (!stop) {
         if (lane == 0) {
           const unsigned char *src = T.recs + (size_t)it.rec * 16;
@@ -597,11 +611,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         B.end = stop ? 1u : 0u;
         if (!stop) B.item = item;
         if (T.trace && !stop) {
-          T.trace[item * 5 + 0] = t_claim;
-          T.trace[item * 5 + 1] = global_ns();
+          T.trace[item * 6 + 0] = t_claim;
+          T.trace[item * 6 + 1] = global_ns();
           unsigned smid;
           asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-          T.trace[item * 5 + 4] = smid;
+          T.trace[item * 6 + 4] = smid;
+          T.trace[item * 6 + 5] = B.ent[0].step;
         }
       }
       __syncwarp();
@@ -623,7 +638,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         if (lane == 0) raise_error(T, (unsigned long long)ERR_STALL << 32);
         break;
       }
-      if (T.trace && lane == 0) T.trace[B.item * 5 + 2] = global_ns();
+      if (T.trace && lane == 0) T.trace[B.item * 6 + 2] = global_ns();
       // fence-based release: one fence orders this item's data before the
       // counter updates; the last finisher of a step fences again (acquiring
       // the other finishers' data) before it releases the step's successors
@@ -638,7 +653,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         }
       }
       __syncwarp();
-      if (T.trace && lane == 0) T.trace[B.item * 5 + 3] = global_ns();
+      if (T.trace && lane == 0) T.trace[B.item * 6 + 3] = global_ns();
       mbar_arrive(&empty_bar[b]);
     }
   } else {
@@ -879,11 +894,28 @@ static cudaError_t exec_occupancy(int nt, int *occ) {
   }
 }
 
+// Launches allow programmatic dependent launch: the CTAs of this executor
+// may become resident while the previous kernel of the stream drains, and
+// wait (griddepcontrol.wait) for its completion before touching memory.
+template <int NT>
+static void exec_launch_t(unsigned grid, cudaStream_t s, const DevTable &t) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = ExecShape<NT>::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = HICCL_PDL;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, hiccl_exec_kernel<NT>, t);
+}
 static void exec_launch(int nt, unsigned grid, cudaStream_t s, const DevTable &t) {
   switch (nt) {
-    case 128: hiccl_exec_kernel<128><<<grid, 128, ExecShape<128>::SMEM, s>>>(t); break;
-    case 256: hiccl_exec_kernel<256><<<grid, 256, ExecShape<256>::SMEM, s>>>(t); break;
-    default: hiccl_exec_kernel<512><<<grid, 512, ExecShape<512>::SMEM, s>>>(t); break;
+    case 128: exec_launch_t<128>(grid, s, t); break;
+    case 256: exec_launch_t<256>(grid, s, t); break;
+    default: exec_launch_t<512>(grid, s, t); break;
   }
 }
 
@@ -1061,7 +1093,7 @@ hiccl_status_t dev_upload(hiccl_comm *c) {
   t.seg = p.seg;
   t.trace = nullptr;
   if (c->trace && t.nitems) {
-    hiccl_status_t st = dalloc((void **)&d->trace, t.nitems * 5 * sizeof(unsigned long long), "trace buffer");
+    hiccl_status_t st = dalloc((void **)&d->trace, t.nitems * 6 * sizeof(unsigned long long), "trace buffer");
     if (st != HICCL_OK) return st;
     t.trace = d->trace;
   }
@@ -1222,7 +1254,7 @@ hiccl_status_t hiccl_get_trace(hiccl_comm_t c, unsigned long long *out, size_t c
   if (c->state != hiccl_comm::READY || !c->dev) return fail(c, HICCL_ERR_STATE, "needs an idle initialized communicator");
   DevState *d = c->dev;
   if (!d->trace) return fail(c, HICCL_ERR_STATE, "tracing is off (HICCL_OPT_TRACE)");
-  const size_t n = std::min<size_t>(capacity, (size_t)d->t.nitems * 5);
+  const size_t n = std::min<size_t>(capacity, (size_t)d->t.nitems * 6);
   if (n && out) {
     cudaError_t e = cudaMemcpy(out, d->trace, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "trace copy");

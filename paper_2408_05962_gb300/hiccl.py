@@ -280,13 +280,14 @@ def hiccl_run_static(comm, stream=None):
 
 def hiccl_get_trace(comm, nitems: int):
     """Per-item executor timestamps of the last start: a list of
-    (staging began, handed to data warps, data done, successors released, SM)."""
-    cap = 5 * int(nitems)
+    (staging began, handed to data warps, data done, successors released, SM,
+    first step)."""
+    cap = 6 * int(nitems)
     buf = (ctypes.c_ulonglong * max(cap, 1))()
     n = ctypes.c_size_t()
     _check(comm, lib().hiccl_get_trace(comm, buf, cap, ctypes.byref(n)))
     v = [int(x) for x in buf[:n.value]]
-    return [tuple(v[i:i + 5]) for i in range(0, len(v), 5)]
+    return [tuple(v[i:i + 6]) for i in range(0, len(v), 6)]
 
 
 def hiccl_autotune(comm, stream=None, flags: int = 0) -> dict:
