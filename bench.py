@@ -314,7 +314,8 @@ def run_ours(args):
 
     W = WORKLOADS[args.workload]
     Pw, hier, stripe, pipe = W["ranks"], W["hierarchy"], W["stripe"], W["pipeline"]
-    d = W["bytes_per_rank"] // 4 // Pw            # values per chunk (64 MiB of fp32 values per rank)
+    bpr = args.bytes_per_rank or W["bytes_per_rank"]
+    d = bpr // 4 // Pw                            # values per chunk (bytes of fp32 values per rank / P)
     dtype = args.dtype
     if args.workload == "seven":
         if dtype != "f32":
@@ -449,7 +450,8 @@ def run_ours(args):
         "warmup": max(args.warmup, 3), "ms_per_step": statistics.mean(step_ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
         "data": "synthetic", "config": workload_config(
-            {"parallelism": f"replicas{world}", "payload": dtype, **({"ring": args.ring} if args.ring > 1 else {})},
+            {"parallelism": f"replicas{world}", "payload": dtype, **({"ring": args.ring} if args.ring > 1 else {}),
+             **({"bytes_per_rank": bpr} if args.bytes_per_rank else {})},
             args.workload),
         "roofline": {"bound": "hbm", "achieved": gbs / world, "peak": peak, "unit": "GB/s",
                      "frac": gbs / world / peak, "peak_source": peak_kind,
@@ -673,6 +675,8 @@ def main(argv=None):
     ap.add_argument("--threads", type=int, default=0, help="executor threads per CTA (0: library default)")
     ap.add_argument("--order", type=int, default=None, help="work order: 0 pipeline slots, 1 stage depth")
     ap.add_argument("--ring", type=int, default=1, help="ring(n) of the hybrid ring+tree topology (1: tree)")
+    ap.add_argument("--bytes-per-rank", type=int, default=0,
+                    help="override the workload's per-rank bytes (profiling of a smaller case; 0: the workload's)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
