@@ -170,13 +170,16 @@ __device__ __forceinline__ uint32_t f32x2_to_e4m3x2(float lo, float hi) {
 // fold of one 16-byte vector position over f inputs, ld(q) giving input q's
 // vector: f32 / i32 natively (add4), BF16 decoded to binary32, folded in
 // order and rounded once
-template <typename LD>
-__device__ __forceinline__ uint4 fold16(LD ld, uint32_t f, uint32_t dt, uint32_t rop = 0) {
-  uint4 v = ld(0);
-  if (dt != HICCL_BF16) {
-    for (uint32_t q = 1; q < f; ++q) v = add4(v, ld(q), dt, rop);
-    return v;
-  }
+struct CombSum {
+  __device__ __forceinline__ float operator()(float a, float b) const { return __fadd_rn(a, b); }
+};
+struct CombAny {
+  uint32_t rop;
+  __device__ __forceinline__ float operator()(float a, float b) const { return comb_f(a, b, rop); }
+};
+template <typename LD, typename COMB>
+__device__ __forceinline__ uint4 fold16_bf16(LD ld, uint32_t f, COMB comb) {
+  const uint4 v = ld(0);
   float a[8];
   const uint32_t w0[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -189,8 +192,8 @@ __device__ __forceinline__ uint4 fold16(LD ld, uint32_t f, uint32_t dt, uint32_t
     const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      a[2 * i] = comb_f(a[2 * i], __uint_as_float(w[i] << 16), rop);
-      a[2 * i + 1] = comb_f(a[2 * i + 1], __uint_as_float(w[i] & 0xffff0000u), rop);
+      a[2 * i] = comb(a[2 * i], __uint_as_float(w[i] << 16));
+      a[2 * i + 1] = comb(a[2 * i + 1], __uint_as_float(w[i] & 0xffff0000u));
     }
   }
   uint4 r;
@@ -199,6 +202,19 @@ __device__ __forceinline__ uint4 fold16(LD ld, uint32_t f, uint32_t dt, uint32_t
   r.z = f32_to_bf16_rn(a[4]) | (f32_to_bf16_rn(a[5]) << 16);
   r.w = f32_to_bf16_rn(a[6]) | (f32_to_bf16_rn(a[7]) << 16);
   return r;
+}
+template <typename LD>
+__device__ __forceinline__ uint4 fold16(LD ld, uint32_t f, uint32_t dt, uint32_t rop = 0) {
+  if (dt != HICCL_BF16) {
+    uint4 v = ld(0);
+    if (rop == HICCL_SUM && dt == HICCL_F32)
+      for (uint32_t q = 1; q < f; ++q) v = add4(v, ld(q), HICCL_F32, HICCL_SUM);
+    else
+      for (uint32_t q = 1; q < f; ++q) v = add4(v, ld(q), dt, rop);
+    return v;
+  }
+  if (rop == HICCL_SUM) return fold16_bf16(ld, f, CombSum{});
+  return fold16_bf16(ld, f, CombAny{rop});
 }
 
 // FP8 blocks (128 codes, binary32 scale at byte 128, zero bytes 132..143):
