@@ -159,6 +159,18 @@ __device__ __forceinline__ float2 e4m3x2_to_f32x2(uint32_t two) {
       : "r"(h2));
   return make_float2(lo, hi);
 }
+// four codes (byte k of w gives component k) -> four binary32 values, exactly
+__device__ __forceinline__ float4 e4m3x4_to_f32x4(uint32_t w) {
+  float4 r;
+  asm("{\n\t.reg .b16 lo, hi, a, b, c, d;\n\t.reg .b32 h0, h1;\n\t"
+      "mov.b32 {lo, hi}, %4;\n\t"
+      "cvt.rn.f16x2.e4m3x2 h0, lo;\n\tcvt.rn.f16x2.e4m3x2 h1, hi;\n\t"
+      "mov.b32 {a, b}, h0;\n\tmov.b32 {c, d}, h1;\n\t"
+      "cvt.f32.f16 %0, a;\n\tcvt.f32.f16 %1, b;\n\tcvt.f32.f16 %2, c;\n\tcvt.f32.f16 %3, d;\n\t}"
+      : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+      : "r"(w));
+  return r;
+}
 // two binary32 -> two e4m3 codes (round to nearest even, saturating at 448);
 // the first value lands in the low byte
 __device__ __forceinline__ uint32_t f32x2_to_e4m3x2(float lo, float hi) {
@@ -231,17 +243,32 @@ __device__ __forceinline__ void fp8_fold_block(BLK blk, char *out, uint32_t f, u
 #pragma unroll
   for (int i = 0; i < 16; ++i) acc[i] = 0.f;
   if (active) {
-    for (uint32_t q = 0; q < f; ++q) {
+    {
+      const char *b = blk(0);
+      const uint4 c = *reinterpret_cast<const uint4 *>(b + 16 * sub);
+      const float sc = *reinterpret_cast<const float *>(b + 128);
+      const uint32_t w[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float4 v = e4m3x4_to_f32x4(w[j]);
+        acc[4 * j + 0] = __fmul_rn(v.x, sc);
+        acc[4 * j + 1] = __fmul_rn(v.y, sc);
+        acc[4 * j + 2] = __fmul_rn(v.z, sc);
+        acc[4 * j + 3] = __fmul_rn(v.w, sc);
+      }
+    }
+    for (uint32_t q = 1; q < f; ++q) {
       const char *b = blk(q);
       const uint4 c = *reinterpret_cast<const uint4 *>(b + 16 * sub);
       const float sc = *reinterpret_cast<const float *>(b + 128);
       const uint32_t w[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
-      for (int i = 0; i < 16; i += 2) {
-        const float2 v = e4m3x2_to_f32x2((w[i >> 2] >> (8 * (i & 3))) & 0xffffu);
-        const float x0 = __fmul_rn(v.x, sc), x1 = __fmul_rn(v.y, sc);
-        acc[i] = q ? __fadd_rn(acc[i], x0) : x0;
-        acc[i + 1] = q ? __fadd_rn(acc[i + 1], x1) : x1;
+      for (int j = 0; j < 4; ++j) {
+        const float4 v = e4m3x4_to_f32x4(w[j]);
+        acc[4 * j + 0] = __fadd_rn(acc[4 * j + 0], __fmul_rn(v.x, sc));
+        acc[4 * j + 1] = __fadd_rn(acc[4 * j + 1], __fmul_rn(v.y, sc));
+        acc[4 * j + 2] = __fadd_rn(acc[4 * j + 2], __fmul_rn(v.z, sc));
+        acc[4 * j + 3] = __fadd_rn(acc[4 * j + 3], __fmul_rn(v.w, sc));
       }
     }
   }
