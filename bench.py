@@ -444,7 +444,13 @@ def run_ours(args):
         coll[kind] = {"ms": med, "gbs": nbytes[kind] / med / 1e6, "frac": nbytes[kind] / med / 1e6 / peak,
                       "dp_over_t_gbs": pbytes[kind] / med / 1e6, "schedule_bytes": nbytes[kind],
                       "level_bytes": comms[kind].level_bytes(), "steps": comms[kind].plan_info()["steps"]}
-    traffic = recorded_traffic()
+    # DRAM bytes of an average executor launch of the default workload, from
+    # the committed ncu capture (null for other workloads or options, or once
+    # the executor sources have changed since the capture)
+    default_run = (args.workload == "seven" and not args.kinds and args.ring == 1 and not args.bytes_per_rank
+                   and not args.item_bytes and not args.ctas_per_sm and not args.threads and args.order is None)
+    step_traffic = recorded_traffic() if default_run else None
+    traffic = step_traffic / len(kinds) if step_traffic else None
     line = {
         "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": statistics.mean(step_ms),
@@ -455,7 +461,8 @@ def run_ours(args):
             args.workload),
         "roofline": {"bound": "hbm", "achieved": gbs / world, "peak": peak, "unit": "GB/s",
                      "frac": gbs / world / peak, "peak_source": peak_kind,
-                     "traffic": traffic, "kernel": "hiccl_exec_kernel"},
+                     "traffic": traffic, "traffic_per_step": step_traffic,
+                     "schedule_bytes_per_launch": step_bytes / len(kinds), "kernel": "hiccl_exec_kernel"},
         "clocks": clk, "gpu_launches": len(kinds) * args.steps * world,
         "e2e": {"value": eb / es / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "collectives": coll, "wall_ms_per_step": wall / args.steps * 1e3,
