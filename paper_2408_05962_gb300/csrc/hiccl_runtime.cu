@@ -498,6 +498,19 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// one arrival on the dependency counter of every successor succ[a..z): the
+// successor indices are loaded four at a time before their updates are issued
+__device__ __forceinline__ void release_succ(const DevTable &T, uint32_t a, uint32_t z) {
+  for (uint32_t q = a; q < z; q += 4) {
+    uint32_t t[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) t[u] = q + u < z ? ldg_ro(T.succ + q + u) : 0xffffffffu;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (t[u] != 0xffffffffu) red_relaxed_add(T.dep + t[u], 1ull);
+  }
+}
+
 template <int NT>
 struct ExecShape {
   static constexpr int D = NT / 32 - 2;                 // data warps
@@ -686,15 +699,35 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
       // fence-based release: one fence orders this item's data before the
       // counter updates; the last finisher of a step fences again (acquiring
       // the other finishers' data) before it releases the step's successors
+      // Both halves of the item's (at most 64) entries are handled at once:
+      // the counter updates and the loads they need are all in flight together.
+      static_assert(MAX_ENTRIES_PER_ITEM <= 64, "two entries per lane");
       __threadfence();
-      for (uint32_t x = lane; x < B.nent; x += 32) {
-        const uint32_t s = B.ent[x].step;
-        const unsigned long long old = atom_relaxed_add(T.done + s, 1ull);
-        if (old + 1 == (unsigned long long)ldg_ro(T.nent + s) * epoch) {
-          __threadfence();
-          const uint32_t a = ldg_ro(T.succ_off + s), z = ldg_ro(T.succ_off + s + 1);
-          for (uint32_t q = a; q < z; ++q) red_relaxed_add(T.dep + ldg_ro(T.succ + q), 1ull);
+      {
+        const uint32_t n = B.nent;
+        const bool v0 = (uint32_t)lane < n, v1 = (uint32_t)lane + 32 < n;
+        const uint32_t s0 = v0 ? B.ent[lane].step : 0u, s1 = v1 ? B.ent[lane + 32].step : 0u;
+        uint32_t t0 = 0, t1 = 0, a0 = 0, z0 = 0, a1 = 0, z1 = 0;
+        unsigned long long o0 = 0, o1 = 0;
+        if (v0) {
+          t0 = ldg_ro(T.nent + s0);
+          a0 = ldg_ro(T.succ_off + s0);
+          z0 = ldg_ro(T.succ_off + s0 + 1);
+          o0 = atom_relaxed_add(T.done + s0, 1ull);
         }
+        if (v1) {
+          t1 = ldg_ro(T.nent + s1);
+          a1 = ldg_ro(T.succ_off + s1);
+          z1 = ldg_ro(T.succ_off + s1 + 1);
+          o1 = atom_relaxed_add(T.done + s1, 1ull);
+        }
+        const bool f0 = v0 && o0 + 1 == (unsigned long long)t0 * epoch;
+        const bool f1 = v1 && o1 + 1 == (unsigned long long)t1 * epoch;
+        // the last finisher of a step acquires the other finishers' data
+        // before it releases the step's successors
+        if (__any_sync(0xffffffffu, f0 || f1)) __threadfence();
+        if (f0) release_succ(T, a0, z0);
+        if (f1) release_succ(T, a1, z1);
       }
       __syncwarp();
       if (T.trace && lane == 0) T.trace[B.item * 6 + 3] = global_ns();
