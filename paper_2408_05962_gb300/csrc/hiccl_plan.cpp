@@ -98,21 +98,57 @@ struct Builder {
   };
   std::vector<Relay> relays;
 
+  // the sorted leaves [b, e) of a (sub)tree, without `skip` (its holder) if present
+  struct Span {
+    const int *b, *e;
+    int skip;
+    bool empty() const { return e == b || (e - b == 1 && *b == skip); }
+  };
+  // per-level work lists of the tree builders, reused across calls
+  struct Scratch {
+    std::vector<long long> qb;
+    std::vector<int> rep;
+    std::vector<const int *> lo, hi;
+    std::vector<Loc> locs;
+    std::vector<int> prods;
+    void clear() {
+      qb.clear();
+      rep.clear();
+      lo.clear();
+      hi.clear();
+      locs.clear();
+      prods.clear();
+    }
+  };
+  std::vector<Scratch> scr;
+  std::vector<int> grp;   // grp[l * P + r] = r / G[l + 1] (level-l subgroup of rank r)
+
   Builder(const hiccl_comm &comm, const std::vector<int> &hier, int stripe, int pipeline)
       : c(comm), h(hier), L((int)hier.size()), s(stripe), m(pipeline) {
     G.assign(L + 1, 1);
     for (int l = L - 1; l >= 0; --l) G[l] = G[l + 1] * h[l];
+    scr.resize(L + 1);
+    if ((long long)c.P * L <= (1ll << 24)) {
+      grp.resize((size_t)c.P * L);
+      for (int l = 0; l < L; ++l)
+        for (int r = 0; r < c.P; ++r) grp[(size_t)l * c.P + r] = (int)(r / G[l + 1]);
+    }
   }
 
   int level_of(int a, int b) const {
     if (a == b) return -1;
+    if (!grp.empty()) {
+      for (int l = 0; l < L; ++l)
+        if (grp[(size_t)l * c.P + a] != grp[(size_t)l * c.P + b]) return l;
+      return -1;
+    }
     for (int l = 0; l < L; ++l)
       if (a / G[l + 1] != b / G[l + 1]) return l;
     return -1;
   }
 
-  int emit(uint8_t kind, const std::vector<Loc> &srcs, const std::vector<Loc> &dsts, int level,
-           const std::vector<int> &preds) {
+  int emit(uint8_t kind, const Loc *srcs, uint32_t ns, const Loc *dsts, uint32_t nd, int level, const int *preds,
+           uint32_t np) {
     HStep st{};
     st.kind = kind;
     st.level = (int8_t)level;
@@ -125,15 +161,20 @@ struct Builder {
     st.dtype = (uint32_t)c.dtype;
     st.rop = p ? (uint32_t)p->op : 0u;
     st.loc0 = (uint32_t)locs.size();
-    st.nsrc = (uint32_t)srcs.size();
-    st.ndst = (uint32_t)dsts.size();
-    locs.insert(locs.end(), srcs.begin(), srcs.end());
-    locs.insert(locs.end(), dsts.begin(), dsts.end());
+    st.nsrc = ns;
+    st.ndst = nd;
+    locs.insert(locs.end(), srcs, srcs + ns);
+    locs.insert(locs.end(), dsts, dsts + nd);
     int idx = (int)steps.size();
     steps.push_back(st);
-    for (int q : preds)
-      if (q >= 0) edges.emplace_back((uint32_t)q, (uint32_t)idx);
+    for (uint32_t k = 0; k < np; ++k)
+      if (preds[k] >= 0) edges.emplace_back((uint32_t)preds[k], (uint32_t)idx);
     return idx;
+  }
+  int emit(uint8_t kind, const std::vector<Loc> &srcs, const std::vector<Loc> &dsts, int level,
+           const std::vector<int> &preds) {
+    return emit(kind, srcs.data(), (uint32_t)srcs.size(), dsts.data(), (uint32_t)dsts.size(), level, preds.data(),
+                (uint32_t)preds.size());
   }
 
   Loc scratch_loc(int rank) {   // addr holds the relay id until layout_relays()
@@ -178,15 +219,19 @@ struct Builder {
   Loc recv_loc(int r) const { return Loc{p->recv[r] + cur_off, r, 0}; }
   static bool same(const Loc &a, const Loc &b) { return a.addr == b.addr && a.scratch == b.scratch; }
 
-  // leaves of `sorted` inside [lo, hi)
-  static std::vector<int> inside(const std::vector<int> &sorted, long long lo, long long hi) {
-    auto a = std::lower_bound(sorted.begin(), sorted.end(), (int)lo);
-    auto b = std::lower_bound(sorted.begin(), sorted.end(), (int)hi);
-    return std::vector<int>(a, b);
+  // the leaves of span `sp` inside ranks [lo, hi)
+  static Span inside(const Span &sp, long long lo, long long hi) {
+    const int *a = std::lower_bound(sp.b, sp.e, (int)lo);
+    const int *b = std::lower_bound(a, sp.e, (int)hi);
+    return Span{a, b, sp.skip};
   }
-  static int pick_rep(long long qbase, long long sub, int holder, const std::vector<int> &ql) {
+  static Span span_of(const std::vector<int> &v) { return Span{v.data(), v.data() + v.size(), -1}; }
+  // the representative of subgroup [qbase, qbase + sub) for `holder`: the rank
+  // at the holder's offset if it is a leaf, else the lowest leaf
+  static int pick_rep(long long qbase, long long sub, int holder, const Span &ql) {
     int cand = (int)(qbase + holder % sub);
-    return std::binary_search(ql.begin(), ql.end(), cand) ? cand : ql.front();
+    if (cand != ql.skip && std::binary_search(ql.b, ql.e, cand)) return cand;
+    return *ql.b != ql.skip ? *ql.b : ql.b[1];
   }
 
   std::vector<int> stripe_ranks(int root, const std::vector<int> &leaves) const {
@@ -205,80 +250,80 @@ struct Builder {
   }
 
   // ---- multicast tree: deliver from `holder` to every rank of `leaves` ---------
-  void mcast_tree(int l, long long base, int holder, Loc src, int src_step,
-                  const std::vector<int> &leaves) {
+  // One hop per level from the holder to the representatives of its sibling
+  // subgroups (ascending), then the same inside every subgroup.
+  void mcast_tree(int l, long long base, int holder, Loc src, int src_step, Span leaves) {
     if (l == L || leaves.empty()) return;
-    long long sub = G[l + 1];
-    std::vector<int> own;
+    const long long sub = G[l + 1];
+    Scratch &S = scr[l];
+    S.clear();
+    Span own{nullptr, nullptr, leaves.skip};
     long long own_base = -1;
-    std::vector<std::pair<long long, std::vector<int>>> hops;   // (qbase, leaves) per rep
-    std::vector<int> reps;
-    for (int q = 0; q < h[l]; ++q) {
-      long long qb = base + q * sub;
-      std::vector<int> ql = inside(leaves, qb, qb + sub);
+    for (const int *i = leaves.b; i < leaves.e;) {
+      const long long qb = base + (*i - base) / sub * sub;
+      const Span q = inside(Span{i, leaves.e, leaves.skip}, qb, qb + sub);
       if (holder >= qb && holder < qb + sub) {
-        own = std::move(ql);
+        own = q;
         own_base = qb;
-      } else if (!ql.empty()) {
-        reps.push_back(pick_rep(qb, sub, holder, ql));
-        hops.emplace_back(qb, std::move(ql));
+      } else if (!q.empty()) {
+        S.qb.push_back(qb);
+        S.rep.push_back(pick_rep(qb, sub, holder, q));
+        S.lo.push_back(q.b);
+        S.hi.push_back(q.e);
+        S.locs.push_back(recv_loc(S.rep.back()));
       }
+      i = q.e;
     }
     int hop_step = -1;
-    if (!reps.empty()) {
-      std::vector<Loc> dsts;
-      for (int r : reps) dsts.push_back(recv_loc(r));
-      hop_step = emit(OP_COPY, {src}, dsts, l, {src_step});
-    }
+    if (!S.rep.empty()) hop_step = emit(OP_COPY, &src, 1, S.locs.data(), (uint32_t)S.locs.size(), l, &src_step, 1);
+    const size_t nh = S.rep.size();
     if (own_base >= 0) mcast_tree(l + 1, own_base, holder, src, src_step, own);
-    for (size_t k = 0; k < reps.size(); ++k) {
-      std::vector<int> rest;
-      for (int r : hops[k].second)
-        if (r != reps[k]) rest.push_back(r);
-      mcast_tree(l + 1, hops[k].first, reps[k], recv_loc(reps[k]), hop_step, rest);
+    for (size_t k = 0; k < nh; ++k) {
+      const Scratch &T = scr[l];   // the deeper calls use the deeper levels' lists
+      const int rep = T.rep[k];
+      mcast_tree(l + 1, T.qb[k], rep, recv_loc(rep), hop_step, Span{T.lo[k], T.hi[k], rep});
     }
   }
 
   // ---- reduction tree: fold `leaves` at `target`; returns (location, producer) ----
-  std::pair<Loc, int> red_tree(int l, long long base, int target, const std::vector<int> &leaves,
-                               const Loc *out) {
+  std::pair<Loc, int> red_tree(int l, long long base, int target, Span leaves, const Loc *out) {
     if (l == L) {
       Loc ref = send_loc(target);
       if (!out || same(*out, ref)) return {ref, -1};
-      int st = emit(OP_COPY, {ref}, {*out}, -1, {});
+      int st = emit(OP_COPY, &ref, 1, out, 1, -1, nullptr, 0);
       return {*out, st};
     }
-    long long sub = G[l + 1];
-    struct Part { long long qb; int rep; std::vector<int> ql; };
-    std::vector<Part> parts;
-    for (int q = 0; q < h[l]; ++q) {
-      long long qb = base + q * sub;
-      std::vector<int> ql = inside(leaves, qb, qb + sub);
-      if (ql.empty()) continue;
-      int rep = (target >= qb && target < qb + sub) ? target : pick_rep(qb, sub, target, ql);
-      parts.push_back(Part{qb, rep, std::move(ql)});
+    const long long sub = G[l + 1];
+    Scratch &S = scr[l];
+    S.clear();
+    for (const int *i = leaves.b; i < leaves.e;) {
+      const long long qb = base + (*i - base) / sub * sub;
+      const Span q = inside(Span{i, leaves.e, -1}, qb, qb + sub);
+      S.qb.push_back(qb);
+      S.rep.push_back((target >= qb && target < qb + sub) ? target : pick_rep(qb, sub, target, q));
+      S.lo.push_back(q.b);
+      S.hi.push_back(q.e);
+      i = q.e;
     }
-    if (parts.size() == 1 && parts[0].rep == target)
-      return red_tree(l + 1, parts[0].qb, target, parts[0].ql, out);
-    std::vector<Loc> ins;
-    std::vector<int> producers;
-    for (auto &pt : parts) {
-      auto r = red_tree(l + 1, pt.qb, pt.rep, pt.ql, nullptr);
-      ins.push_back(r.first);
-      producers.push_back(r.second);
+    if (S.rep.size() == 1 && S.rep[0] == target)
+      return red_tree(l + 1, S.qb[0], target, Span{S.lo[0], S.hi[0], -1}, out);
+    const size_t np = S.rep.size();
+    for (size_t k = 0; k < np; ++k) {
+      auto r = red_tree(l + 1, scr[l].qb[k], scr[l].rep[k], Span{scr[l].lo[k], scr[l].hi[k], -1}, nullptr);
+      scr[l].locs.push_back(r.first);
+      scr[l].prods.push_back(r.second);
     }
     Loc o = out ? *out : scratch_loc(target);
-    int st = emit(ins.size() > 1 ? OP_REDUCE : OP_COPY, ins, {o}, l, producers);
+    const Scratch &T = scr[l];
+    int st = emit(np > 1 ? OP_REDUCE : OP_COPY, T.locs.data(), (uint32_t)np, &o, 1, l, T.prods.data(), (uint32_t)np);
     return {o, st};
   }
 
   // ---- ring across the nodes of level lr (Sec. 4.4), tree inside them ----------
   // chain order: the holder's node first, then ascending node index, cyclically
-  std::vector<int> node_leaves(long long a, const std::vector<int> &leaves) const {
-    return inside(leaves, a * G[lr], (a + 1) * G[lr]);
-  }
+  Span node_leaves(long long a, const Span &leaves) const { return inside(leaves, a * G[lr], (a + 1) * G[lr]); }
 
-  void mcast_ring(int holder, Loc src, int src_step, const std::vector<int> &leaves) {
+  void mcast_ring(int holder, Loc src, int src_step, Span leaves) {
     if (ring == 1) {
       mcast_tree(0, 0, holder, src, src_step, leaves);
       return;
@@ -287,34 +332,32 @@ struct Builder {
     mcast_tree(lr, a0 * N, holder, src, src_step, node_leaves(a0, leaves));
     for (int i = 1; i < ring; ++i) {
       const long long a = (a0 + i) % ring;
-      std::vector<int> nl = node_leaves(a, leaves);
+      const Span nl = node_leaves(a, leaves);
       if (nl.empty()) continue;
       const int e = pick_rep(a * N, N, holder, nl);
-      const int hop = emit(OP_COPY, {src}, {recv_loc(e)}, level_of(holder, e), {src_step});
-      std::vector<int> rest;
-      for (int r : nl)
-        if (r != e) rest.push_back(r);
-      mcast_tree(lr, a * N, e, recv_loc(e), hop, rest);
+      const Loc d = recv_loc(e);
+      const int hop = emit(OP_COPY, &src, 1, &d, 1, level_of(holder, e), &src_step, 1);
+      mcast_tree(lr, a * N, e, d, hop, Span{nl.b, nl.e, e});
       holder = e;
-      src = recv_loc(e);
+      src = d;
       src_step = hop;
     }
   }
 
   // the fold along the chain: the last node's tree fold travels back, each
   // earlier entry rank folds its node's partials and then the incoming one
-  std::pair<Loc, int> red_ring(int target, const std::vector<int> &leaves, const Loc *out) {
+  std::pair<Loc, int> red_ring(int target, Span leaves, const Loc *out) {
     if (ring == 1) return red_tree(0, 0, target, leaves, out);
     const long long N = G[lr], a0 = target / N;
-    struct Node { long long a; std::vector<int> nl; int e; };
+    struct Node { long long a; Span nl; int e; };
     std::vector<Node> chain;
     int prev = target;
     for (int i = 0; i < ring; ++i) {
       const long long a = (a0 + i) % ring;
-      std::vector<int> nl = node_leaves(a, leaves);
+      const Span nl = node_leaves(a, leaves);
       if (nl.empty()) continue;
       const int e = a == a0 ? target : pick_rep(a * N, N, prev, nl);
-      chain.push_back(Node{a, std::move(nl), e});
+      chain.push_back(Node{a, nl, e});
       prev = e;
     }
     std::pair<Loc, int> inc{};
@@ -334,7 +377,7 @@ struct Builder {
           const long long sub = G[lr + 1];
           for (int q = 0; q < h[lr]; ++q) {
             const long long qb = nd.a * N + q * sub;
-            std::vector<int> ql = inside(nd.nl, qb, qb + sub);
+            const Span ql = inside(nd.nl, qb, qb + sub);
             if (ql.empty()) continue;
             const int rep = (nd.e >= qb && nd.e < qb + sub) ? nd.e : pick_rep(qb, sub, nd.e, ql);
             auto r = red_tree(lr + 1, qb, rep, ql, nullptr);
@@ -347,13 +390,14 @@ struct Builder {
         ins.push_back(inc.first);
         producers.push_back(inc.second);
         const Loc dst = o ? *o : scratch_loc(nd.e);
-        inc = {dst, emit(OP_REDUCE, ins, {dst}, lvl, producers)};
+        inc = {dst, emit(OP_REDUCE, ins.data(), (uint32_t)ins.size(), &dst, 1, lvl, producers.data(),
+                         (uint32_t)producers.size())};
       }
       inc_rank = nd.e;
     }
     if (inc_rank == target) return inc;
     const Loc dst = out ? *out : scratch_loc(target);
-    return {dst, emit(OP_COPY, {inc.first}, {dst}, level_of(inc_rank, target), {inc.second})};
+    return {dst, emit(OP_COPY, &inc.first, 1, &dst, 1, level_of(inc_rank, target), &inc.second, 1)};
   }
 
   std::vector<unsigned long long> bounds(size_t count, int parts) const {
@@ -377,25 +421,31 @@ struct Builder {
     std::vector<int> others;
     for (int j : pr.leaves)
       if (j != pr.root) others.push_back(j);
+    std::vector<int> branch;
     for (int b = 0; b < nb; ++b) {
+      const int k = ks[b];
+      if (k != pr.root) {   // the leaves of branch b: all but k (the root too, unless in place)
+        branch.clear();
+        for (int j : others)
+          if (j != k) branch.push_back(j);
+        if (self_copy) branch.insert(std::lower_bound(branch.begin(), branch.end(), pr.root), pr.root);
+      }
       for (int ch = 0; ch < m; ++ch) {
         unsigned long long lo = bd[b * m + ch], hi = bd[b * m + ch + 1];
         if (hi <= lo) continue;
         begin_piece(b, ch, lo * c.esize, (hi - lo) * c.esize);
-        int k = ks[b];
         Loc src = send_loc(pr.root);
         if (k == pr.root) {
-          if (self_copy) emit(OP_COPY, {src}, {recv_loc(pr.root)}, -1, {});
-          mcast_ring(k, src, -1, others);
+          if (self_copy) {
+            const Loc d = recv_loc(pr.root);
+            emit(OP_COPY, &src, 1, &d, 1, -1, nullptr, 0);
+          }
+          mcast_ring(k, src, -1, span_of(others));
         } else {
           bool k_leaf = std::binary_search(pr.leaves.begin(), pr.leaves.end(), k);
           Loc dst = k_leaf ? recv_loc(k) : scratch_loc(k);
-          int s0 = emit(OP_COPY, {src}, {dst}, level_of(pr.root, k), {});
-          std::vector<int> branch;
-          for (int j : others)
-            if (j != k) branch.push_back(j);
-          if (self_copy) branch.insert(std::lower_bound(branch.begin(), branch.end(), pr.root), pr.root);
-          mcast_ring(k, dst, s0, branch);
+          int s0 = emit(OP_COPY, &src, 1, &dst, 1, level_of(pr.root, k), nullptr, 0);
+          mcast_ring(k, dst, s0, span_of(branch));
         }
       }
     }
@@ -413,10 +463,10 @@ struct Builder {
         int k = ks[b];
         Loc fin = recv_loc(pr.root);
         if (k == pr.root) {
-          red_ring(k, pr.leaves, &fin);
+          red_ring(k, span_of(pr.leaves), &fin);
         } else {
-          auto r = red_ring(k, pr.leaves, nullptr);
-          emit(OP_COPY, {r.first}, {fin}, level_of(k, pr.root), {r.second});
+          auto r = red_ring(k, span_of(pr.leaves), nullptr);
+          emit(OP_COPY, &r.first, 1, &fin, 1, level_of(k, pr.root), &r.second, 1);
         }
       }
     }
@@ -429,20 +479,116 @@ struct Access {
   bool write;
 };
 
+struct Range {
+  unsigned long long lo, hi;
+  int prim;
+  bool write;
+  int rank = -1;   // owner of the buffer
+};
+
+// user-buffer ranges a primitive reads and writes (an exact in-place root
+// takes no part)
+void prim_ranges(const hiccl_comm &c, int i, std::vector<Range> &rs) {
+  const Prim &p = c.prims[i];
+  if (p.count == 0) return;
+  unsigned long long n = (unsigned long long)p.count * c.esize;
+  if (p.kind == 0) {
+    rs.push_back(Range{p.send[p.root], p.send[p.root] + n, i, false, p.root});
+    for (int j : p.leaves) {
+      if (j == p.root && p.recv[j] == p.send[p.root]) continue;
+      rs.push_back(Range{p.recv[j], p.recv[j] + n, i, true, j});
+    }
+  } else {
+    for (int j : p.leaves) {
+      if (j == p.root && p.send[j] == p.recv[p.root]) continue;   // exact in place
+      rs.push_back(Range{p.send[j], p.send[j] + n, i, false, j});
+    }
+    rs.push_back(Range{p.recv[p.root], p.recv[p.root] + n, i, true, p.root});
+  }
+}
+
+// sorted by lo, with prefix maxima of hi: every range overlapping [lo, hi)
+// is found by a binary search on hi and a backward scan
+struct RangeIndex {
+  std::vector<Range> r;
+  std::vector<unsigned long long> pmax;
+  void build() {
+    std::sort(r.begin(), r.end(), [](const Range &a, const Range &b) { return a.lo < b.lo; });
+    pmax.resize(r.size());
+    for (size_t k = 0; k < r.size(); ++k) pmax[k] = std::max(r[k].hi, k ? pmax[k - 1] : 0ull);
+  }
+  template <typename F>
+  void overlaps(unsigned long long lo, unsigned long long hi, F f) const {
+    size_t k = std::lower_bound(r.begin(), r.end(), hi, [](const Range &x, unsigned long long v) { return x.lo < v; }) -
+               r.begin();
+    while (k > 0) {
+      --k;
+      if (pmax[k] <= lo) break;
+      if (r[k].hi > lo && r[k].lo < hi) f(r[k]);
+    }
+  }
+};
+
 // fence dependencies (Sec. 3.3): edges from earlier-epoch steps to the steps
-// of epoch e whose user-buffer accesses conflict with theirs
+// of epoch e whose user-buffer accesses conflict with theirs.  Only the
+// "hot" byte ranges, where a primitive of epoch e and an earlier one conflict
+// (one of them writes), can hold conflicting step accesses; step accesses
+// outside them are skipped before the step-level matching.
 void fence_edges(Builder &B, const std::vector<uint32_t> &epoch_first) {
+  const hiccl_comm &c = B.c;
+  struct Span {
+    unsigned long long lo, hi;
+  };
+  std::vector<Span> hot;
+  std::vector<std::vector<int>> hot_ranks(c.prims.size());   // per primitive, ranks with hot ranges
+  auto in_hot = [&](unsigned long long lo, unsigned long long hi) {
+    auto it = std::upper_bound(hot.begin(), hot.end(), lo, [](unsigned long long v, const Span &x) { return v < x.hi; });
+    return it != hot.end() && it->lo < hi;
+  };
   auto collect = [&](uint32_t s, std::vector<Access> &out) {
     const HStep &st = B.steps[s];
+    const std::vector<int> &hr = hot_ranks[st.prim];
+    if (hr.empty()) return;
     for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k) {
       const Loc &l = B.locs[st.loc0 + k];
-      if (l.scratch) continue;
+      if (l.scratch || std::find(hr.begin(), hr.end(), l.rank) == hr.end() || !in_hot(l.addr, l.addr + st.nbytes))
+        continue;
       out.push_back(Access{l.addr, l.addr + st.nbytes, s, k >= st.nsrc});
     }
   };
   for (size_t e = 1; e + 1 < epoch_first.size(); ++e) {
     uint32_t first = epoch_first[e], end = epoch_first[e + 1];
     if (first == end || first == 0) continue;
+    // conflicting primitive ranges of epoch e against all earlier epochs
+    RangeIndex earlier;
+    std::vector<Range> mine;
+    for (size_t i = 0; i < c.prims.size(); ++i) {
+      if (c.prims[i].epoch < (int)e) prim_ranges(c, (int)i, earlier.r);
+      else if (c.prims[i].epoch == (int)e) prim_ranges(c, (int)i, mine);
+    }
+    earlier.build();
+    hot.clear();
+    for (auto &v : hot_ranks) v.clear();
+    auto mark = [&](const Range &x) {
+      std::vector<int> &v = hot_ranks[x.prim];
+      if (std::find(v.begin(), v.end(), x.rank) == v.end()) v.push_back(x.rank);
+    };
+    for (const Range &m : mine)
+      earlier.overlaps(m.lo, m.hi, [&](const Range &x) {
+        if (!(m.write || x.write)) return;
+        hot.push_back(Span{std::max(m.lo, x.lo), std::min(m.hi, x.hi)});
+        mark(m);
+        mark(x);
+      });
+    if (hot.empty()) continue;
+    std::sort(hot.begin(), hot.end(), [](const Span &a, const Span &b) { return a.lo < b.lo; });
+    size_t w = 0;
+    for (size_t k = 1; k < hot.size(); ++k) {
+      if (hot[k].lo <= hot[w].hi) hot[w].hi = std::max(hot[w].hi, hot[k].hi);
+      else hot[++w] = hot[k];
+    }
+    hot.resize(w + 1);
+    // step accesses inside the hot ranges
     std::vector<Access> prev;
     for (uint32_t s = 0; s < first; ++s) collect(s, prev);
     if (prev.empty()) continue;
@@ -450,10 +596,12 @@ void fence_edges(Builder &B, const std::vector<uint32_t> &epoch_first) {
     std::vector<unsigned long long> pmax(prev.size());
     for (size_t k = 0; k < prev.size(); ++k) pmax[k] = std::max(prev[k].hi, k ? pmax[k - 1] : 0ull);
     std::vector<Access> cur;
+    std::vector<uint32_t> found;
     for (uint32_t s = first; s < end; ++s) {
       cur.clear();
       collect(s, cur);
-      std::vector<uint32_t> found;
+      if (cur.empty()) continue;
+      found.clear();
       for (const Access &a : cur) {
         size_t k = std::lower_bound(prev.begin(), prev.end(), a.hi,
                                     [](const Access &x, unsigned long long v) { return x.lo < v; }) -
@@ -472,36 +620,14 @@ void fence_edges(Builder &B, const std::vector<uint32_t> &epoch_first) {
   }
 }
 
-struct Range {
-  unsigned long long lo, hi;
-  int prim;
-  bool write;
-};
-
 // race check (Sec. 3.2): primitives of one epoch must not write what another
 // reads or writes; a primitive's own writes must not overlap each other or its
 // reads, except an exact in-place root
 bool find_race(const hiccl_comm &c, std::string &msg) {
   for (int e = 0; e < c.epochs; ++e) {
     std::vector<Range> rs;
-    for (size_t i = 0; i < c.prims.size(); ++i) {
-      const Prim &p = c.prims[i];
-      if (p.epoch != e || p.count == 0) continue;
-      unsigned long long n = (unsigned long long)p.count * c.esize;
-      if (p.kind == 0) {
-        rs.push_back(Range{p.send[p.root], p.send[p.root] + n, (int)i, false});
-        for (int j : p.leaves) {
-          if (j == p.root && p.recv[j] == p.send[p.root]) continue;
-          rs.push_back(Range{p.recv[j], p.recv[j] + n, (int)i, true});
-        }
-      } else {
-        for (int j : p.leaves) {
-          if (j == p.root && p.send[j] == p.recv[p.root]) continue;   // exact in place
-          rs.push_back(Range{p.send[j], p.send[j] + n, (int)i, false});
-        }
-        rs.push_back(Range{p.recv[p.root], p.recv[p.root] + n, (int)i, true});
-      }
-    }
+    for (size_t i = 0; i < c.prims.size(); ++i)
+      if (c.prims[i].epoch == e) prim_ranges(c, (int)i, rs);
     std::sort(rs.begin(), rs.end(), [](const Range &a, const Range &b) { return a.lo < b.lo; });
     for (size_t a = 0; a < rs.size(); ++a) {
       for (size_t b = a + 1; b < rs.size() && rs[b].lo < rs[a].hi; ++b) {
