@@ -73,7 +73,7 @@ struct DevRun {
 // operand pointers of the entries' steps.  A pointer offset with PTR_GLOBAL
 // set indexes the global pointer array instead (steps with many operands, or
 // an item whose inline pointer area is full).
-constexpr uint32_t PTR_CAP = 384;              // inline pointers per item
+constexpr uint32_t PTR_CAP = 192;              // inline pointers per item
 constexpr uint32_t PTR_STEP_MAX = 64;          // a step with more operands keeps them global
 constexpr uint32_t PTR_GLOBAL = 0x80000000u;
 struct RecEnt {

@@ -514,7 +514,7 @@ __device__ __forceinline__ void release_succ(const DevTable &T, uint32_t a, uint
 template <int NT>
 struct ExecShape {
   static constexpr int D = NT / 32 - 2;                 // data warps
-  static constexpr int NS = NT >= 512 ? 2 : NT >= 256 ? 3 : 4;   // staging slots per data warp
+  static constexpr int NS = NT >= 512 ? 2 : 4;   // staging slots per data warp
   static constexpr int SMEM = D * NS * SEG_BYTES;       // dynamic shared memory (bytes)
 };
 
