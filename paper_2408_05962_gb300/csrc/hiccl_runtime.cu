@@ -301,20 +301,22 @@ __device__ __forceinline__ void warp_copy(const unsigned long long *ptrs, uint32
   const char *src = reinterpret_cast<const char *>(ptrs[0]) + lo;
   uint32_t done = 0;
   if (aligned) {
-    constexpr int U = SEG_BYTES / (16 * 32);   // one pass covers the segment
+    constexpr int U = 8;   // 4 KiB per pass
     const uint32_t nvec = n >> 4;
-    uint4 v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint32_t i = u * 32 + lane;
-      if (i < nvec) v[u] = ld16(src + (i << 4));
-    }
-    for (uint32_t k = 0; k < ndst; ++k) {
-      char *dst = reinterpret_cast<char *>(ptrs[1 + k]) + lo;
+    for (uint32_t base = 0; base < nvec; base += 32 * U) {
+      uint4 v[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const uint32_t i = u * 32 + lane;
-        if (i < nvec) st16(dst + (i << 4), v[u]);
+        const uint32_t i = base + u * 32 + lane;
+        if (i < nvec) v[u] = ld16(src + (i << 4));
+      }
+      for (uint32_t k = 0; k < ndst; ++k) {
+        char *dst = reinterpret_cast<char *>(ptrs[1 + k]) + lo;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const uint32_t i = base + u * 32 + lane;
+          if (i < nvec) st16(dst + (i << 4), v[u]);
+        }
       }
     }
     done = nvec << 4;
