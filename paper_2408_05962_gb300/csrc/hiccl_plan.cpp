@@ -23,6 +23,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -664,41 +665,63 @@ void build_image(const Plan &p, unsigned long long relay_base, TableImage &im) {
   }
   const size_t NI = p.item_off.empty() ? 0 : p.item_off.size() - 1;
   im.items.assign(NI, DevItem{});
-  im.recs.clear();
-  std::vector<RecEnt> ents;
-  std::vector<unsigned long long> iptr;
-  std::vector<uint32_t> rpre;
+  // pass 1: record sizes and offsets (the inline-pointer decision is the same
+  // in both passes: entries in order while the step's operands fit)
+  std::vector<unsigned long long> at(NI + 1, 0);
   for (size_t i = 0; i < NI; ++i) {
-    const uint32_t e0 = p.item_off[i], e1 = p.item_off[i + 1];
-    const uint32_t r0 = p.run_off[i], r1 = p.run_off[i + 1];
-    ents.clear();
-    iptr.clear();
-    for (uint32_t e = e0; e < e1; ++e) {
-      const uint32_t s = p.entries[e].step;
-      const HStep &st = p.steps[s];
+    uint32_t nptr = 0;
+    for (uint32_t e = p.item_off[i]; e < p.item_off[i + 1]; ++e) {
+      const HStep &st = p.steps[p.entries[e].step];
       const uint32_t np = st.nsrc + st.ndst;
-      RecEnt re{s, meta[s], PTR_GLOBAL | st.loc0, im.indeg[s]};
-      if (np <= PTR_STEP_MAX && iptr.size() + np <= PTR_CAP) {
-        re.poff = (uint32_t)iptr.size();
-        iptr.insert(iptr.end(), im.ptrs.begin() + st.loc0, im.ptrs.begin() + st.loc0 + np);
-      }
-      ents.push_back(re);
+      if (np <= PTR_STEP_MAX && nptr + np <= PTR_CAP) nptr += np;
     }
-    rpre.assign(1, 0u);
-    for (uint32_t r = r0; r < r1; ++r)
-      rpre.push_back(rpre.back() + (uint32_t)((p.runs[r].bytes + p.seg - 1) / p.seg));
-    DevItem it{(uint32_t)(im.recs.size() / 16), e1 - e0, r1 - r0, (uint32_t)iptr.size()};
-    const size_t at = im.recs.size();
-    im.recs.resize(at + rec_bytes(it), 0);
-    unsigned char *q = im.recs.data() + at;
-    std::memcpy(q, ents.data(), ents.size() * sizeof(RecEnt));
-    q += rec_ent_bytes(it.nent);
-    std::memcpy(q, rpre.data(), rpre.size() * 4);
-    q += rec_rpre_bytes(it.nrun);
-    if (r1 > r0) std::memcpy(q, &p.runs[r0], (r1 - r0) * sizeof(DevRun));
-    q += rec_run_bytes(it.nrun);
-    if (!iptr.empty()) std::memcpy(q, iptr.data(), iptr.size() * 8);
-    im.items[i] = it;
+    DevItem &it = im.items[i];
+    it.rec = (uint32_t)(at[i] / 16);
+    it.nent = p.item_off[i + 1] - p.item_off[i];
+    it.nrun = p.run_off[i + 1] - p.run_off[i];
+    it.nptr = nptr;
+    at[i + 1] = at[i] + rec_bytes(it);
+  }
+  im.recs.assign(at[NI], 0);
+  // pass 2: fill the records in place, in parallel for large plans
+  auto fill = [&](size_t i0, size_t i1) {
+    for (size_t i = i0; i < i1; ++i) {
+      const DevItem &it = im.items[i];
+      unsigned char *q = im.recs.data() + at[i];
+      RecEnt *ent = reinterpret_cast<RecEnt *>(q);
+      uint32_t *rpre = reinterpret_cast<uint32_t *>(q + rec_ent_bytes(it.nent));
+      DevRun *run = reinterpret_cast<DevRun *>(q + rec_ent_bytes(it.nent) + rec_rpre_bytes(it.nrun));
+      unsigned long long *ptr = reinterpret_cast<unsigned long long *>(q + rec_ent_bytes(it.nent) +
+                                                                       rec_rpre_bytes(it.nrun) + rec_run_bytes(it.nrun));
+      uint32_t nptr = 0;
+      const uint32_t e0 = p.item_off[i];
+      for (uint32_t k = 0; k < it.nent; ++k) {
+        const uint32_t st_i = p.entries[e0 + k].step;
+        const HStep &st = p.steps[st_i];
+        const uint32_t np = st.nsrc + st.ndst;
+        RecEnt re{st_i, meta[st_i], PTR_GLOBAL | st.loc0, im.indeg[st_i]};
+        if (np <= PTR_STEP_MAX && nptr + np <= PTR_CAP) {
+          re.poff = nptr;
+          std::memcpy(ptr + nptr, im.ptrs.data() + st.loc0, np * 8);
+          nptr += np;
+        }
+        ent[k] = re;
+      }
+      const uint32_t r0 = p.run_off[i];
+      rpre[0] = 0;
+      for (uint32_t r = 0; r < it.nrun; ++r) {
+        rpre[r + 1] = rpre[r] + (uint32_t)((p.runs[r0 + r].bytes + p.seg - 1) / p.seg);
+        run[r] = p.runs[r0 + r];
+      }
+    }
+  };
+  const size_t nthr = NI >= 32768 ? std::min<size_t>(8, std::max(1u, std::thread::hardware_concurrency())) : 1;
+  if (nthr <= 1) {
+    fill(0, NI);
+  } else {
+    std::vector<std::thread> th;
+    for (size_t t = 0; t < nthr; ++t) th.emplace_back(fill, NI * t / nthr, NI * (t + 1) / nthr);
+    for (auto &x : th) x.join();
   }
 }
 
