@@ -297,6 +297,36 @@ def _fp8_blocks(x):
     return out.reshape(P, -1)
 
 
+def _decode_rows(t, dtype):
+    """Payload rows (device) -> binary32 values (device)."""
+    import torch
+    if dtype == "bf16":
+        return (t.to(torch.int32) << 16).view(torch.float32)
+    blk = t.reshape(t.shape[0], -1, 144)
+    codes = blk[:, :, :128].contiguous().view(torch.float8_e4m3fn).to(torch.float32)
+    scale = blk[:, :, 128:132].contiguous().view(torch.float32)
+    return (codes * scale).reshape(t.shape[0], -1)
+
+
+def _lowprec_accuracy(b, dtype, xs, device):
+    """Error of the reduced-precision All-reduce result, measured after the
+    timed region with plain torch arithmetic: relative L2 and max-norm errors
+    against the FP64 sum of the decoded inputs, and the relative L2 error
+    against the FP64 sum of the unquantized binary32 sources."""
+    import torch
+    P = b.send.shape[0]
+    y64 = torch.zeros(_decode_rows(b.send[:1], dtype).shape[1], dtype=torch.float64, device=device)
+    x64 = torch.zeros_like(y64)
+    for r in range(P):
+        y64 += _decode_rows(b.send[r:r + 1], dtype)[0].double()
+        x64 += torch.from_numpy(xs[r]).to(device).double()
+    y = _decode_rows(b.recv[:1], dtype)[0].double()
+    return {"rel_l2_vs_fp64_of_decoded": float((y - y64).norm() / y64.norm()),
+            "rel_max_vs_fp64_of_decoded": float((y - y64).abs().max() / y64.abs().max()),
+            "rel_l2_vs_fp64_of_unquantized": float((y - x64).norm() / x64.norm()),
+            "bound_rel_l2": 1e-2 if dtype == "bf16" else 6e-2}
+
+
 def run_ours(args):
     import torch
 
@@ -447,6 +477,10 @@ def run_ours(args):
         b, t, desc = oracle_sample(args.cpu_budget)
         cpu = {"value": b / t / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc}
 
+    accuracy = None
+    if dtype in ("bf16", "fp8") and "allreduce" in bufs:
+        accuracy = _lowprec_accuracy(bufs["allreduce"], dtype, xs, device)
+
     coll = {}
     for kind in kinds:
         med = statistics.median(per_kind[kind])
@@ -477,6 +511,8 @@ def run_ours(args):
         "collectives": coll, "wall_ms_per_step": wall / args.steps * 1e3,
         "cpu_baseline": cpu,
     }
+    if accuracy:
+        line["accuracy"] = accuracy
     if rank == 0:
         print(json.dumps(line), flush=True)
     for c in comms.values():
