@@ -13,9 +13,11 @@ Formats, written from their definitions:
 * **FP8 block** (this library's payload layout): 128 e4m3 codes followed by
   their binary32 scale and 12 zero bytes -- 144 bytes per 128 elements.  The
   value of code q is decode(q) * scale.  Quantizing a block of binary32
-  values x: amax = max|x|; scale = amax / 448 and inv = 448 / amax (binary32
-  divisions; both 1 when amax is 0); codes = encode(x * inv) (binary32
-  multiply: one reciprocal per block rather than a division per value).
+  values x: amax = max|x| over the values that are not NaN (0 when there are
+  none); scale = amax / 448 and inv = 448 / amax (binary32 divisions; both 1
+  when amax is 0); codes = encode(x * inv) (binary32 multiply: one
+  reciprocal per block rather than a division per value), so a NaN value
+  stays a NaN code and does not poison its block.
 
 Reduction of these payloads (the reading of "FP32 accumulation"): every
 input of a reduce step is decoded to binary32, the inputs are folded in the
@@ -110,7 +112,7 @@ def fp8_quantize(x: np.ndarray) -> np.ndarray:
     """binary32 values (length a multiple of 128) -> array of FP8 blocks."""
     x = np.asarray(x, dtype=np.float32).reshape(-1, FP8_BLOCK)
     out = np.zeros(x.shape[0], dtype=FP8_BLOCK_DTYPE)
-    amax = np.max(np.abs(x), axis=1)
+    amax = np.max(np.where(np.isnan(x), np.float32(0), np.abs(x)), axis=1)
     zero = amax == 0
     safe = np.where(zero, np.float32(1.0), amax).astype(np.float32)
     scale = np.where(zero, np.float32(1.0), (safe / np.float32(FP8_MAX)).astype(np.float32)).astype(np.float32)

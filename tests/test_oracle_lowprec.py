@@ -154,3 +154,18 @@ def test_lowprec_simulated_equals_semantics(dtype, name, P, h, s, m):
     simulate(factorize(prog, h, s, m), got, order_seed=s + m)
     for k in ref:
         assert np.array_equal(ref[k].view(np.uint8), got[k].view(np.uint8)), k
+
+
+def test_fp8_block_amax_ignores_nan():
+    """A NaN value stays a NaN code without poisoning its block: the scale
+    comes from the largest magnitude that is not NaN, and a block of NaNs
+    only keeps scale 1."""
+    x = np.linspace(-2.0, 3.0, 128, dtype=np.float32)
+    x[5] = np.nan
+    b = LP.fp8_quantize(x)
+    assert b["s"][0] == np.float32(np.float32(3.0) / np.float32(448.0))
+    y = LP.fp8_dequantize(b)
+    assert np.isnan(y[5]) and np.sum(np.isnan(y)) == 1
+    assert float(y[-1]) == 3.0
+    allnan = LP.fp8_quantize(np.full(128, np.nan, np.float32))
+    assert allnan["s"][0] == 1.0 and np.all(np.isnan(LP.fp8_dequantize(allnan)))
