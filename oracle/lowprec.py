@@ -118,14 +118,16 @@ def fp8_quantize(x: np.ndarray) -> np.ndarray:
     scale = np.where(zero, np.float32(1.0), (safe / np.float32(FP8_MAX)).astype(np.float32)).astype(np.float32)
     inv = np.where(zero, np.float32(1.0), (np.float32(FP8_MAX) / safe).astype(np.float32)).astype(np.float32)
     out["s"] = scale
-    out["q"] = e4m3_encode((x * inv[:, None]).astype(np.float32))
+    with np.errstate(invalid="ignore", over="ignore"):    # infinite or NaN values stay so
+        out["q"] = e4m3_encode((x * inv[:, None]).astype(np.float32))
     return out
 
 
 def fp8_dequantize(b: np.ndarray) -> np.ndarray:
     """array of FP8 blocks -> binary32 values."""
     b = np.asarray(b, dtype=FP8_BLOCK_DTYPE)
-    return (e4m3_decode(b["q"]) * b["s"][:, None]).astype(np.float32).reshape(-1)
+    with np.errstate(invalid="ignore", over="ignore"):
+        return (e4m3_decode(b["q"]) * b["s"][:, None]).astype(np.float32).reshape(-1)
 
 
 # ---------------------------------------------------------------------------
