@@ -308,6 +308,23 @@ hiccl_status_t hiccl_set_option(hiccl_comm_t comm, hiccl_option_t opt, long long
  * hiccl_wait.  HICCL_ERR_STATE if tracing was not enabled. */
 hiccl_status_t hiccl_get_trace(hiccl_comm_t comm, unsigned long long *out, size_t capacity, size_t *written);
 
+/* Check a planned table before it reaches the GPU (hiccl_init and
+ * hiccl_group also run this check): the table order is topological (so the
+ * dependency graph is acyclic) and the successor lists mirror it; every
+ * user-buffer operand lies in its primitive's registered ranges and every
+ * relay operand in the relay arena; the work-item entries of each step tile
+ * its segments exactly once; no item mixes pipeline slots or exceeds 64
+ * entries; the runs of an item cover its entries.  HICCL_ERR_INVALID with the
+ * first violation in hiccl_last_error; HICCL_ERR_STATE without a plan. */
+hiccl_status_t hiccl_validate(hiccl_comm_t comm);
+
+/* Host-side fault injection for tests of hiccl_validate: corrupt the host
+ * copy of a planned (hiccl_plan, not uploaded) table.  what = 0: make a step
+ * depend on a later step (a cycle); 1: move a user-buffer operand out of its
+ * primitive's buffers; 2: drop the last entry's segments.  Nothing of it
+ * reaches the GPU: hiccl_init on the corrupted communicator is refused. */
+hiccl_status_t hiccl_debug_corrupt(hiccl_comm_t comm, int what);
+
 /* Fault injection for tests: add `extra` (0 restores) phantom dependencies to
  * step `index` in the uploaded table, so that the executor's bounded wait for
  * it runs out and hiccl_wait reports HICCL_ERR_TIMEOUT.  Host-side only: it

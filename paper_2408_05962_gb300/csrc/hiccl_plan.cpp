@@ -726,6 +726,93 @@ void build_image(const Plan &p, unsigned long long relay_base, TableImage &im) {
 }
 
 
+// Consistency of a finished plan, checked before anything reaches the GPU:
+// the table order is topological (every predecessor precedes its step, so
+// the dependency graph has no cycle) and the successor lists mirror it;
+// every user-buffer operand lies in its primitive's registered ranges and
+// every relay operand inside the relay arena; the entries of each step tile
+// its segments exactly once, in order; no item mixes slots (an item never
+// waits on itself) or exceeds its entry bound; the runs of each item cover
+// its entries' bytes.  Returns false with a message on the first violation.
+bool validate_plan(const hiccl_comm &c, const Plan &p, std::string &msg) {
+  const size_t N = p.steps.size();
+  auto bad = [&](const std::string &m) {
+    msg = m;
+    return false;
+  };
+  if (p.pred_off.size() != N + 1 || p.succ_off.size() != N + 1 || p.nent.size() != N)
+    return bad("table arrays have the wrong size");
+  std::vector<uint32_t> nsucc(N, 0);
+  for (size_t i = 0; i < N; ++i)
+    for (uint32_t k = p.pred_off[i]; k < p.pred_off[i + 1]; ++k) {
+      const uint32_t q = p.preds[k];
+      if (q >= i) return bad("step " + std::to_string(i) + " depends on a later step " + std::to_string(q));
+      ++nsucc[q];
+    }
+  for (size_t q = 0; q < N; ++q) {
+    if (p.succ_off[q + 1] - p.succ_off[q] != nsucc[q])
+      return bad("successor list of step " + std::to_string(q) + " does not mirror the predecessors");
+    for (uint32_t k = p.succ_off[q]; k < p.succ_off[q + 1]; ++k)
+      if (p.succ[k] <= q || p.succ[k] >= N) return bad("bad successor of step " + std::to_string(q));
+  }
+  for (size_t i = 0; i < N; ++i) {
+    const HStep &st = p.steps[i];
+    if (st.nsrc == 0 || st.ndst == 0 || (size_t)st.loc0 + st.nsrc + st.ndst > p.locs.size())
+      return bad("step " + std::to_string(i) + " has bad operands");
+    for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k) {
+      const Loc &l = p.locs[st.loc0 + k];
+      if (l.scratch) {
+        if (l.addr + st.nbytes > p.scratch_bytes) return bad("relay operand of step " + std::to_string(i) + " outside the arena");
+        continue;
+      }
+      if (c.group || st.prim < 0 || (size_t)st.prim >= c.prims.size()) continue;
+      const Prim &pr = c.prims[st.prim];
+      const unsigned long long n = (unsigned long long)pr.count * c.esize;
+      if (l.rank < 0 || l.rank >= c.P) return bad("operand of step " + std::to_string(i) + " has a bad rank");
+      const unsigned long long sb = pr.send[l.rank], rb = pr.recv[l.rank];
+      const bool in_send = sb && l.addr >= sb && l.addr + st.nbytes <= sb + n;
+      const bool in_recv = rb && l.addr >= rb && l.addr + st.nbytes <= rb + n;
+      if (!in_send && !in_recv)
+        return bad("operand " + std::to_string(k) + " of step " + std::to_string(i) +
+                   " lies outside its primitive's buffers");
+    }
+  }
+  std::vector<unsigned long long> next(N, 0);
+  std::vector<uint32_t> cnt(N, 0);
+  for (const DevEntry &e : p.entries) {
+    if (e.step >= N || e.seg_lo != next[e.step] || e.seg_hi <= e.seg_lo)
+      return bad("entries of step " + std::to_string(e.step) + " do not tile its segments");
+    next[e.step] = e.seg_hi;
+    ++cnt[e.step];
+  }
+  for (size_t i = 0; i < N; ++i) {
+    const unsigned long long nseg = (p.steps[i].nbytes + p.seg - 1) / p.seg;
+    if (next[i] != nseg || cnt[i] != p.nent[i])
+      return bad("entries of step " + std::to_string(i) + " do not cover it exactly once");
+  }
+  if (p.item_off.empty() || p.item_off.back() != p.entries.size() || p.run_off.size() != p.item_off.size())
+    return bad("item offsets do not cover the entries");
+  for (size_t it = 0; it + 1 < p.item_off.size(); ++it) {
+    const uint32_t e0 = p.item_off[it], e1 = p.item_off[it + 1];
+    if (e1 <= e0 || e1 - e0 > MAX_ENTRIES_PER_ITEM) return bad("item " + std::to_string(it) + " has a bad size");
+    unsigned long long bytes = 0;
+    for (uint32_t e = e0; e < e1; ++e) {
+      const DevEntry &en = p.entries[e];
+      if (p.steps[en.step].slot != p.steps[p.entries[e0].step].slot)
+        return bad("item " + std::to_string(it) + " mixes pipeline slots");
+      bytes += std::min<unsigned long long>(p.steps[en.step].nbytes, (unsigned long long)en.seg_hi * p.seg) -
+               (unsigned long long)en.seg_lo * p.seg;
+    }
+    unsigned long long rbytes = 0;
+    for (uint32_t r = p.run_off[it]; r < p.run_off[it + 1]; ++r) {
+      if (p.runs[r].entry >= e1 - e0) return bad("run of item " + std::to_string(it) + " names a bad entry");
+      rbytes += p.runs[r].bytes;
+    }
+    if (rbytes != bytes) return bad("runs of item " + std::to_string(it) + " do not cover its entries");
+  }
+  return true;
+}
+
 static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevels, int stripe,
                                  int pipeline) {
   if (!hierarchy || nlevels < 1 || nlevels > 64) return fail(c, HICCL_ERR_INVALID, "bad hierarchy");
@@ -1013,6 +1100,10 @@ static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevel
   plan.stages = N ? maxdepth + 1 : 0;
   plan.slots = N ? maxslot + 1 : 0;
   plan.valid = true;
+  {
+    std::string why;
+    if (!validate_plan(*c, plan, why)) return fail(c, HICCL_ERR_INVALID, "internal plan check: " + why);
+  }
   c->plan = std::move(plan);
   return HICCL_OK;
 }
@@ -1343,6 +1434,13 @@ hiccl_status_t hiccl_group(const hiccl_comm_t *comms, int n, hiccl_comm_t *out) 
   P.entries.swap(ents);
   P.runs.swap(runs);
   P.valid = true;
+  {
+    std::string why;
+    if (!validate_plan(*g, P, why)) {
+      hiccl_destroy(g);
+      return HICCL_ERR_INVALID;
+    }
+  }
   g->state = hiccl_comm::PLANNED;
   hiccl_status_t st = dev_upload(g);
   if (st != HICCL_OK) {
@@ -1370,6 +1468,48 @@ hiccl_status_t hiccl_hbm_bytes(hiccl_comm_t c, unsigned long long *rd, unsigned 
   if (rd) *rd = c->plan.hbm_read;
   if (wr) *wr = c->plan.hbm_write;
   return HICCL_OK;
+}
+
+hiccl_status_t hiccl_validate(hiccl_comm_t c) {
+  if (!c) return HICCL_ERR_INVALID;
+  if (!c->plan.valid) return fail(c, HICCL_ERR_STATE, "no plan");
+  std::string why;
+  if (!validate_plan(*c, c->plan, why)) return fail(c, HICCL_ERR_INVALID, "plan check: " + why);
+  return HICCL_OK;
+}
+
+hiccl_status_t hiccl_debug_corrupt(hiccl_comm_t c, int what) {
+  if (!c) return HICCL_ERR_INVALID;
+  if (c->state != hiccl_comm::PLANNED || !c->plan.valid)
+    return fail(c, HICCL_ERR_STATE, "needs a planned communicator that is not uploaded");
+  Plan &p = c->plan;
+  const size_t N = p.steps.size();
+  switch (what) {
+    case 0: {   // a dependency on a later step: a cycle in the dependency graph
+      for (size_t i = 0; i + 1 < N; ++i)
+        if (p.pred_off[i + 1] > p.pred_off[i]) {
+          p.preds[p.pred_off[i]] = (uint32_t)(N - 1);
+          return HICCL_OK;
+        }
+      return fail(c, HICCL_ERR_INVALID, "no step with a predecessor");
+    }
+    case 1: {   // a user-buffer operand moved out of its primitive's buffers
+      for (const HStep &st : p.steps)
+        for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k)
+          if (!p.locs[st.loc0 + k].scratch) {
+            p.locs[st.loc0 + k].addr += (unsigned long long)c->prims[st.prim].count * c->esize + 4096;
+            return HICCL_OK;
+          }
+      return fail(c, HICCL_ERR_INVALID, "no user operand");
+    }
+    case 2: {   // the last entry of a step dropped: segments left uncovered
+      if (p.entries.empty()) return fail(c, HICCL_ERR_INVALID, "no entries");
+      p.entries.back().seg_hi = p.entries.back().seg_lo;
+      return HICCL_OK;
+    }
+    default:
+      return fail(c, HICCL_ERR_INVALID, "unknown corruption");
+  }
 }
 
 hiccl_status_t hiccl_plan_info(hiccl_comm_t c, hiccl_plan_info_t *out) {

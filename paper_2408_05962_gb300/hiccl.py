@@ -109,6 +109,8 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_ulonglong)]),
     "hiccl_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong]),
     "hiccl_debug_withhold": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_int]),
+    "hiccl_validate": (ctypes.c_int, [ctypes.c_void_p]),
+    "hiccl_debug_corrupt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "hiccl_run_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "hiccl_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(TuneResult)]),
     "hiccl_group": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
@@ -265,6 +267,14 @@ def hiccl_set_option(comm, opt: int, value: int):
     _check(comm, lib().hiccl_set_option(comm, int(opt), int(value)))
 
 
+def hiccl_validate(comm):
+    _check(comm, lib().hiccl_validate(comm))
+
+
+def hiccl_debug_corrupt(comm, what: int):
+    _check(comm, lib().hiccl_debug_corrupt(comm, int(what)))
+
+
 def hiccl_debug_withhold(comm, index: int, extra: int):
     _check(comm, lib().hiccl_debug_withhold(comm, int(index), int(extra)))
 
@@ -385,6 +395,12 @@ class Comm:
 
     def set_option(self, opt, value):
         hiccl_set_option(self.handle, opt, value)
+
+    def validate(self):
+        hiccl_validate(self.handle)
+
+    def corrupt(self, what):
+        hiccl_debug_corrupt(self.handle, what)
 
     def withhold(self, index, extra):
         hiccl_debug_withhold(self.handle, index, extra)

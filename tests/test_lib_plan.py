@@ -270,3 +270,32 @@ def test_planner_scales_to_a_thousand_ranks():
     assert info["stages"] == 3 and info["steps"] > 0
     assert comm.level_bytes()[0] == 256 * (P - 4) * d * 4
     assert dt < 60.0, dt
+
+
+@pytest.mark.parametrize("what,needle", [(0, "depends on a later step"), (1, "outside its primitive"),
+                                         (2, "do not tile")])
+def test_corrupted_tables_are_caught_on_the_host(what, needle):
+    """Host-side fault tests: a table with a dependency cycle, an operand
+    outside its primitive's buffers, or uncovered segments is rejected by the
+    plan check before anything reaches the GPU (and hiccl_init on it is
+    refused); the uncorrupted plan passes the same check."""
+    from paper_2408_05962_gb300 import hiccl as H
+    prog = PR.allreduce(8, 37)
+    fake = FakeAddresses(prog)
+    comm = register(prog, fake.addr)
+    comm.plan([2, 4], 2, 2)
+    comm.validate()
+    comm.corrupt(what)
+    with pytest.raises(H.HicclError) as e:
+        comm.validate()
+    assert e.value.status == H.ERR_INVALID
+    assert needle in H.hiccl_last_error(comm.handle)
+
+
+@pytest.mark.parametrize("name", COLL)
+def test_every_plan_passes_the_check(name):
+    for P, h, s, m in [(8, [2, 4], 4, 3), (12, [2, 2, 3], 3, 2)]:
+        prog = PR.BUILDERS[name](P, 11)
+        comm = register(prog, FakeAddresses(prog).addr)
+        comm.plan(h, s, m)
+        comm.validate()
