@@ -747,6 +747,8 @@ bool validate_plan(const hiccl_comm &c, const Plan &p, std::string &msg) {
     for (uint32_t k = p.pred_off[i]; k < p.pred_off[i + 1]; ++k) {
       const uint32_t q = p.preds[k];
       if (q >= i) return bad("step " + std::to_string(i) + " depends on a later step " + std::to_string(q));
+      if (p.steps[q].slot >= p.steps[i].slot)
+        return bad("step " + std::to_string(i) + " is not in a later pipeline slot than its predecessor");
       ++nsucc[q];
     }
   for (size_t q = 0; q < N; ++q) {
