@@ -9,11 +9,10 @@ payload) arrive at any time.  The server
 * plans admitted requests on a pool of host threads (the native factorizer
   and the table upload; ctypes releases the GIL during the calls);
 * launches planned requests on whichever of its ``slots`` CUDA streams is
-  free -- each request alone (``max_batch`` 1), or up to ``max_batch``
+  free -- each request alone (``group_max`` 1), or up to ``group_max``
   waiting requests together as one grouped persistent launch
-  (``hiccl_group``, whose combined table is built on a planner thread);
-  requests that arrive while others run take the next free slot, and
-  launches on different slots overlap on the device;
+  (``hiccl_group``); requests that arrive while others run take the next free
+  slot, and launches on different slots overlap on the device;
 * retires a launch when its event completes, freeing its memory and recording
   each request's latency (completion observed minus arrival).
 
@@ -101,8 +100,8 @@ class Server:
         import torch
         self.device = torch.device(device)
         self.arena = DeviceArena(budget_bytes, self.device)
-        self.slots = [{"stream": torch.cuda.Stream(self.device), "event": None, "group": None, "reqs": [],
-                       "pending": None} for _ in range(slots)]
+        self.slots = [{"stream": torch.cuda.Stream(self.device), "event": None, "group": None, "reqs": []}
+                      for _ in range(slots)]
         self.max_batch = max_batch
         self.pool = ThreadPoolExecutor(max_workers=planners)
         self.waiting: deque = deque()     # submitted, not admitted
@@ -174,43 +173,25 @@ class Server:
                 keep.append((fut, req))
         self.planning = keep
 
-    def _start(self, sl, grp, batch):
-        import torch
-        now = time.perf_counter()
-        for r in batch:
-            r.t_launch = now
-        grp.start(sl["stream"])
-        ev = torch.cuda.Event()
-        ev.record(sl["stream"])
-        sl["event"], sl["group"], sl["reqs"] = ev, grp, batch
-        self.launches += 1
-
     def _launch(self):
         for sl in self.slots:
-            if sl["event"] is not None:
-                continue
-            if sl["pending"] is not None:        # a group being built on a planner thread
-                fut, batch = sl["pending"]
-                if not fut.done():
-                    continue
-                sl["pending"] = None
-                err = fut.exception()
-                if err is not None:
-                    for r in batch:
-                        r.error = str(err)
-                        self._finish(r, time.perf_counter())
-                    continue
-                self._start(sl, fut.result(), batch)
-                continue
             if not self.ready:
+                return
+            if sl["event"] is not None:
                 continue
             batch = []
             while self.ready and len(batch) < self.max_batch:
                 batch.append(self.ready.popleft())
-            if len(batch) == 1 and self.max_batch == 1:
-                self._start(sl, batch[0].comm, batch)
-            else:   # the combined table is built and uploaded off the polling thread
-                sl["pending"] = (self.pool.submit(H.Comm.group, [r.comm for r in batch]), batch)
+            grp = batch[0].comm if len(batch) == 1 and self.max_batch == 1 else H.Comm.group([r.comm for r in batch])
+            now = time.perf_counter()
+            for r in batch:
+                r.t_launch = now
+            grp.start(sl["stream"])
+            import torch
+            ev = torch.cuda.Event()
+            ev.record(sl["stream"])
+            sl["event"], sl["group"], sl["reqs"] = ev, grp, batch
+            self.launches += 1
 
     def _retire(self):
         for sl in self.slots:
@@ -247,8 +228,7 @@ class Server:
         self._launch()
 
     def busy(self) -> bool:
-        return bool(self.waiting or self.planning or self.ready
-                    or any(s["event"] is not None or s["pending"] is not None for s in self.slots))
+        return bool(self.waiting or self.planning or self.ready or any(s["event"] for s in self.slots))
 
     def drain(self, timeout_s: float = 600.0):
         t0 = time.perf_counter()
