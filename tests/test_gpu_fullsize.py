@@ -76,3 +76,42 @@ def test_allreduce_64mib_sampled():
     expect = S.nested_fold({r: x[r, idx] for r in range(P)}, h)
     for r in range(P):
         assert np.array_equal(y[r, idx].view(np.uint32), expect.view(np.uint32)), r
+
+
+def test_buffers_beyond_four_gib():
+    """Byte offsets past 2**32 (a 4.5 GiB buffer per rank, 1.2 G values):
+    a Broadcast over {2, 2} with stripe 2 and pipeline 4 and a Reduce of the
+    same size, checked on sampled values (the generators fill the buffers on
+    the device; the expected values are formed from the same samples)."""
+    import torch
+    from paper_2408_05962_gb300 import collectives as C
+    from paper_2408_05962_gb300 import hiccl as H
+    P, h = 4, [2, 2]
+    n = (9 << 29) // 4 // P * P              # 4.5 GiB of fp32 per rank
+    d = n // P
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    for kind in ("broadcast", "reduce"):
+        b = C.Buffers(kind, P, d, torch.float32)
+        b.send.uniform_(-1.0, 1.0, generator=g)
+        b.recv.fill_(-3.0)
+        comm = H.Comm(P, "f32")
+        C.compose(comm, kind, d, b.send_ptrs(), b.recv_ptrs())
+        comm.init(h, 2, 4)
+        comm.start()
+        comm.wait()
+        rng = np.random.Generator(np.random.PCG64(3))
+        idx = np.unique(np.concatenate([rng.integers(0, n, 20000), [0, n - 1, (1 << 30) - 1, 1 << 30, n // 2]]))
+        ti = torch.from_numpy(idx).cuda()
+        xs = b.send[:, ti].cpu().numpy()
+        ys = b.recv[:, ti].cpu().numpy()
+        if kind == "broadcast":
+            for r in range(P):
+                assert np.array_equal(ys[r].view(np.uint32), xs[0].view(np.uint32)), r
+        else:
+            expect = S.nested_fold({r: xs[r] for r in range(P)}, h)
+            assert np.array_equal(ys[0].view(np.uint32), expect.view(np.uint32))
+            assert np.all(ys[1:] == -3.0)
+        comm.destroy()
+        del b
+        torch.cuda.empty_cache()
