@@ -147,6 +147,13 @@ __device__ __forceinline__ uint32_t f32_to_bf16_rn(float x) {
   asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(x));
   return h;
 }
+// two binary32 -> two BF16 (round to nearest even) in one word; the first
+// value lands in the low half
+__device__ __forceinline__ uint32_t f32x2_to_bf16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
 // FP8 e4m3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits, no
 // infinities, S.1111.111 = NaN): two codes -> two binary32 values, exactly
 // (every e4m3 value is a binary16 value); the low byte gives .x
@@ -209,10 +216,10 @@ __device__ __forceinline__ uint4 fold16_bf16(LD ld, uint32_t f, COMB comb) {
     }
   }
   uint4 r;
-  r.x = f32_to_bf16_rn(a[0]) | (f32_to_bf16_rn(a[1]) << 16);
-  r.y = f32_to_bf16_rn(a[2]) | (f32_to_bf16_rn(a[3]) << 16);
-  r.z = f32_to_bf16_rn(a[4]) | (f32_to_bf16_rn(a[5]) << 16);
-  r.w = f32_to_bf16_rn(a[6]) | (f32_to_bf16_rn(a[7]) << 16);
+  r.x = f32x2_to_bf16x2(a[0], a[1]);
+  r.y = f32x2_to_bf16x2(a[2], a[3]);
+  r.z = f32x2_to_bf16x2(a[4], a[5]);
+  r.w = f32x2_to_bf16x2(a[6], a[7]);
   return r;
 }
 template <typename LD>
