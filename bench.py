@@ -297,6 +297,16 @@ def _fp8_blocks(x):
     return out.reshape(P, -1)
 
 
+def min_bytes(kind: str, P: int, B: int) -> int:
+    """HBM bytes a collective cannot avoid on one device: every input byte it
+    needs read once and every output byte written once (B = the largest
+    per-rank buffer, d*P values; root-only results for Reduce and Gather)."""
+    d = B // P
+    return {"broadcast": B + P * B, "reduce": P * B + B, "allgather": P * d + P * B,
+            "reducescatter": P * B + P * d, "allreduce": 2 * P * B, "allreduce_single": 2 * P * B,
+            "scatter": B + P * d, "gather": P * d + B, "alltoall": 2 * P * B}.get(kind, 0)
+
+
 def _decode_rows(t, dtype):
     """Payload rows (device) -> binary32 values (device)."""
     import torch
@@ -361,7 +371,7 @@ def run_ours(args):
             x = None
         else:
             x = torch.from_numpy(xs)
-    comms, bufs, nbytes, pbytes = {}, {}, {}, {}
+    comms, bufs, nbytes, pbytes, mbytes = {}, {}, {}, {}, {}
     kinds = tuple(args.kinds.split(",")) if args.kinds else W["kinds"]
     tdt = {"f32": torch.float32, "bf16": torch.int16, "fp8": torch.uint8}[dtype]
     for kind in kinds:
@@ -387,6 +397,7 @@ def run_ours(args):
         rd, wr = comm.hbm_bytes()
         comms[kind], bufs[kind], nbytes[kind] = comm, b, rd + wr
         pbytes[kind] = H.nbytes(H.DTYPES[dtype], d * Pw)   # the paper's d*p per collective
+        mbytes[kind] = min_bytes(kind, Pw, pbytes[kind])
     stream = torch.cuda.current_stream(device)
     step_bytes = sum(nbytes.values())
 
@@ -486,6 +497,7 @@ def run_ours(args):
         med = statistics.median(per_kind[kind])
         coll[kind] = {"ms": med, "gbs": nbytes[kind] / med / 1e6, "frac": nbytes[kind] / med / 1e6 / peak,
                       "dp_over_t_gbs": pbytes[kind] / med / 1e6, "schedule_bytes": nbytes[kind],
+                      "min_bytes": mbytes[kind], "min_gbs": mbytes[kind] / med / 1e6,
                       "level_bytes": comms[kind].level_bytes(), "steps": comms[kind].plan_info()["steps"]}
     # DRAM bytes of an average executor launch of the default workload, from
     # the committed ncu capture (null for other workloads or options, or once
