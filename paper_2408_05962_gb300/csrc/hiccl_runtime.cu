@@ -718,23 +718,26 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         const uint32_t s0 = v0 ? B.ent[lane].step : 0u, s1 = v1 ? B.ent[lane + 32].step : 0u;
         uint32_t t0 = 0, t1 = 0, a0 = 0, z0 = 0, a1 = 0, z1 = 0;
         unsigned long long o0 = 0, o1 = 0;
+        // a step covered by this entry alone needs no counter: this item
+        // finishes it, and the fence above already orders its data before
+        // the successors' updates below
         if (v0) {
           t0 = ldg_ro(T.nent + s0);
           a0 = ldg_ro(T.succ_off + s0);
           z0 = ldg_ro(T.succ_off + s0 + 1);
-          o0 = atom_relaxed_add(T.done + s0, 1ull);
+          if (t0 > 1) o0 = atom_relaxed_add(T.done + s0, 1ull);
         }
         if (v1) {
           t1 = ldg_ro(T.nent + s1);
           a1 = ldg_ro(T.succ_off + s1);
           z1 = ldg_ro(T.succ_off + s1 + 1);
-          o1 = atom_relaxed_add(T.done + s1, 1ull);
+          if (t1 > 1) o1 = atom_relaxed_add(T.done + s1, 1ull);
         }
-        const bool f0 = v0 && o0 + 1 == (unsigned long long)t0 * epoch;
-        const bool f1 = v1 && o1 + 1 == (unsigned long long)t1 * epoch;
-        // the last finisher of a step acquires the other finishers' data
-        // before it releases the step's successors
-        if (__any_sync(0xffffffffu, f0 || f1)) __threadfence();
+        const bool f0 = v0 && (t0 == 1 || o0 + 1 == (unsigned long long)t0 * epoch);
+        const bool f1 = v1 && (t1 == 1 || o1 + 1 == (unsigned long long)t1 * epoch);
+        // the last finisher of a step split over several items acquires the
+        // other finishers' data before it releases the step's successors
+        if (__any_sync(0xffffffffu, (f0 && t0 > 1) || (f1 && t1 > 1))) __threadfence();
         if (f0) release_succ(T, a0, z0);
         if (f1) release_succ(T, a1, z1);
       }
