@@ -73,7 +73,9 @@ struct DevRun {
 // operand pointers of the entries' steps.  A pointer offset with PTR_GLOBAL
 // set indexes the global pointer array instead (steps with many operands, or
 // an item whose inline pointer area is full).
-constexpr uint32_t PTR_CAP = 192;              // inline pointers per item
+constexpr uint32_t PTR_CAP = 160;              // inline pointers per item
+constexpr uint32_t SUCC_CAP = 128;             // inline successors per item
+constexpr uint32_t SUCC_GLOBAL = 0xffffffffu;  // the item's successor lists stay global
 constexpr uint32_t PTR_STEP_MAX = 64;          // a step with more operands keeps them global
 constexpr uint32_t PTR_GLOBAL = 0x80000000u;
 struct RecEnt {
@@ -87,14 +89,23 @@ struct DevItem {
   uint32_t nent;
   uint32_t nrun;
   uint32_t nptr;    // inline pointers
+  uint32_t nsucc;   // inline successors, or SUCC_GLOBAL
+  uint32_t pad[3];
 };
-static_assert(sizeof(RecEnt) == 16 && sizeof(DevItem) == 16 && sizeof(DevRun) == 24, "record layout");
+static_assert(sizeof(RecEnt) == 16 && sizeof(DevItem) == 32 && sizeof(DevRun) == 24, "record layout");
 HICCL_HD inline uint32_t rec_ent_bytes(uint32_t nent) { return nent * 16u; }
 HICCL_HD inline uint32_t rec_rpre_bytes(uint32_t nrun) { return ((nrun + 1u) * 4u + 15u) & ~15u; }
 HICCL_HD inline uint32_t rec_run_bytes(uint32_t nrun) { return (nrun * 24u + 15u) & ~15u; }
 HICCL_HD inline uint32_t rec_ptr_bytes(uint32_t nptr) { return (nptr * 8u + 15u) & ~15u; }
+// completion section: per entry the step's completion target, then the
+// offsets of the entries' successor lists (nent + 1), then the successors
+HICCL_HD inline uint32_t rec_cmp_words(uint32_t nent, uint32_t nsucc) {
+  return 2u * nent + 1u + (nsucc == SUCC_GLOBAL ? 0u : nsucc);
+}
+HICCL_HD inline uint32_t rec_cmp_bytes(uint32_t nent, uint32_t nsucc) { return (rec_cmp_words(nent, nsucc) * 4u + 15u) & ~15u; }
 HICCL_HD inline uint32_t rec_bytes(const DevItem &it) {
-  return rec_ent_bytes(it.nent) + rec_rpre_bytes(it.nrun) + rec_run_bytes(it.nrun) + rec_ptr_bytes(it.nptr);
+  return rec_ent_bytes(it.nent) + rec_rpre_bytes(it.nrun) + rec_run_bytes(it.nrun) + rec_ptr_bytes(it.nptr) +
+         rec_cmp_bytes(it.nent, it.nsucc);
 }
 
 // per-launch control block (device memory, zeroed at upload)

@@ -675,11 +675,17 @@ void build_image(const Plan &p, unsigned long long relay_base, TableImage &im) {
       const uint32_t np = st.nsrc + st.ndst;
       if (np <= PTR_STEP_MAX && nptr + np <= PTR_CAP) nptr += np;
     }
+    uint32_t nsucc = 0;
+    for (uint32_t e = p.item_off[i]; e < p.item_off[i + 1]; ++e) {
+      const uint32_t st_i = p.entries[e].step;
+      nsucc += p.succ_off[st_i + 1] - p.succ_off[st_i];
+    }
     DevItem &it = im.items[i];
     it.rec = (uint32_t)(at[i] / 16);
     it.nent = p.item_off[i + 1] - p.item_off[i];
     it.nrun = p.run_off[i + 1] - p.run_off[i];
     it.nptr = nptr;
+    it.nsucc = nsucc <= SUCC_CAP ? nsucc : SUCC_GLOBAL;
     at[i + 1] = at[i] + rec_bytes(it);
   }
   im.recs.assign(at[NI], 0);
@@ -712,6 +718,20 @@ void build_image(const Plan &p, unsigned long long relay_base, TableImage &im) {
       for (uint32_t r = 0; r < it.nrun; ++r) {
         rpre[r + 1] = rpre[r] + (uint32_t)((p.runs[r0 + r].bytes + p.seg - 1) / p.seg);
         run[r] = p.runs[r0 + r];
+      }
+      uint32_t *cmp = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(ptr) + rec_ptr_bytes(it.nptr));
+      uint32_t *soff = cmp + it.nent, *sl = cmp + 2 * it.nent + 1;
+      soff[0] = 0;
+      for (uint32_t k = 0; k < it.nent; ++k) {
+        const uint32_t st_i = p.entries[e0 + k].step;
+        cmp[k] = p.nent[st_i];
+        const uint32_t a = p.succ_off[st_i], z = p.succ_off[st_i + 1];
+        if (it.nsucc != SUCC_GLOBAL) {
+          for (uint32_t q = a; q < z; ++q) sl[soff[k] + (q - a)] = p.succ[q];
+          soff[k + 1] = soff[k] + (z - a);
+        } else {
+          soff[k + 1] = 0;
+        }
       }
     }
   };

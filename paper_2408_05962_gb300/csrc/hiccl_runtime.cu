@@ -439,14 +439,16 @@ struct __align__(16) ItemBuf {
   uint32_t rpre[MAX_ENTRIES_PER_ITEM + 4];  // prefix sums of the runs' segment counts
   DevRun run[MAX_ENTRIES_PER_ITEM];         // data ranges (runs of contiguous entries)
   unsigned long long ptr[PTR_CAP];          // inline operand pointers
+  uint32_t cmp[(2 * MAX_ENTRIES_PER_ITEM + 1 + SUCC_CAP + 3) / 4 * 4];   // completion section
   uint32_t nent;
   uint32_t nrun;
   uint32_t end;                             // no more items: leave the loop
-  uint32_t pad;
+  uint32_t nsucc;                           // inline successors, or SUCC_GLOBAL
   unsigned long long item;                  // ticket of the staged item
+  unsigned long long pad;
 };
 static_assert(offsetof(ItemBuf, rpre) % 16 == 0 && offsetof(ItemBuf, run) % 16 == 0 &&
-                  offsetof(ItemBuf, ptr) % 16 == 0 && sizeof(ItemBuf) % 16 == 0,
+                  offsetof(ItemBuf, ptr) % 16 == 0 && offsetof(ItemBuf, cmp) % 16 == 0 && sizeof(ItemBuf) % 16 == 0,
               "bulk-copy destinations must be 16-byte aligned");
 
 // operand pointers of entry k of a staged item
@@ -595,7 +597,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
     // and its record prefetched into L2, while the current item's record is
     // in flight and its predecessors are awaited.
     unsigned long long nxt = 0;
-    DevItem nd{0, 0, 0, 0};
+    DevItem nd{0, 0, 0, 0, 0, {0, 0, 0}};
     if (lane == 0) nxt = atomicAdd(&T.ctl->ticket, 1ull);
     nxt = __shfl_sync(0xffffffffu, nxt, 0);
     if (nxt < T.nitems) nd = T.items[nxt];
@@ -622,14 +624,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         if (lane == 0) {
           const unsigned char *src = T.recs + (size_t)it.rec * 16;
           const uint32_t be = rec_ent_bytes(it.nent), br = rec_rpre_bytes(it.nrun), bu = rec_run_bytes(it.nrun),
-                         bp = rec_ptr_bytes(it.nptr);
-          mbar_expect_tx(&rec_bar[b], be + br + bu + bp);
+                         bp = rec_ptr_bytes(it.nptr), bc = rec_cmp_bytes(it.nent, it.nsucc);
+          mbar_expect_tx(&rec_bar[b], be + br + bu + bp + bc);
           bulk_g2s(B.ent, src, be, &rec_bar[b]);
           bulk_g2s(B.rpre, src + be, br, &rec_bar[b]);
           if (bu) bulk_g2s(B.run, src + be + br, bu, &rec_bar[b]);
           if (bp) bulk_g2s(B.ptr, src + be + br + bu, bp, &rec_bar[b]);
+          bulk_g2s(B.cmp, src + be + br + bu + bp, bc, &rec_bar[b]);
           B.nent = it.nent;
           B.nrun = it.nrun;
+          B.nsucc = it.nsucc;
           nxt = atomicAdd(&T.ctl->ticket, 1ull);
         }
         nxt = __shfl_sync(0xffffffffu, nxt, 0);
@@ -713,7 +717,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
       static_assert(MAX_ENTRIES_PER_ITEM <= 64, "two entries per lane");
       __threadfence();
       {
+        // completion targets and successor lists come from the staged record
+        // (successor lists of an item with too many stay in the global table)
         const uint32_t n = B.nent;
+        const bool inl = B.nsucc != SUCC_GLOBAL;
+        const uint32_t *soff = B.cmp + n, *sl = B.cmp + 2 * n + 1;
         const bool v0 = (uint32_t)lane < n, v1 = (uint32_t)lane + 32 < n;
         const uint32_t s0 = v0 ? B.ent[lane].step : 0u, s1 = v1 ? B.ent[lane + 32].step : 0u;
         uint32_t t0 = 0, t1 = 0, a0 = 0, z0 = 0, a1 = 0, z1 = 0;
@@ -722,15 +730,15 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         // finishes it, and the fence above already orders its data before
         // the successors' updates below
         if (v0) {
-          t0 = ldg_ro(T.nent + s0);
-          a0 = ldg_ro(T.succ_off + s0);
-          z0 = ldg_ro(T.succ_off + s0 + 1);
+          t0 = B.cmp[lane];
+          a0 = inl ? soff[lane] : ldg_ro(T.succ_off + s0);
+          z0 = inl ? soff[lane + 1] : ldg_ro(T.succ_off + s0 + 1);
           if (t0 > 1) o0 = atom_relaxed_add(T.done + s0, 1ull);
         }
         if (v1) {
-          t1 = ldg_ro(T.nent + s1);
-          a1 = ldg_ro(T.succ_off + s1);
-          z1 = ldg_ro(T.succ_off + s1 + 1);
+          t1 = B.cmp[lane + 32];
+          a1 = inl ? soff[lane + 32] : ldg_ro(T.succ_off + s1);
+          z1 = inl ? soff[lane + 33] : ldg_ro(T.succ_off + s1 + 1);
           if (t1 > 1) o1 = atom_relaxed_add(T.done + s1, 1ull);
         }
         const bool f0 = v0 && (t0 == 1 || o0 + 1 == (unsigned long long)t0 * epoch);
@@ -738,8 +746,15 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         // the last finisher of a step split over several items acquires the
         // other finishers' data before it releases the step's successors
         if (__any_sync(0xffffffffu, (f0 && t0 > 1) || (f1 && t1 > 1))) __threadfence();
-        if (f0) release_succ(T, a0, z0);
-        if (f1) release_succ(T, a1, z1);
+        if (inl) {
+          if (f0)
+            for (uint32_t q = a0; q < z0; ++q) red_relaxed_add(T.dep + sl[q], 1ull);
+          if (f1)
+            for (uint32_t q = a1; q < z1; ++q) red_relaxed_add(T.dep + sl[q], 1ull);
+        } else {
+          if (f0) release_succ(T, a0, z0);
+          if (f1) release_succ(T, a1, z1);
+        }
       }
       __syncwarp();
       if (T.trace && lane == 0) T.trace[B.item * 6 + 3] = global_ns();
