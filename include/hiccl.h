@@ -278,7 +278,7 @@ typedef enum {
   HICCL_OPT_ORDER = 3,        /* work order: 0 pipeline slots, 1 stage depth (default)    */
   HICCL_OPT_THREADS = 4,      /* threads per executor CTA: 128, 256 (default), 512       */
   HICCL_OPT_TRACE = 5,        /* 1: record per-item timestamps (hiccl_get_trace); default 0 */
-  HICCL_OPT_SLOT_ITEMS = 6,   /* items a pipeline slot is spread over (default 1024)      */
+  HICCL_OPT_SLOT_ITEMS = 6,   /* items a pipeline slot is spread over (default 768)       */
   HICCL_OPT_RING = 7          /* ring(n) of Sec. 4.4: n nodes chained (default 1, tree)    */
 } hiccl_option_t;
 

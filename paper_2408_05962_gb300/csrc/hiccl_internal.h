@@ -222,7 +222,7 @@ struct hiccl_comm {
   int threads = 256;
   unsigned long long item_bytes = 65536;
   int order = 1;
-  unsigned long long slot_items = 1024;
+  unsigned long long slot_items = 768;
   int trace = 0;
   int ring = 1;                       // ring(n) of Sec. 4.4; 1 = tree only
   hiccl::Plan plan;
