@@ -274,7 +274,7 @@ hiccl_status_t hiccl_get_step(hiccl_comm_t comm, unsigned long long index,
 typedef enum {
   HICCL_OPT_TIMEOUT_NS = 0,   /* dependency-wait limit inside the executor (default 1e9)  */
   HICCL_OPT_CTAS_PER_SM = 1,  /* executor CTAs per SM, capped by occupancy (default 2)    */
-  HICCL_OPT_ITEM_BYTES = 2,   /* largest work item, bytes of step data (default 65536)    */
+  HICCL_OPT_ITEM_BYTES = 2,   /* largest work item, bytes of step data (default 49152; 65536 for FP8) */
   HICCL_OPT_ORDER = 3,        /* work order: 0 pipeline slots, 1 stage depth (default)    */
   HICCL_OPT_THREADS = 4,      /* threads per executor CTA: 128, 256 (default), 512       */
   HICCL_OPT_TRACE = 5,        /* 1: record per-item timestamps (hiccl_get_trace); default 0 */

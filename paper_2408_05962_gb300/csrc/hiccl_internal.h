@@ -220,7 +220,7 @@ struct hiccl_comm {
   unsigned long long timeout_ns = 1000000000ull;
   int ctas_per_sm = 2;
   int threads = 256;
-  unsigned long long item_bytes = 65536;
+  unsigned long long item_bytes = 49152;   // set per payload at creation
   int order = 1;
   unsigned long long slot_items = 768;
   int trace = 0;

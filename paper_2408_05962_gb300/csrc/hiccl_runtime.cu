@@ -1334,7 +1334,7 @@ hiccl_status_t hiccl_autotune(hiccl_comm_t c, void *stream, int flags, hiccl_tun
   }
   const hiccl_tune_t base = top;
   for (int order : {1, 0})
-    for (unsigned long long ib : {32768ull, 65536ull, 131072ull}) {
+    for (unsigned long long ib : {32768ull, 49152ull, 65536ull, 131072ull}) {
       hiccl_tune_t k = base;
       k.order = order;
       k.item_bytes = ib;
