@@ -423,6 +423,9 @@ __device__ __forceinline__ void warp_reduce(const unsigned long long *ptrs, uint
   }
 }
 
+// Build-time settings: HICCL_NBUF work items staged ahead of the data warps
+// per CTA (3 keeps two 256-thread CTAs per SM within shared memory);
+// HICCL_PDL 1 lets executor launches use programmatic dependent launch.
 #ifndef HICCL_NBUF
 #define HICCL_NBUF 3
 #endif
@@ -431,7 +434,6 @@ __device__ __forceinline__ void warp_reduce(const unsigned long long *ptrs, uint
 #endif
 constexpr int NBUF = HICCL_NBUF;   // work items staged ahead of the data warps
 
-// one staged work item: its entries, their steps' descriptors and pointers
 // A staged work item: the sections of its record at fixed offsets (each
 // filled by one bulk copy), then the control fields.
 struct __align__(16) ItemBuf {
