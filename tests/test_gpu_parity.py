@@ -149,3 +149,17 @@ def test_ring(name, dtype, P, h, ring, s, m, d):
     S.run_program(prog, ref, h, ring)
     outs, _ = run_on_gpu(prog, h, s, m, mem0, options={H.OPT_RING: ring})
     assert_bit_equal(ref, outs[0])
+
+
+@pytest.mark.parametrize("name", ["allreduce", "reducescatter", "reduce"])
+@pytest.mark.parametrize("P,h,ring,s,m", [(12, [4, 3], 4, 3, 2), (16, [4, 4], 16, 1, 2)])
+def test_ring_fp8(name, P, h, ring, s, m):
+    """The ring order with block-scaled FP8 payloads: every chain step
+    re-quantizes the partial (a fresh block scale per level, as the tree)."""
+    from paper_2408_05962_gb300 import hiccl as H
+    prog = PR.BUILDERS[name](P, 3, dtype="fp8")
+    mem0 = fill(prog, P + ring)
+    ref = {k: v.copy() for k, v in mem0.items()}
+    S.run_program(prog, ref, h, ring)
+    outs, _ = run_on_gpu(prog, h, s, m, mem0, options={H.OPT_RING: ring})
+    assert_bit_equal(ref, outs[0])

@@ -299,3 +299,9 @@ def test_every_plan_passes_the_check(name):
         comm = register(prog, FakeAddresses(prog).addr)
         comm.plan(h, s, m)
         comm.validate()
+
+
+@pytest.mark.parametrize("name", ["allreduce", "reducescatter", "reduce", "allgather"])
+@pytest.mark.parametrize("P,h,ring,s,m", [(12, [4, 3], 4, 3, 2), (16, [4, 4], 16, 1, 2), (12, [2, 2, 3], 2, 3, 1)])
+def test_ring_fp8_collectives(name, P, h, ring, s, m):
+    _check(PR.BUILDERS[name](P, 3, dtype="fp8"), h, s, m, seed=P + ring, ring=ring)
