@@ -130,8 +130,8 @@ hiccl_status_t hiccl_add_collective(hiccl_comm_t comm, hiccl_collective_t kind, 
 
 /* ---- optimization (Sec. 4) -------------------------------------------------- */
 
-/* Factorize the registered program and upload it to the current device
- * (Sec. 4, Sec. 5.2 "memoizing").
+/* Factorize the registered program, check the plan (hiccl_validate) and
+ * upload it to the current device (Sec. 4, Sec. 5.2 "memoizing").
  *   hierarchy : nlevels (>= 1) factors >= 1, top level first, whose product
  *               is nranks; ranks of a level-l group are contiguous (Sec. 4.2).
  *   stripe    : s in [1, nranks], branches per primitive (Sec. 4.3).
@@ -154,7 +154,11 @@ hiccl_status_t hiccl_plan(hiccl_comm_t comm, const int *hierarchy, int nlevels,
 /* Enqueue one execution of the collective on `cuda_stream` (a cudaStream_t,
  * NULL for the legacy default stream) and return without waiting (the
  * paper's non-blocking start).  HICCL_ERR_STATE before hiccl_init or while a
- * previous start has not been waited on. */
+ * previous start has not been waited on.  Stream order is kept: the launch
+ * may become resident while the previous kernel of the stream drains
+ * (programmatic dependent launch) but touches no memory before that kernel
+ * has completed.  Under CUDA-graph capture only the launch is recorded; each
+ * replay is a complete execution. */
 hiccl_status_t hiccl_start(hiccl_comm_t comm, void *cuda_stream);
 
 /* Block until the last start has finished and its buffers may be reused
