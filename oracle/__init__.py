@@ -10,14 +10,16 @@ the product package; the two share only the seeded input generators in
 Contents (each function cites the passage of the paper it restates):
 
 * ``hierarchy``  -- group arithmetic of the hierarchy vector (Sec. 4.2).
-* ``semantics``  -- primitive semantics (Sec. 3.1), the collective definitions
-  of Table 2, the hierarchical fixed-order sum, FP64 reference sums, a race
-  check (Sec. 3.2).
+* ``semantics``  -- primitive semantics (Sec. 3.1) with the sum, max, min and
+  logical-or operators, the collective definitions of Table 2, the
+  hierarchical fixed-order fold and its ring order (Sec. 4.4), FP64 reference
+  sums, a race check (Sec. 3.2).
 * ``programs``   -- the collectives of Table 2 (single and multiple steps) and
   the All-reduce program of Listing 2, composed from primitives.
-* ``factorize``  -- the optimizer of Sec. 4: striping (4.3), tree (4.2) and
-  pipelining (4.5), emitting point-to-point copy / reduce operations with
-  their levels and dependencies, plus per-level and HBM byte accounting.
+* ``factorize``  -- the optimizer of Sec. 4: striping (4.3), ring (4.4), tree
+  (4.2) and pipelining (4.5), emitting point-to-point copy / reduce
+  operations with their levels and dependencies, plus per-level and HBM
+  byte accounting.
 * ``simulate``   -- executes a factorized plan on NumPy buffers.
 * ``lowprec``    -- BF16 rounding and FP8-e4m3 block-scaled encoding used for
   the reduced-precision payloads.
