@@ -264,7 +264,7 @@ __device__ __forceinline__ void fp8_fold_block(BLK blk, char *out, uint32_t f, u
         acc[4 * j + 3] = __fmul_rn(v.w, sc);
       }
     }
-#pragma unroll 1
+#pragma unroll 2
     for (uint32_t q = 1; q < f; ++q) {
       const char *b = blk(q);
       const uint4 c = *reinterpret_cast<const uint4 *>(b + 16 * sub);
