@@ -206,6 +206,7 @@ __device__ __forceinline__ uint4 fold16_bf16(LD ld, uint32_t f, COMB comb) {
     a[2 * i] = __uint_as_float(w0[i] << 16);
     a[2 * i + 1] = __uint_as_float(w0[i] & 0xffff0000u);
   }
+#pragma unroll 2
   for (uint32_t q = 1; q < f; ++q) {
     const uint4 u = ld(q);
     const uint32_t w[4] = {u.x, u.y, u.z, u.w};
@@ -226,10 +227,12 @@ template <typename LD>
 __device__ __forceinline__ uint4 fold16(LD ld, uint32_t f, uint32_t dt, uint32_t rop = 0) {
   if (dt != HICCL_BF16) {
     uint4 v = ld(0);
-    if (rop == HICCL_SUM && dt == HICCL_F32)
+    if (rop == HICCL_SUM && dt == HICCL_F32) {
+#pragma unroll 4
       for (uint32_t q = 1; q < f; ++q) v = add4(v, ld(q), HICCL_F32, HICCL_SUM);
-    else
+    } else {
       for (uint32_t q = 1; q < f; ++q) v = add4(v, ld(q), dt, rop);
+    }
     return v;
   }
   if (rop == HICCL_SUM) return fold16_bf16(ld, f, CombSum{});
