@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <new>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -136,6 +137,33 @@ struct Builder {
     }
   }
 
+  // Reserve the step, operand and edge arrays once: at the largest plans
+  // (millions of steps, hundreds of millions of operands) growing them by
+  // doubling costs more than the tree walks.  A piece of a primitive with n
+  // leaves takes at most min(n, number of tree nodes) steps, and its operands
+  // are about one per leaf plus two per step.  The estimate only sizes the
+  // first allocation; a larger plan grows as usual, and a failed reservation
+  // is ignored.
+  void reserve_for(const std::vector<Prim> &prims) {
+    unsigned long long nodes = 0;   // tree nodes of a full leaf set: sum over levels of P / G[l]
+    for (int l = 0; l < L; ++l) nodes += (unsigned long long)(c.P / G[l]);
+    unsigned long long ns = 0, nl = 0;
+    for (const Prim &pr : prims) {
+      if (!pr.count) continue;
+      const unsigned long long n = pr.leaves.size(), pieces = (unsigned long long)s * (unsigned long long)m;
+      const unsigned long long st = std::min<unsigned long long>(n, nodes) + 2;
+      ns += pieces * st;
+      nl += pieces * (n + 2 * st + 4);
+    }
+    if (ns > 0xFFFFFFF0ull || nl > (1ull << 34)) return;   // far beyond what can be planned
+    try {
+      steps.reserve(ns);
+      locs.reserve(nl);
+      edges.reserve(ns);
+    } catch (const std::bad_alloc &) {
+    }
+  }
+
   int level_of(int a, int b) const {
     if (a == b) return -1;
     if (!grp.empty()) {
@@ -220,18 +248,29 @@ struct Builder {
   Loc recv_loc(int r) const { return Loc{p->recv[r] + cur_off, r, 0}; }
   static bool same(const Loc &a, const Loc &b) { return a.addr == b.addr && a.scratch == b.scratch; }
 
-  // the leaves of span `sp` inside ranks [lo, hi)
+  // the leaves of span `sp` inside ranks [lo, hi); a span of consecutive
+  // ranks (a full leaf set) is cut by arithmetic instead of searching
   static Span inside(const Span &sp, long long lo, long long hi) {
+    const long long n = sp.e - sp.b;
+    if (n > 0 && (long long)sp.e[-1] - sp.b[0] == n - 1) {
+      const long long a = std::min(std::max(lo - sp.b[0], 0ll), n), z = std::min(std::max(hi - sp.b[0], a), n);
+      return Span{sp.b + a, sp.b + z, sp.skip};
+    }
     const int *a = std::lower_bound(sp.b, sp.e, (int)lo);
     const int *b = std::lower_bound(a, sp.e, (int)hi);
     return Span{a, b, sp.skip};
+  }
+  static bool holds(const Span &sp, long long r) {   // r is a rank of the span
+    const long long n = sp.e - sp.b;
+    if (n > 0 && (long long)sp.e[-1] - sp.b[0] == n - 1) return r >= sp.b[0] && r <= sp.e[-1];
+    return std::binary_search(sp.b, sp.e, (int)r);
   }
   static Span span_of(const std::vector<int> &v) { return Span{v.data(), v.data() + v.size(), -1}; }
   // the representative of subgroup [qbase, qbase + sub) for `holder`: the rank
   // at the holder's offset if it is a leaf, else the lowest leaf
   static int pick_rep(long long qbase, long long sub, int holder, const Span &ql) {
     int cand = (int)(qbase + holder % sub);
-    if (cand != ql.skip && std::binary_search(ql.b, ql.e, cand)) return cand;
+    if (cand != ql.skip && holds(ql, cand)) return cand;
     return *ql.b != ql.skip ? *ql.b : ql.b[1];
   }
 
@@ -258,6 +297,12 @@ struct Builder {
     const long long sub = G[l + 1];
     Scratch &S = scr[l];
     S.clear();
+    if (sub == 1) {   // bottom level: every other leaf represents its own one-rank subgroup
+      for (const int *i = leaves.b; i < leaves.e; ++i)
+        if (*i != holder && *i != leaves.skip) S.locs.push_back(recv_loc(*i));
+      if (!S.locs.empty()) emit(OP_COPY, &src, 1, S.locs.data(), (uint32_t)S.locs.size(), l, &src_step, 1);
+      return;
+    }
     Span own{nullptr, nullptr, leaves.skip};
     long long own_base = -1;
     for (const int *i = leaves.b; i < leaves.e;) {
@@ -297,6 +342,17 @@ struct Builder {
     const long long sub = G[l + 1];
     Scratch &S = scr[l];
     S.clear();
+    if (sub == 1) {   // bottom level: fold the leaves' own buffers in rank order
+      if (leaves.e - leaves.b == 1 && *leaves.b == target) return red_tree(L, target, target, leaves, out);
+      for (const int *i = leaves.b; i < leaves.e; ++i) {
+        S.locs.push_back(send_loc(*i));
+        S.prods.push_back(-1);
+      }
+      const size_t np = S.locs.size();
+      Loc o = out ? *out : scratch_loc(target);
+      int st = emit(np > 1 ? OP_REDUCE : OP_COPY, S.locs.data(), (uint32_t)np, &o, 1, l, S.prods.data(), (uint32_t)np);
+      return {o, st};
+    }
     for (const int *i = leaves.b; i < leaves.e;) {
       const long long qb = base + (*i - base) / sub * sub;
       const Span q = inside(Span{i, leaves.e, -1}, qb, qb + sub);
@@ -870,6 +926,7 @@ static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevel
   Builder B(*c, h, stripe, pipeline);
   B.ring = c->ring;
   B.lr = ring_lvl;
+  B.reserve_for(c->prims);
   std::vector<uint32_t> epoch_first(c->epochs + 1, 0);
   int e_seen = 0;
   for (size_t i = 0; i < c->prims.size(); ++i) {
@@ -892,23 +949,8 @@ static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevel
     if (st.nsrc > MAX_FANIN || st.ndst > MAX_FANIN)
       return fail(c, HICCL_ERR_UNSUPPORTED, "a step has more than 1024 inputs or outputs");
 
-  // bounds: every user location lies in its primitive's registered range
-  for (const HStep &st : B.steps) {
-    const Prim &p = c->prims[st.prim];
-    unsigned long long n = (unsigned long long)p.count * c->esize;
-    for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k) {
-      const Loc &l = B.locs[st.loc0 + k];
-      bool ok;
-      if (l.scratch) {
-        ok = l.addr + st.nbytes <= B.scratch_top;
-      } else {
-        unsigned long long base_s = p.send[l.rank], base_r = p.recv[l.rank];
-        ok = (base_s && l.addr >= base_s && l.addr + st.nbytes <= base_s + n) ||
-             (base_r && l.addr >= base_r && l.addr + st.nbytes <= base_r + n);
-      }
-      if (!ok) return fail(c, HICCL_ERR_INVALID, "internal: step outside its primitive's buffers");
-    }
-  }
+  // (every operand lying in its primitive's buffers or in the relay arena is
+  // checked with the rest of the plan at the end)
 
   // predecessor lists in emission order (every edge points backwards)
   std::vector<uint32_t> pcount(N + 1, 0);
@@ -962,16 +1004,46 @@ static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevel
   std::vector<uint32_t> order(N);
   std::iota(order.begin(), order.end(), 0u);
   // (inside a slot: primitive, branch, tree position, channel -- so the same
-  // step of adjacent channels is adjacent and can move as one range)
-  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
-    if (slot[a] != slot[b]) return slot[a] < slot[b];
-    if (klass[a] != klass[b]) return klass[a] < klass[b];
-    const HStep &x = B.steps[a], &y = B.steps[b];
-    if (x.prim != y.prim) return x.prim < y.prim;
-    if (x.branch != y.branch) return x.branch < y.branch;
-    if (x.local != y.local) return x.local < y.local;
-    return x.channel < y.channel;
-  });
+  // step of adjacent channels is adjacent and can move as one range).  The
+  // key identifies a step, so no two compare equal; it is packed into two
+  // words when every field fits its bits, else compared field by field.
+  {
+    unsigned long long mprim = 0, mbranch = 0, mlocal = 0, mchan = 0;
+    for (const HStep &st : B.steps) {
+      mprim = std::max<unsigned long long>(mprim, (unsigned)st.prim);
+      mbranch = std::max<unsigned long long>(mbranch, (unsigned)st.branch);
+      mlocal = std::max<unsigned long long>(mlocal, st.local);
+      mchan = std::max<unsigned long long>(mchan, (unsigned)st.channel);
+    }
+    if (maxslot < (1ull << 30) && mprim < (1ull << 32) && mbranch < (1ull << 30) && mlocal < (1ull << 18) &&
+        mchan < (1ull << 16)) {
+      struct Key {
+        unsigned long long hi, lo;
+        uint32_t idx;
+      };
+      std::vector<Key> keys(N);
+      for (size_t i = 0; i < N; ++i) {
+        const HStep &st = B.steps[i];
+        keys[i] = Key{(slot[i] << 34) | ((unsigned long long)klass[i] << 32) | (unsigned)st.prim,
+                      ((unsigned long long)(unsigned)st.branch << 34) | ((unsigned long long)st.local << 16) |
+                          (unsigned)st.channel,
+                      (uint32_t)i};
+      }
+      std::sort(keys.begin(), keys.end(),
+                [](const Key &a, const Key &b) { return a.hi != b.hi ? a.hi < b.hi : a.lo < b.lo; });
+      for (size_t k = 0; k < N; ++k) order[k] = keys[k].idx;
+    } else {
+      std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+        if (slot[a] != slot[b]) return slot[a] < slot[b];
+        if (klass[a] != klass[b]) return klass[a] < klass[b];
+        const HStep &x = B.steps[a], &y = B.steps[b];
+        if (x.prim != y.prim) return x.prim < y.prim;
+        if (x.branch != y.branch) return x.branch < y.branch;
+        if (x.local != y.local) return x.local < y.local;
+        return x.channel < y.channel;
+      });
+    }
+  }
   std::vector<uint32_t> pos(N);
   for (size_t k = 0; k < N; ++k) pos[order[k]] = (uint32_t)k;
 
@@ -980,16 +1052,12 @@ static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevel
   plan.stripe = stripe;
   plan.pipeline = pipeline;
   plan.steps.resize(N);
-  plan.locs.reserve(B.locs.size());
   for (size_t k = 0; k < N; ++k) {
-    HStep st = B.steps[order[k]];
-    uint32_t n = st.nsrc + st.ndst;
-    uint32_t old0 = st.loc0;
-    st.loc0 = (uint32_t)plan.locs.size();
-    st.slot = slot[order[k]];
-    plan.locs.insert(plan.locs.end(), B.locs.begin() + old0, B.locs.begin() + old0 + n);
-    plan.steps[k] = st;
+    plan.steps[k] = B.steps[order[k]];
+    plan.steps[k].slot = slot[order[k]];
   }
+  // operands stay in emission order: a step names its own with loc0
+  plan.locs = std::move(B.locs);
   // predecessor and successor CSR in the new numbering
   plan.pred_off.assign(N + 1, 0);
   plan.succ_off.assign(N + 1, 0);
