@@ -11,7 +11,8 @@
  * measured on links.
  *
  * Conventions for every function below:
- *   - A status is returned; nothing aborts.  On failure the communicator's
+ *   - A status is returned; nothing aborts or throws (host memory running
+ *     out inside a call is HICCL_ERR_NOMEM).  On failure the communicator's
  *     state is unchanged and hiccl_last_error() holds a message.
  *   - "device pointer" means a pointer into memory of the current CUDA
  *     device (cudaMalloc / PyTorch allocations); host pointers there are a

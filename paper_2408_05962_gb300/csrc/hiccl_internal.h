@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -232,6 +233,28 @@ struct hiccl_comm {
 
 namespace hiccl {
 hiccl_status_t fail(hiccl_comm *c, hiccl_status_t st, const std::string &msg);
+// Run the body of a C-ABI call so that no C++ exception leaves it: host
+// memory exhaustion becomes HICCL_ERR_NOMEM, anything else HICCL_ERR_INVALID,
+// with the message on `c` where there is one.
+template <typename F>
+hiccl_status_t guarded(hiccl_comm *c, F &&body) noexcept {
+  hiccl_status_t st;
+  const char *msg;
+  try {
+    return body();
+  } catch (const std::bad_alloc &) {
+    st = HICCL_ERR_NOMEM;
+    msg = "out of host memory";
+  } catch (...) {
+    st = HICCL_ERR_INVALID;
+    msg = "internal error";
+  }
+  try {
+    return fail(c, st, msg);
+  } catch (...) {
+    return st;
+  }
+}
 // factorize c's program again (hiccl_plan.cpp), keeping c's state
 hiccl_status_t replan(hiccl_comm *c, const std::vector<int> &hierarchy, int stripe, int pipeline);
 // runtime entry points (hiccl_runtime.cu)

@@ -1211,19 +1211,21 @@ hiccl_status_t replan(hiccl_comm *c, const std::vector<int> &hierarchy, int stri
 extern "C" {
 
 hiccl_status_t hiccl_create(int nranks, hiccl_dtype_t dtype, hiccl_comm_t *out) {
-  if (!out) return HICCL_ERR_INVALID;
-  *out = nullptr;
-  if (nranks < 1 || nranks > (1 << 30)) return HICCL_ERR_INVALID;
-  if (esize_of(dtype) == 0) return HICCL_ERR_INVALID;
-  hiccl_comm *c = new (std::nothrow) hiccl_comm();
-  if (!c) return HICCL_ERR_NOMEM;
-  c->P = nranks;
-  c->dtype = dtype;
-  c->esize = esize_of(dtype);
-  // measured on the executor: FP8 folds prefer larger items
-  c->item_bytes = dtype == HICCL_FP8E4M3 ? 65536 : 49152;
-  *out = c;
-  return HICCL_OK;
+  return guarded(nullptr, [&]() -> hiccl_status_t {
+    if (!out) return HICCL_ERR_INVALID;
+    *out = nullptr;
+    if (nranks < 1 || nranks > (1 << 30)) return HICCL_ERR_INVALID;
+    if (esize_of(dtype) == 0) return HICCL_ERR_INVALID;
+    hiccl_comm *c = new (std::nothrow) hiccl_comm();
+    if (!c) return HICCL_ERR_NOMEM;
+    c->P = nranks;
+    c->dtype = dtype;
+    c->esize = esize_of(dtype);
+    // measured on the executor: FP8 folds prefer larger items
+    c->item_bytes = dtype == HICCL_FP8E4M3 ? 65536 : 49152;
+    *out = c;
+    return HICCL_OK;
+  });
 }
 
 static hiccl_status_t check_leaves(hiccl_comm *c, const int *leaves, int nleaves, std::vector<int> &out,
@@ -1247,465 +1249,493 @@ static bool aligned_elem(const hiccl_comm *c, unsigned long long a) {
 
 hiccl_status_t hiccl_add_multicast(hiccl_comm_t c, const void *const *send, void *const *recv,
                                    size_t count, int root, const int *leaves, int nleaves) {
-  if (!c) return HICCL_ERR_INVALID;
-  if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "add after init");
-  if (!send || !recv) return fail(c, HICCL_ERR_INVALID, "null pointer array");
-  if (root < 0 || root >= c->P) return fail(c, HICCL_ERR_INVALID, "root out of range");
-  Prim p;
-  p.kind = 0;
-  p.root = root;
-  if (!to_units(c, count, p.count)) return fail(c, HICCL_ERR_INVALID, "FP8 counts must be multiples of 128");
-  p.epoch = c->epochs - 1;
-  hiccl_status_t st = check_leaves(c, leaves, nleaves, p.leaves, true);
-  if (st != HICCL_OK) return st;
-  if (p.leaves.empty()) return HICCL_OK;   // nothing to deliver
-  p.send.assign(c->P, 0);
-  p.recv.assign(c->P, 0);
-  p.send[root] = (unsigned long long)(uintptr_t)send[root];
-  for (int j : p.leaves) p.recv[j] = (unsigned long long)(uintptr_t)recv[j];
-  if (count > 0) {
-    if (!p.send[root]) return fail(c, HICCL_ERR_INVALID, "null send buffer at the root");
-    for (int j : p.leaves)
-      if (!p.recv[j]) return fail(c, HICCL_ERR_INVALID, "null recv buffer at a leaf");
-    if (!aligned_elem(c, p.send[root])) return fail(c, HICCL_ERR_INVALID, "misaligned send buffer");
-    for (int j : p.leaves)
-      if (!aligned_elem(c, p.recv[j])) return fail(c, HICCL_ERR_INVALID, "misaligned recv buffer");
-    if ((unsigned long long)p.count > (~0ull) / 256) return fail(c, HICCL_ERR_INVALID, "count too large");
-  }
-  c->prims.push_back(std::move(p));
-  return HICCL_OK;
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c) return HICCL_ERR_INVALID;
+    if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "add after init");
+    if (!send || !recv) return fail(c, HICCL_ERR_INVALID, "null pointer array");
+    if (root < 0 || root >= c->P) return fail(c, HICCL_ERR_INVALID, "root out of range");
+    Prim p;
+    p.kind = 0;
+    p.root = root;
+    if (!to_units(c, count, p.count)) return fail(c, HICCL_ERR_INVALID, "FP8 counts must be multiples of 128");
+    p.epoch = c->epochs - 1;
+    hiccl_status_t st = check_leaves(c, leaves, nleaves, p.leaves, true);
+    if (st != HICCL_OK) return st;
+    if (p.leaves.empty()) return HICCL_OK;   // nothing to deliver
+    p.send.assign(c->P, 0);
+    p.recv.assign(c->P, 0);
+    p.send[root] = (unsigned long long)(uintptr_t)send[root];
+    for (int j : p.leaves) p.recv[j] = (unsigned long long)(uintptr_t)recv[j];
+    if (count > 0) {
+      if (!p.send[root]) return fail(c, HICCL_ERR_INVALID, "null send buffer at the root");
+      for (int j : p.leaves)
+        if (!p.recv[j]) return fail(c, HICCL_ERR_INVALID, "null recv buffer at a leaf");
+      if (!aligned_elem(c, p.send[root])) return fail(c, HICCL_ERR_INVALID, "misaligned send buffer");
+      for (int j : p.leaves)
+        if (!aligned_elem(c, p.recv[j])) return fail(c, HICCL_ERR_INVALID, "misaligned recv buffer");
+      if ((unsigned long long)p.count > (~0ull) / 256) return fail(c, HICCL_ERR_INVALID, "count too large");
+    }
+    c->prims.push_back(std::move(p));
+    return HICCL_OK;
+  });
 }
 
 hiccl_status_t hiccl_add_reduction(hiccl_comm_t c, const void *const *send, void *const *recv,
                                    size_t count, const int *leaves, int nleaves, int root,
                                    hiccl_op_t op) {
-  if (!c) return HICCL_ERR_INVALID;
-  if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "add after init");
-  if (!send || !recv) return fail(c, HICCL_ERR_INVALID, "null pointer array");
-  if (op != HICCL_SUM && op != HICCL_MAX && op != HICCL_MIN && op != HICCL_LOR)
-    return fail(c, HICCL_ERR_INVALID, "unknown reduction operator");
-  if (op != HICCL_SUM && c->dtype == HICCL_FP8E4M3)
-    return fail(c, HICCL_ERR_UNSUPPORTED, "FP8 payloads reduce with HICCL_SUM only");
-  if (op == HICCL_LOR && c->dtype != HICCL_I32)
-    return fail(c, HICCL_ERR_UNSUPPORTED, "HICCL_LOR needs HICCL_I32 payloads");
-  if (root < 0 || root >= c->P) return fail(c, HICCL_ERR_INVALID, "root out of range");
-  Prim p;
-  p.kind = 1;
-  p.op = (int)op;
-  p.root = root;
-  if (!to_units(c, count, p.count)) return fail(c, HICCL_ERR_INVALID, "FP8 counts must be multiples of 128");
-  p.epoch = c->epochs - 1;
-  hiccl_status_t st = check_leaves(c, leaves, nleaves, p.leaves, false);
-  if (st != HICCL_OK) return st;
-  p.send.assign(c->P, 0);
-  p.recv.assign(c->P, 0);
-  for (int j : p.leaves) p.send[j] = (unsigned long long)(uintptr_t)send[j];
-  p.recv[root] = (unsigned long long)(uintptr_t)recv[root];
-  if (count > 0) {
-    if (!p.recv[root]) return fail(c, HICCL_ERR_INVALID, "null recv buffer at the root");
-    for (int j : p.leaves)
-      if (!p.send[j]) return fail(c, HICCL_ERR_INVALID, "null send buffer at a leaf");
-    if (!aligned_elem(c, p.recv[root])) return fail(c, HICCL_ERR_INVALID, "misaligned recv buffer");
-    for (int j : p.leaves)
-      if (!aligned_elem(c, p.send[j])) return fail(c, HICCL_ERR_INVALID, "misaligned send buffer");
-    if ((unsigned long long)p.count > (~0ull) / 256) return fail(c, HICCL_ERR_INVALID, "count too large");
-  }
-  c->prims.push_back(std::move(p));
-  return HICCL_OK;
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c) return HICCL_ERR_INVALID;
+    if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "add after init");
+    if (!send || !recv) return fail(c, HICCL_ERR_INVALID, "null pointer array");
+    if (op != HICCL_SUM && op != HICCL_MAX && op != HICCL_MIN && op != HICCL_LOR)
+      return fail(c, HICCL_ERR_INVALID, "unknown reduction operator");
+    if (op != HICCL_SUM && c->dtype == HICCL_FP8E4M3)
+      return fail(c, HICCL_ERR_UNSUPPORTED, "FP8 payloads reduce with HICCL_SUM only");
+    if (op == HICCL_LOR && c->dtype != HICCL_I32)
+      return fail(c, HICCL_ERR_UNSUPPORTED, "HICCL_LOR needs HICCL_I32 payloads");
+    if (root < 0 || root >= c->P) return fail(c, HICCL_ERR_INVALID, "root out of range");
+    Prim p;
+    p.kind = 1;
+    p.op = (int)op;
+    p.root = root;
+    if (!to_units(c, count, p.count)) return fail(c, HICCL_ERR_INVALID, "FP8 counts must be multiples of 128");
+    p.epoch = c->epochs - 1;
+    hiccl_status_t st = check_leaves(c, leaves, nleaves, p.leaves, false);
+    if (st != HICCL_OK) return st;
+    p.send.assign(c->P, 0);
+    p.recv.assign(c->P, 0);
+    for (int j : p.leaves) p.send[j] = (unsigned long long)(uintptr_t)send[j];
+    p.recv[root] = (unsigned long long)(uintptr_t)recv[root];
+    if (count > 0) {
+      if (!p.recv[root]) return fail(c, HICCL_ERR_INVALID, "null recv buffer at the root");
+      for (int j : p.leaves)
+        if (!p.send[j]) return fail(c, HICCL_ERR_INVALID, "null send buffer at a leaf");
+      if (!aligned_elem(c, p.recv[root])) return fail(c, HICCL_ERR_INVALID, "misaligned recv buffer");
+      for (int j : p.leaves)
+        if (!aligned_elem(c, p.send[j])) return fail(c, HICCL_ERR_INVALID, "misaligned send buffer");
+      if ((unsigned long long)p.count > (~0ull) / 256) return fail(c, HICCL_ERR_INVALID, "count too large");
+    }
+    c->prims.push_back(std::move(p));
+    return HICCL_OK;
+  });
 }
 
 hiccl_status_t hiccl_add_fence(hiccl_comm_t c) {
-  if (!c) return HICCL_ERR_INVALID;
-  if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "add after init");
-  c->epochs++;
-  return HICCL_OK;
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c) return HICCL_ERR_INVALID;
+    if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "add after init");
+    c->epochs++;
+    return HICCL_OK;
+  });
 }
 
 hiccl_status_t hiccl_add_collective(hiccl_comm_t c, hiccl_collective_t kind, size_t d, const void *const *send,
                                     void *const *recv, int root, hiccl_op_t op) {
-  if (!c) return HICCL_ERR_INVALID;
-  if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "add after init");
-  if (!send || !recv) return fail(c, HICCL_ERR_INVALID, "null pointer array");
-  const int P = c->P;
-  if (root < 0 || root >= P) return fail(c, HICCL_ERR_INVALID, "root out of range");
-  size_t du = 0;
-  if (!to_units(c, d, du)) return fail(c, HICCL_ERR_INVALID, "FP8 counts must be multiples of 128");
-  const unsigned long long cb = (unsigned long long)du * c->esize;   // bytes of one chunk
-  std::vector<int> all(P), others;
-  for (int r = 0; r < P; ++r) all[r] = r;
-  std::vector<const void *> s(P, nullptr);
-  std::vector<void *> v(P, nullptr);
-  auto sa = [&](int r, unsigned long long k) { return (const void *)((const char *)send[r] + k * cb); };
-  auto ra = [&](int r, unsigned long long k) { return (void *)((char *)recv[r] + k * cb); };
-  auto reset = [&]() {
-    std::fill(s.begin(), s.end(), nullptr);
-    std::fill(v.begin(), v.end(), nullptr);
-  };
-  hiccl_status_t st = HICCL_OK;
-  const size_t dp = d * P;
-  switch (kind) {
-    case HICCL_BROADCAST:
-      return hiccl_add_multicast(c, send, recv, dp, root, all.data(), P);
-    case HICCL_REDUCE:
-      return hiccl_add_reduction(c, send, recv, dp, all.data(), P, root, op);
-    case HICCL_ALLGATHER:
-      for (int i = 0; i < P && st == HICCL_OK; ++i) {
-        for (int r = 0; r < P; ++r) v[r] = ra(r, i);
-        st = hiccl_add_multicast(c, send, v.data(), d, i, all.data(), P);
-      }
-      return st;
-    case HICCL_REDUCESCATTER:
-      for (int j = 0; j < P && st == HICCL_OK; ++j) {
-        for (int r = 0; r < P; ++r) s[r] = sa(r, j);
-        st = hiccl_add_reduction(c, s.data(), recv, d, all.data(), P, j, op);
-      }
-      return st;
-    case HICCL_ALLREDUCE_SINGLE:
-      for (int j = 0; j < P && st == HICCL_OK; ++j)
-        st = hiccl_add_reduction(c, send, recv, dp, all.data(), P, j, op);
-      return st;
-    case HICCL_SCATTER:
-      for (int j = 0; j < P && st == HICCL_OK; ++j) {
-        reset();
-        s[root] = sa(root, j);
-        v[j] = recv[j];
-        st = hiccl_add_reduction(c, s.data(), v.data(), d, &root, 1, j, HICCL_SUM);
-      }
-      return st;
-    case HICCL_GATHER:
-      for (int i = 0; i < P && st == HICCL_OK; ++i) {
-        reset();
-        s[i] = send[i];
-        v[root] = ra(root, i);
-        st = hiccl_add_multicast(c, s.data(), v.data(), d, i, &root, 1);
-      }
-      return st;
-    case HICCL_ALLTOALL:
-      for (int i = 0; i < P && st == HICCL_OK; ++i)
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c) return HICCL_ERR_INVALID;
+    if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "add after init");
+    if (!send || !recv) return fail(c, HICCL_ERR_INVALID, "null pointer array");
+    const int P = c->P;
+    if (root < 0 || root >= P) return fail(c, HICCL_ERR_INVALID, "root out of range");
+    size_t du = 0;
+    if (!to_units(c, d, du)) return fail(c, HICCL_ERR_INVALID, "FP8 counts must be multiples of 128");
+    const unsigned long long cb = (unsigned long long)du * c->esize;   // bytes of one chunk
+    std::vector<int> all(P), others;
+    for (int r = 0; r < P; ++r) all[r] = r;
+    std::vector<const void *> s(P, nullptr);
+    std::vector<void *> v(P, nullptr);
+    auto sa = [&](int r, unsigned long long k) { return (const void *)((const char *)send[r] + k * cb); };
+    auto ra = [&](int r, unsigned long long k) { return (void *)((char *)recv[r] + k * cb); };
+    auto reset = [&]() {
+      std::fill(s.begin(), s.end(), nullptr);
+      std::fill(v.begin(), v.end(), nullptr);
+    };
+    hiccl_status_t st = HICCL_OK;
+    const size_t dp = d * P;
+    switch (kind) {
+      case HICCL_BROADCAST:
+        return hiccl_add_multicast(c, send, recv, dp, root, all.data(), P);
+      case HICCL_REDUCE:
+        return hiccl_add_reduction(c, send, recv, dp, all.data(), P, root, op);
+      case HICCL_ALLGATHER:
+        for (int i = 0; i < P && st == HICCL_OK; ++i) {
+          for (int r = 0; r < P; ++r) v[r] = ra(r, i);
+          st = hiccl_add_multicast(c, send, v.data(), d, i, all.data(), P);
+        }
+        return st;
+      case HICCL_REDUCESCATTER:
+        for (int j = 0; j < P && st == HICCL_OK; ++j) {
+          for (int r = 0; r < P; ++r) s[r] = sa(r, j);
+          st = hiccl_add_reduction(c, s.data(), recv, d, all.data(), P, j, op);
+        }
+        return st;
+      case HICCL_ALLREDUCE_SINGLE:
+        for (int j = 0; j < P && st == HICCL_OK; ++j)
+          st = hiccl_add_reduction(c, send, recv, dp, all.data(), P, j, op);
+        return st;
+      case HICCL_SCATTER:
         for (int j = 0; j < P && st == HICCL_OK; ++j) {
           reset();
-          s[i] = sa(i, j);
-          v[j] = ra(j, i);
-          st = hiccl_add_multicast(c, s.data(), v.data(), d, i, &j, 1);
+          s[root] = sa(root, j);
+          v[j] = recv[j];
+          st = hiccl_add_reduction(c, s.data(), v.data(), d, &root, 1, j, HICCL_SUM);
         }
-      return st;
-    case HICCL_ALLREDUCE:
-      for (int j = 0; j < P && st == HICCL_OK; ++j) {
-        reset();
-        for (int r = 0; r < P; ++r) s[r] = sa(r, j);
-        v[j] = ra(j, j);
-        st = hiccl_add_reduction(c, s.data(), v.data(), d, all.data(), P, j, op);
-      }
-      if (st == HICCL_OK) st = hiccl_add_fence(c);
-      for (int i = 0; i < P && st == HICCL_OK; ++i) {
-        others.clear();
-        for (int r = 0; r < P; ++r)
-          if (r != i) others.push_back(r);
-        for (int r = 0; r < P; ++r) {
-          s[r] = ra(r, i);
-          v[r] = ra(r, i);
+        return st;
+      case HICCL_GATHER:
+        for (int i = 0; i < P && st == HICCL_OK; ++i) {
+          reset();
+          s[i] = send[i];
+          v[root] = ra(root, i);
+          st = hiccl_add_multicast(c, s.data(), v.data(), d, i, &root, 1);
         }
-        st = hiccl_add_multicast(c, s.data(), v.data(), d, i, others.data(), (int)others.size());
-      }
-      return st;
-  }
-  return fail(c, HICCL_ERR_INVALID, "unknown collective");
+        return st;
+      case HICCL_ALLTOALL:
+        for (int i = 0; i < P && st == HICCL_OK; ++i)
+          for (int j = 0; j < P && st == HICCL_OK; ++j) {
+            reset();
+            s[i] = sa(i, j);
+            v[j] = ra(j, i);
+            st = hiccl_add_multicast(c, s.data(), v.data(), d, i, &j, 1);
+          }
+        return st;
+      case HICCL_ALLREDUCE:
+        for (int j = 0; j < P && st == HICCL_OK; ++j) {
+          reset();
+          for (int r = 0; r < P; ++r) s[r] = sa(r, j);
+          v[j] = ra(j, j);
+          st = hiccl_add_reduction(c, s.data(), v.data(), d, all.data(), P, j, op);
+        }
+        if (st == HICCL_OK) st = hiccl_add_fence(c);
+        for (int i = 0; i < P && st == HICCL_OK; ++i) {
+          others.clear();
+          for (int r = 0; r < P; ++r)
+            if (r != i) others.push_back(r);
+          for (int r = 0; r < P; ++r) {
+            s[r] = ra(r, i);
+            v[r] = ra(r, i);
+          }
+          st = hiccl_add_multicast(c, s.data(), v.data(), d, i, others.data(), (int)others.size());
+        }
+        return st;
+    }
+    return fail(c, HICCL_ERR_INVALID, "unknown collective");
+  });
 }
 
 hiccl_status_t hiccl_plan(hiccl_comm_t c, const int *hierarchy, int nlevels, int stripe, int pipeline) {
-  if (!c) return HICCL_ERR_INVALID;
-  if (c->state == hiccl_comm::READY || c->state == hiccl_comm::RUNNING)
-    return fail(c, HICCL_ERR_STATE, "already initialized");
-  hiccl_status_t st = build_plan(c, hierarchy, nlevels, stripe, pipeline);
-  if (st == HICCL_OK) c->state = hiccl_comm::PLANNED;
-  return st;
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c) return HICCL_ERR_INVALID;
+    if (c->state == hiccl_comm::READY || c->state == hiccl_comm::RUNNING)
+      return fail(c, HICCL_ERR_STATE, "already initialized");
+    hiccl_status_t st = build_plan(c, hierarchy, nlevels, stripe, pipeline);
+    if (st == HICCL_OK) c->state = hiccl_comm::PLANNED;
+    return st;
+  });
 }
 
 hiccl_status_t hiccl_init(hiccl_comm_t c, const int *hierarchy, int nlevels, int stripe, int pipeline) {
-  if (!c) return HICCL_ERR_INVALID;
-  if (c->state == hiccl_comm::READY || c->state == hiccl_comm::RUNNING)
-    return fail(c, HICCL_ERR_STATE, "already initialized");
-  hiccl_status_t st = build_plan(c, hierarchy, nlevels, stripe, pipeline);
-  if (st != HICCL_OK) return st;
-  c->state = hiccl_comm::PLANNED;
-  st = dev_upload(c);
-  if (st != HICCL_OK) return st;
-  c->state = hiccl_comm::READY;
-  return HICCL_OK;
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c) return HICCL_ERR_INVALID;
+    if (c->state == hiccl_comm::READY || c->state == hiccl_comm::RUNNING)
+      return fail(c, HICCL_ERR_STATE, "already initialized");
+    hiccl_status_t st = build_plan(c, hierarchy, nlevels, stripe, pipeline);
+    if (st != HICCL_OK) return st;
+    c->state = hiccl_comm::PLANNED;
+    st = dev_upload(c);
+    if (st != HICCL_OK) return st;
+    c->state = hiccl_comm::READY;
+    return HICCL_OK;
+  });
 }
 
 hiccl_status_t hiccl_group(const hiccl_comm_t *comms, int n, hiccl_comm_t *out) {
-  if (!out) return HICCL_ERR_INVALID;
-  *out = nullptr;
-  if (!comms || n < 1) return HICCL_ERR_INVALID;
-  unsigned long long segb = 0;
-  for (int i = 0; i < n; ++i) {
-    if (!comms[i] || !comms[i]->plan.valid) return HICCL_ERR_STATE;
-    if (segb && comms[i]->plan.seg != segb) return HICCL_ERR_UNSUPPORTED;   // FP8 with other payloads
-    segb = comms[i]->plan.seg;
-  }
-  hiccl_comm *g = new (std::nothrow) hiccl_comm();
-  if (!g) return HICCL_ERR_NOMEM;
-  g->group = true;
-  g->P = comms[0]->P;
-  g->dtype = comms[0]->dtype;
-  g->esize = comms[0]->esize;
-  g->timeout_ns = comms[0]->timeout_ns;
-  g->ctas_per_sm = comms[0]->ctas_per_sm;
-  g->threads = comms[0]->threads;
-  Plan &P = g->plan;
-  P.seg = segb;
-  P.pred_off.push_back(0);
-  P.succ_off.push_back(0);
-  // member tables, concatenated; every member's relays move to its own range
-  struct ItemRef { unsigned long long slot; uint32_t rank; int member; uint32_t item; };
-  std::vector<ItemRef> items;
-  std::vector<uint32_t> step_off(n), entry_off(n), run_off(n);
-  unsigned long long relay_off = 0;
-  for (int i = 0; i < n; ++i) {
-    const Plan &q = comms[i]->plan;
-    const uint32_t so = (uint32_t)P.steps.size(), lo = (uint32_t)P.locs.size();
-    step_off[i] = so;
-    entry_off[i] = (uint32_t)P.entries.size();
-    run_off[i] = (uint32_t)P.runs.size();
-    for (HStep st : q.steps) {
-      st.loc0 += lo;
-      P.steps.push_back(st);
+  return guarded(nullptr, [&]() -> hiccl_status_t {
+    if (!out) return HICCL_ERR_INVALID;
+    *out = nullptr;
+    if (!comms || n < 1) return HICCL_ERR_INVALID;
+    unsigned long long segb = 0;
+    for (int i = 0; i < n; ++i) {
+      if (!comms[i] || !comms[i]->plan.valid) return HICCL_ERR_STATE;
+      if (segb && comms[i]->plan.seg != segb) return HICCL_ERR_UNSUPPORTED;   // FP8 with other payloads
+      segb = comms[i]->plan.seg;
     }
-    for (Loc l : q.locs) {
-      if (l.scratch) l.addr += relay_off;
-      P.locs.push_back(l);
+    hiccl_comm *g = new (std::nothrow) hiccl_comm();
+    if (!g) return HICCL_ERR_NOMEM;
+    g->group = true;
+    g->P = comms[0]->P;
+    g->dtype = comms[0]->dtype;
+    g->esize = comms[0]->esize;
+    g->timeout_ns = comms[0]->timeout_ns;
+    g->ctas_per_sm = comms[0]->ctas_per_sm;
+    g->threads = comms[0]->threads;
+    Plan &P = g->plan;
+    P.seg = segb;
+    P.pred_off.push_back(0);
+    P.succ_off.push_back(0);
+    // member tables, concatenated; every member's relays move to its own range
+    struct ItemRef { unsigned long long slot; uint32_t rank; int member; uint32_t item; };
+    std::vector<ItemRef> items;
+    std::vector<uint32_t> step_off(n), entry_off(n), run_off(n);
+    unsigned long long relay_off = 0;
+    for (int i = 0; i < n; ++i) {
+      const Plan &q = comms[i]->plan;
+      const uint32_t so = (uint32_t)P.steps.size(), lo = (uint32_t)P.locs.size();
+      step_off[i] = so;
+      entry_off[i] = (uint32_t)P.entries.size();
+      run_off[i] = (uint32_t)P.runs.size();
+      for (HStep st : q.steps) {
+        st.loc0 += lo;
+        P.steps.push_back(st);
+      }
+      for (Loc l : q.locs) {
+        if (l.scratch) l.addr += relay_off;
+        P.locs.push_back(l);
+      }
+      for (size_t k = 0; k < q.steps.size(); ++k) {
+        for (uint32_t x = q.pred_off[k]; x < q.pred_off[k + 1]; ++x) P.preds.push_back(q.preds[x] + so);
+        P.pred_off.push_back((uint32_t)P.preds.size());
+        for (uint32_t x = q.succ_off[k]; x < q.succ_off[k + 1]; ++x) P.succ.push_back(q.succ[x] + so);
+        P.succ_off.push_back((uint32_t)P.succ.size());
+      }
+      P.nent.insert(P.nent.end(), q.nent.begin(), q.nent.end());
+      for (DevEntry e : q.entries) {
+        e.step += so;
+        P.entries.push_back(e);
+      }
+      P.runs.insert(P.runs.end(), q.runs.begin(), q.runs.end());
+      // rank of each item inside its slot, for interleaving the members
+      unsigned long long prev_slot = ~0ull;
+      uint32_t rank = 0;
+      for (size_t t = 0; t + 1 < q.item_off.size(); ++t) {
+        const unsigned long long sl = q.steps[q.entries[q.item_off[t]].step].slot;
+        rank = sl == prev_slot ? rank + 1 : 0;
+        prev_slot = sl;
+        items.push_back(ItemRef{sl, rank, i, (uint32_t)t});
+      }
+      relay_off = (relay_off + q.scratch_bytes + 255ull) & ~255ull;
+      P.hbm_read += q.hbm_read;
+      P.hbm_write += q.hbm_write;
+      P.stages = std::max(P.stages, q.stages);
+      P.slots = std::max(P.slots, q.slots);
     }
-    for (size_t k = 0; k < q.steps.size(); ++k) {
-      for (uint32_t x = q.pred_off[k]; x < q.pred_off[k + 1]; ++x) P.preds.push_back(q.preds[x] + so);
-      P.pred_off.push_back((uint32_t)P.preds.size());
-      for (uint32_t x = q.succ_off[k]; x < q.succ_off[k + 1]; ++x) P.succ.push_back(q.succ[x] + so);
-      P.succ_off.push_back((uint32_t)P.succ.size());
+    P.scratch_bytes = relay_off;
+    // one ticket order for all: by slot, then round-robin over the members;
+    // each member keeps its own (topological) item order
+    std::stable_sort(items.begin(), items.end(), [](const ItemRef &a, const ItemRef &b) {
+      if (a.slot != b.slot) return a.slot < b.slot;
+      if (a.rank != b.rank) return a.rank < b.rank;
+      return a.member < b.member;
+    });
+    std::vector<DevEntry> ents;
+    std::vector<DevRun> runs;
+    P.item_off.assign(1, 0);
+    P.run_off.assign(1, 0);
+    for (const ItemRef &it : items) {
+      const Plan &q = comms[it.member]->plan;
+      for (uint32_t x = q.item_off[it.item]; x < q.item_off[it.item + 1]; ++x)
+        ents.push_back(P.entries[entry_off[it.member] + x]);
+      for (uint32_t x = q.run_off[it.item]; x < q.run_off[it.item + 1]; ++x) runs.push_back(P.runs[run_off[it.member] + x]);
+      P.item_off.push_back((uint32_t)ents.size());
+      P.run_off.push_back((uint32_t)runs.size());
     }
-    P.nent.insert(P.nent.end(), q.nent.begin(), q.nent.end());
-    for (DevEntry e : q.entries) {
-      e.step += so;
-      P.entries.push_back(e);
+    P.entries.swap(ents);
+    P.runs.swap(runs);
+    P.valid = true;
+    {
+      std::string why;
+      if (!validate_plan(*g, P, why)) {
+        hiccl_destroy(g);
+        return HICCL_ERR_INVALID;
+      }
     }
-    P.runs.insert(P.runs.end(), q.runs.begin(), q.runs.end());
-    // rank of each item inside its slot, for interleaving the members
-    unsigned long long prev_slot = ~0ull;
-    uint32_t rank = 0;
-    for (size_t t = 0; t + 1 < q.item_off.size(); ++t) {
-      const unsigned long long sl = q.steps[q.entries[q.item_off[t]].step].slot;
-      rank = sl == prev_slot ? rank + 1 : 0;
-      prev_slot = sl;
-      items.push_back(ItemRef{sl, rank, i, (uint32_t)t});
-    }
-    relay_off = (relay_off + q.scratch_bytes + 255ull) & ~255ull;
-    P.hbm_read += q.hbm_read;
-    P.hbm_write += q.hbm_write;
-    P.stages = std::max(P.stages, q.stages);
-    P.slots = std::max(P.slots, q.slots);
-  }
-  P.scratch_bytes = relay_off;
-  // one ticket order for all: by slot, then round-robin over the members;
-  // each member keeps its own (topological) item order
-  std::stable_sort(items.begin(), items.end(), [](const ItemRef &a, const ItemRef &b) {
-    if (a.slot != b.slot) return a.slot < b.slot;
-    if (a.rank != b.rank) return a.rank < b.rank;
-    return a.member < b.member;
-  });
-  std::vector<DevEntry> ents;
-  std::vector<DevRun> runs;
-  P.item_off.assign(1, 0);
-  P.run_off.assign(1, 0);
-  for (const ItemRef &it : items) {
-    const Plan &q = comms[it.member]->plan;
-    for (uint32_t x = q.item_off[it.item]; x < q.item_off[it.item + 1]; ++x)
-      ents.push_back(P.entries[entry_off[it.member] + x]);
-    for (uint32_t x = q.run_off[it.item]; x < q.run_off[it.item + 1]; ++x) runs.push_back(P.runs[run_off[it.member] + x]);
-    P.item_off.push_back((uint32_t)ents.size());
-    P.run_off.push_back((uint32_t)runs.size());
-  }
-  P.entries.swap(ents);
-  P.runs.swap(runs);
-  P.valid = true;
-  {
-    std::string why;
-    if (!validate_plan(*g, P, why)) {
+    g->state = hiccl_comm::PLANNED;
+    hiccl_status_t st = dev_upload(g);
+    if (st != HICCL_OK) {
       hiccl_destroy(g);
-      return HICCL_ERR_INVALID;
+      return st;
     }
-  }
-  g->state = hiccl_comm::PLANNED;
-  hiccl_status_t st = dev_upload(g);
-  if (st != HICCL_OK) {
-    hiccl_destroy(g);
-    return st;
-  }
-  g->state = hiccl_comm::READY;
-  *out = g;
-  return HICCL_OK;
+    g->state = hiccl_comm::READY;
+    *out = g;
+    return HICCL_OK;
+  });
 }
 
 hiccl_status_t hiccl_level_bytes(hiccl_comm_t c, unsigned long long *per_level, int nlevels) {
-  if (!c) return HICCL_ERR_INVALID;
-  if (!c->plan.valid) return fail(c, HICCL_ERR_STATE, "no plan");
-  if (c->group) return fail(c, HICCL_ERR_UNSUPPORTED, "per-level bytes of a group: query its members");
-  if (!per_level || nlevels != (int)c->plan.level_bytes.size())
-    return fail(c, HICCL_ERR_INVALID, "nlevels must equal the hierarchy's");
-  for (int l = 0; l < nlevels; ++l) per_level[l] = c->plan.level_bytes[l];
-  return HICCL_OK;
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c) return HICCL_ERR_INVALID;
+    if (!c->plan.valid) return fail(c, HICCL_ERR_STATE, "no plan");
+    if (c->group) return fail(c, HICCL_ERR_UNSUPPORTED, "per-level bytes of a group: query its members");
+    if (!per_level || nlevels != (int)c->plan.level_bytes.size())
+      return fail(c, HICCL_ERR_INVALID, "nlevels must equal the hierarchy's");
+    for (int l = 0; l < nlevels; ++l) per_level[l] = c->plan.level_bytes[l];
+    return HICCL_OK;
+  });
 }
 
 hiccl_status_t hiccl_hbm_bytes(hiccl_comm_t c, unsigned long long *rd, unsigned long long *wr) {
-  if (!c) return HICCL_ERR_INVALID;
-  if (!c->plan.valid) return fail(c, HICCL_ERR_STATE, "no plan");
-  if (rd) *rd = c->plan.hbm_read;
-  if (wr) *wr = c->plan.hbm_write;
-  return HICCL_OK;
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c) return HICCL_ERR_INVALID;
+    if (!c->plan.valid) return fail(c, HICCL_ERR_STATE, "no plan");
+    if (rd) *rd = c->plan.hbm_read;
+    if (wr) *wr = c->plan.hbm_write;
+    return HICCL_OK;
+  });
 }
 
 hiccl_status_t hiccl_validate(hiccl_comm_t c) {
-  if (!c) return HICCL_ERR_INVALID;
-  if (!c->plan.valid) return fail(c, HICCL_ERR_STATE, "no plan");
-  std::string why;
-  if (!validate_plan(*c, c->plan, why)) return fail(c, HICCL_ERR_INVALID, "plan check: " + why);
-  return HICCL_OK;
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c) return HICCL_ERR_INVALID;
+    if (!c->plan.valid) return fail(c, HICCL_ERR_STATE, "no plan");
+    std::string why;
+    if (!validate_plan(*c, c->plan, why)) return fail(c, HICCL_ERR_INVALID, "plan check: " + why);
+    return HICCL_OK;
+  });
 }
 
 hiccl_status_t hiccl_debug_corrupt(hiccl_comm_t c, int what) {
-  if (!c) return HICCL_ERR_INVALID;
-  if (c->state != hiccl_comm::PLANNED || !c->plan.valid)
-    return fail(c, HICCL_ERR_STATE, "needs a planned communicator that is not uploaded");
-  Plan &p = c->plan;
-  const size_t N = p.steps.size();
-  switch (what) {
-    case 0: {   // a dependency on a later step: a cycle in the dependency graph
-      for (size_t i = 0; i + 1 < N; ++i)
-        if (p.pred_off[i + 1] > p.pred_off[i]) {
-          p.preds[p.pred_off[i]] = (uint32_t)(N - 1);
-          return HICCL_OK;
-        }
-      return fail(c, HICCL_ERR_INVALID, "no step with a predecessor");
-    }
-    case 1: {   // a user-buffer operand moved out of its primitive's buffers
-      for (const HStep &st : p.steps)
-        for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k)
-          if (!p.locs[st.loc0 + k].scratch) {
-            p.locs[st.loc0 + k].addr += (unsigned long long)c->prims[st.prim].count * c->esize + 4096;
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c) return HICCL_ERR_INVALID;
+    if (c->state != hiccl_comm::PLANNED || !c->plan.valid)
+      return fail(c, HICCL_ERR_STATE, "needs a planned communicator that is not uploaded");
+    Plan &p = c->plan;
+    const size_t N = p.steps.size();
+    switch (what) {
+      case 0: {   // a dependency on a later step: a cycle in the dependency graph
+        for (size_t i = 0; i + 1 < N; ++i)
+          if (p.pred_off[i + 1] > p.pred_off[i]) {
+            p.preds[p.pred_off[i]] = (uint32_t)(N - 1);
             return HICCL_OK;
           }
-      return fail(c, HICCL_ERR_INVALID, "no user operand");
+        return fail(c, HICCL_ERR_INVALID, "no step with a predecessor");
+      }
+      case 1: {   // a user-buffer operand moved out of its primitive's buffers
+        for (const HStep &st : p.steps)
+          for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k)
+            if (!p.locs[st.loc0 + k].scratch) {
+              p.locs[st.loc0 + k].addr += (unsigned long long)c->prims[st.prim].count * c->esize + 4096;
+              return HICCL_OK;
+            }
+        return fail(c, HICCL_ERR_INVALID, "no user operand");
+      }
+      case 2: {   // the last entry of a step dropped: segments left uncovered
+        if (p.entries.empty()) return fail(c, HICCL_ERR_INVALID, "no entries");
+        p.entries.back().seg_hi = p.entries.back().seg_lo;
+        return HICCL_OK;
+      }
+      default:
+        return fail(c, HICCL_ERR_INVALID, "unknown corruption");
     }
-    case 2: {   // the last entry of a step dropped: segments left uncovered
-      if (p.entries.empty()) return fail(c, HICCL_ERR_INVALID, "no entries");
-      p.entries.back().seg_hi = p.entries.back().seg_lo;
-      return HICCL_OK;
-    }
-    default:
-      return fail(c, HICCL_ERR_INVALID, "unknown corruption");
-  }
+  });
 }
 
 hiccl_status_t hiccl_plan_info(hiccl_comm_t c, hiccl_plan_info_t *out) {
-  if (!c || !out) return HICCL_ERR_INVALID;
-  if (!c->plan.valid) return fail(c, HICCL_ERR_STATE, "no plan");
-  const Plan &p = c->plan;
-  std::memset(out, 0, sizeof(*out));
-  out->steps = p.steps.size();
-  for (const HStep &st : p.steps) (st.kind == OP_COPY ? out->copy_steps : out->reduce_steps)++;
-  out->items = p.item_off.size() - 1;
-  out->edges = p.succ.size();
-  out->stages = p.stages;
-  out->slots = p.slots;
-  out->runs = p.runs.size();
-  out->scratch_bytes = p.scratch_bytes;
-  unsigned long long N = p.steps.size();
-  TableImage im;
-  build_image(p, 0, im);
-  out->table_bytes = im.recs.size() + im.items.size() * sizeof(DevItem) + N * (4 + 4 + 16) + 4 +
-                     p.succ.size() * 4 + im.ptrs.size() * 8 + sizeof(DevCtl);
-  return HICCL_OK;
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c || !out) return HICCL_ERR_INVALID;
+    if (!c->plan.valid) return fail(c, HICCL_ERR_STATE, "no plan");
+    const Plan &p = c->plan;
+    std::memset(out, 0, sizeof(*out));
+    out->steps = p.steps.size();
+    for (const HStep &st : p.steps) (st.kind == OP_COPY ? out->copy_steps : out->reduce_steps)++;
+    out->items = p.item_off.size() - 1;
+    out->edges = p.succ.size();
+    out->stages = p.stages;
+    out->slots = p.slots;
+    out->runs = p.runs.size();
+    out->scratch_bytes = p.scratch_bytes;
+    unsigned long long N = p.steps.size();
+    TableImage im;
+    build_image(p, 0, im);
+    out->table_bytes = im.recs.size() + im.items.size() * sizeof(DevItem) + N * (4 + 4 + 16) + 4 +
+                       p.succ.size() * 4 + im.ptrs.size() * 8 + sizeof(DevCtl);
+    return HICCL_OK;
+  });
 }
 
 hiccl_status_t hiccl_get_step(hiccl_comm_t c, unsigned long long index, hiccl_step_desc_t *d,
                               unsigned long long *src_addr, int *src_scratch, int *src_rank,
                               unsigned long long *dst_addr, int *dst_scratch, int *dst_rank,
                               unsigned long long *preds) {
-  if (!c || !d) return HICCL_ERR_INVALID;
-  if (!c->plan.valid) return fail(c, HICCL_ERR_STATE, "no plan");
-  const Plan &p = c->plan;
-  if (index >= p.steps.size()) return fail(c, HICCL_ERR_INVALID, "step index out of range");
-  const HStep &st = p.steps[index];
-  d->kind = st.kind;
-  d->level = st.level;
-  d->nsrc = (int)st.nsrc;
-  d->ndst = (int)st.ndst;
-  d->npreds = (int)(p.pred_off[index + 1] - p.pred_off[index]);
-  d->prim = st.prim;
-  d->branch = st.branch;
-  d->channel = st.channel;
-  d->op = st.kind == 1 ? (int)st.rop : 0;
-  d->reserved = 0;
-  d->nbytes = st.nbytes;
-  d->slot = st.slot;
-  for (uint32_t k = 0; k < st.nsrc; ++k) {
-    const Loc &l = p.locs[st.loc0 + k];
-    if (src_addr) src_addr[k] = l.addr;
-    if (src_scratch) src_scratch[k] = l.scratch;
-    if (src_rank) src_rank[k] = l.rank;
-  }
-  for (uint32_t k = 0; k < st.ndst; ++k) {
-    const Loc &l = p.locs[st.loc0 + st.nsrc + k];
-    if (dst_addr) dst_addr[k] = l.addr;
-    if (dst_scratch) dst_scratch[k] = l.scratch;
-    if (dst_rank) dst_rank[k] = l.rank;
-  }
-  if (preds)
-    for (uint32_t k = p.pred_off[index]; k < p.pred_off[index + 1]; ++k) preds[k - p.pred_off[index]] = p.preds[k];
-  return HICCL_OK;
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c || !d) return HICCL_ERR_INVALID;
+    if (!c->plan.valid) return fail(c, HICCL_ERR_STATE, "no plan");
+    const Plan &p = c->plan;
+    if (index >= p.steps.size()) return fail(c, HICCL_ERR_INVALID, "step index out of range");
+    const HStep &st = p.steps[index];
+    d->kind = st.kind;
+    d->level = st.level;
+    d->nsrc = (int)st.nsrc;
+    d->ndst = (int)st.ndst;
+    d->npreds = (int)(p.pred_off[index + 1] - p.pred_off[index]);
+    d->prim = st.prim;
+    d->branch = st.branch;
+    d->channel = st.channel;
+    d->op = st.kind == 1 ? (int)st.rop : 0;
+    d->reserved = 0;
+    d->nbytes = st.nbytes;
+    d->slot = st.slot;
+    for (uint32_t k = 0; k < st.nsrc; ++k) {
+      const Loc &l = p.locs[st.loc0 + k];
+      if (src_addr) src_addr[k] = l.addr;
+      if (src_scratch) src_scratch[k] = l.scratch;
+      if (src_rank) src_rank[k] = l.rank;
+    }
+    for (uint32_t k = 0; k < st.ndst; ++k) {
+      const Loc &l = p.locs[st.loc0 + st.nsrc + k];
+      if (dst_addr) dst_addr[k] = l.addr;
+      if (dst_scratch) dst_scratch[k] = l.scratch;
+      if (dst_rank) dst_rank[k] = l.rank;
+    }
+    if (preds)
+      for (uint32_t k = p.pred_off[index]; k < p.pred_off[index + 1]; ++k) preds[k - p.pred_off[index]] = p.preds[k];
+    return HICCL_OK;
+  });
 }
 
 hiccl_status_t hiccl_set_option(hiccl_comm_t c, hiccl_option_t opt, long long value) {
-  if (!c) return HICCL_ERR_INVALID;
-  switch (opt) {
-    case HICCL_OPT_TIMEOUT_NS:
-      if (value < 1000) return fail(c, HICCL_ERR_INVALID, "timeout below 1 us");
-      c->timeout_ns = (unsigned long long)value;
-      return HICCL_OK;
-    case HICCL_OPT_CTAS_PER_SM:
-      if (value < 1 || value > 32) return fail(c, HICCL_ERR_INVALID, "ctas per SM must be in [1, 32]");
-      c->ctas_per_sm = (int)value;
-      return HICCL_OK;
-    case HICCL_OPT_THREADS:
-      if (value != 128 && value != 256 && value != 512)
-        return fail(c, HICCL_ERR_INVALID, "threads per CTA must be 128, 256 or 512");
-      c->threads = (int)value;
-      return HICCL_OK;
-    case HICCL_OPT_TRACE:
-      if (c->state != hiccl_comm::COMPOSING && c->state != hiccl_comm::PLANNED)
-        return fail(c, HICCL_ERR_STATE, "set before hiccl_init");
-      c->trace = value ? 1 : 0;
-      return HICCL_OK;
-    case HICCL_OPT_SLOT_ITEMS:
-      if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "set before planning");
-      if (value < 1 || value > (1ll << 24)) return fail(c, HICCL_ERR_INVALID, "slot items out of range");
-      c->slot_items = (unsigned long long)value;
-      return HICCL_OK;
-    case HICCL_OPT_ITEM_BYTES:
-      if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "set before planning");
-      if (value < (long long)SEG_BYTES || value > (1ll << 30)) return fail(c, HICCL_ERR_INVALID, "item bytes out of range");
-      c->item_bytes = (unsigned long long)value;
-      return HICCL_OK;
-    case HICCL_OPT_RING:
-      if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "set before planning");
-      if (value < 1 || value > c->P) return fail(c, HICCL_ERR_INVALID, "ring must be in [1, nranks]");
-      c->ring = (int)value;
-      return HICCL_OK;
-    case HICCL_OPT_ORDER:
-      if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "set before planning");
-      if (value != 0 && value != 1) return fail(c, HICCL_ERR_INVALID, "order must be 0 or 1");
-      c->order = (int)value;
-      return HICCL_OK;
-  }
-  return fail(c, HICCL_ERR_INVALID, "unknown option");
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c) return HICCL_ERR_INVALID;
+    switch (opt) {
+      case HICCL_OPT_TIMEOUT_NS:
+        if (value < 1000) return fail(c, HICCL_ERR_INVALID, "timeout below 1 us");
+        c->timeout_ns = (unsigned long long)value;
+        return HICCL_OK;
+      case HICCL_OPT_CTAS_PER_SM:
+        if (value < 1 || value > 32) return fail(c, HICCL_ERR_INVALID, "ctas per SM must be in [1, 32]");
+        c->ctas_per_sm = (int)value;
+        return HICCL_OK;
+      case HICCL_OPT_THREADS:
+        if (value != 128 && value != 256 && value != 512)
+          return fail(c, HICCL_ERR_INVALID, "threads per CTA must be 128, 256 or 512");
+        c->threads = (int)value;
+        return HICCL_OK;
+      case HICCL_OPT_TRACE:
+        if (c->state != hiccl_comm::COMPOSING && c->state != hiccl_comm::PLANNED)
+          return fail(c, HICCL_ERR_STATE, "set before hiccl_init");
+        c->trace = value ? 1 : 0;
+        return HICCL_OK;
+      case HICCL_OPT_SLOT_ITEMS:
+        if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "set before planning");
+        if (value < 1 || value > (1ll << 24)) return fail(c, HICCL_ERR_INVALID, "slot items out of range");
+        c->slot_items = (unsigned long long)value;
+        return HICCL_OK;
+      case HICCL_OPT_ITEM_BYTES:
+        if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "set before planning");
+        if (value < (long long)SEG_BYTES || value > (1ll << 30)) return fail(c, HICCL_ERR_INVALID, "item bytes out of range");
+        c->item_bytes = (unsigned long long)value;
+        return HICCL_OK;
+      case HICCL_OPT_RING:
+        if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "set before planning");
+        if (value < 1 || value > c->P) return fail(c, HICCL_ERR_INVALID, "ring must be in [1, nranks]");
+        c->ring = (int)value;
+        return HICCL_OK;
+      case HICCL_OPT_ORDER:
+        if (c->state != hiccl_comm::COMPOSING) return fail(c, HICCL_ERR_STATE, "set before planning");
+        if (value != 0 && value != 1) return fail(c, HICCL_ERR_INVALID, "order must be 0 or 1");
+        c->order = (int)value;
+        return HICCL_OK;
+    }
+    return fail(c, HICCL_ERR_INVALID, "unknown option");
+  });
 }
 
 const char *hiccl_last_error(hiccl_comm_t c) {

@@ -1214,176 +1214,186 @@ using namespace hiccl;
 extern "C" {
 
 hiccl_status_t hiccl_start(hiccl_comm_t c, void *stream) {
-  if (!c) return HICCL_ERR_INVALID;
-  if (c->state == hiccl_comm::RUNNING) return fail(c, HICCL_ERR_STATE, "previous start not waited on");
-  if (c->state != hiccl_comm::READY || !c->dev) return fail(c, HICCL_ERR_STATE, "start before init");
-  DevState *d = c->dev;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaStreamIsCapturing");
-  if (cap == cudaStreamCaptureStatusNone) *d->host_err = 0;
-  DevTable t = d->t;
-  t.timeout_ns = c->timeout_ns;
-  if (t.nitems > 0) {
-    const int nt = c->threads;
-    const int ti = nt == 128 ? 1 : nt == 256 ? 2 : 3;
-    const int per_sm = std::min(c->ctas_per_sm, d->occ[ti]);
-    const unsigned long long grid = std::min<unsigned long long>(t.nitems, (unsigned long long)d->nsm * per_sm);
-    exec_launch(nt, (unsigned)grid, s, t);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(c, e, "executor launch");
-  }
-  // under stream capture only the launch is recorded: each replay of the
-  // graph is a complete start (counters re-arm themselves on the device);
-  // the caller synchronizes the graph launch on its stream
-  if (cap != cudaStreamCaptureStatusNone) return HICCL_OK;
-  cudaError_t e = cudaEventRecord(d->done_ev, s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
-  c->state = hiccl_comm::RUNNING;
-  return HICCL_OK;
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c) return HICCL_ERR_INVALID;
+    if (c->state == hiccl_comm::RUNNING) return fail(c, HICCL_ERR_STATE, "previous start not waited on");
+    if (c->state != hiccl_comm::READY || !c->dev) return fail(c, HICCL_ERR_STATE, "start before init");
+    DevState *d = c->dev;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaStreamIsCapturing");
+    if (cap == cudaStreamCaptureStatusNone) *d->host_err = 0;
+    DevTable t = d->t;
+    t.timeout_ns = c->timeout_ns;
+    if (t.nitems > 0) {
+      const int nt = c->threads;
+      const int ti = nt == 128 ? 1 : nt == 256 ? 2 : 3;
+      const int per_sm = std::min(c->ctas_per_sm, d->occ[ti]);
+      const unsigned long long grid = std::min<unsigned long long>(t.nitems, (unsigned long long)d->nsm * per_sm);
+      exec_launch(nt, (unsigned)grid, s, t);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(c, e, "executor launch");
+    }
+    // under stream capture only the launch is recorded: each replay of the
+    // graph is a complete start (counters re-arm themselves on the device);
+    // the caller synchronizes the graph launch on its stream
+    if (cap != cudaStreamCaptureStatusNone) return HICCL_OK;
+    cudaError_t e = cudaEventRecord(d->done_ev, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
+    c->state = hiccl_comm::RUNNING;
+    return HICCL_OK;
+  });
 }
 
 hiccl_status_t hiccl_wait(hiccl_comm_t c) {
-  if (!c) return HICCL_ERR_INVALID;
-  if (c->state != hiccl_comm::RUNNING) return fail(c, HICCL_ERR_STATE, "wait without start");
-  DevState *d = c->dev;
-  cudaError_t e = cudaEventSynchronize(d->done_ev);
-  c->state = hiccl_comm::READY;
-  if (e != cudaSuccess) return cuda_fail(c, e, "executor");
-  const unsigned long long err = *(volatile unsigned long long *)d->host_err;
-  if (err) {
-    // the aborted launch left the counters mid-way: re-arm everything
-    cudaError_t e2 = cudaMemsetAsync(d->counters, 0, d->counters_bytes, d->upload);
-    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(d->upload);
-    if (e2 != cudaSuccess) return cuda_fail(c, e2, "counter reset");
-    *d->host_err = 0;
-    const unsigned code = (unsigned)(err >> 32), step = (unsigned)(err & 0xffffffffu);
-    if (code == ERR_TIMEOUT)
-      return fail(c, HICCL_ERR_TIMEOUT, "dependency wait of step " + std::to_string(step) + " timed out");
-    if (code == ERR_STALL) return fail(c, HICCL_ERR_TIMEOUT, "an executor pipeline wait timed out");
-    return fail(c, HICCL_ERR_CUDA, "executor error " + std::to_string(code));
-  }
-  return HICCL_OK;
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c) return HICCL_ERR_INVALID;
+    if (c->state != hiccl_comm::RUNNING) return fail(c, HICCL_ERR_STATE, "wait without start");
+    DevState *d = c->dev;
+    cudaError_t e = cudaEventSynchronize(d->done_ev);
+    c->state = hiccl_comm::READY;
+    if (e != cudaSuccess) return cuda_fail(c, e, "executor");
+    const unsigned long long err = *(volatile unsigned long long *)d->host_err;
+    if (err) {
+      // the aborted launch left the counters mid-way: re-arm everything
+      cudaError_t e2 = cudaMemsetAsync(d->counters, 0, d->counters_bytes, d->upload);
+      if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(d->upload);
+      if (e2 != cudaSuccess) return cuda_fail(c, e2, "counter reset");
+      *d->host_err = 0;
+      const unsigned code = (unsigned)(err >> 32), step = (unsigned)(err & 0xffffffffu);
+      if (code == ERR_TIMEOUT)
+        return fail(c, HICCL_ERR_TIMEOUT, "dependency wait of step " + std::to_string(step) + " timed out");
+      if (code == ERR_STALL) return fail(c, HICCL_ERR_TIMEOUT, "an executor pipeline wait timed out");
+      return fail(c, HICCL_ERR_CUDA, "executor error " + std::to_string(code));
+    }
+    return HICCL_OK;
+  });
 }
 
 hiccl_status_t hiccl_autotune(hiccl_comm_t c, void *stream, int flags, hiccl_tune_t *best) {
-  if (!c) return HICCL_ERR_INVALID;
-  if (c->group) return fail(c, HICCL_ERR_UNSUPPORTED, "tune the members, then group them");
-  if (c->state != hiccl_comm::READY || !c->dev) return fail(c, HICCL_ERR_STATE, "needs an idle initialized communicator");
-  const std::vector<int> h = c->plan.hierarchy;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-    if (e0) cudaEventDestroy(e0);
-    return cuda_fail(c, cudaGetLastError(), "cudaEventCreate");
-  }
-  hiccl_tune_t cur{c->plan.stripe, c->plan.pipeline, c->order, c->threads, c->item_bytes, 0.f, 0};
-  hiccl_tune_t top = cur;
-  top.us = 3.4e38f;
-  int trials = 0;
-  // time one configuration; the communicator is left initialized with it
-  auto trial = [&](const hiccl_tune_t &k, float &us) -> hiccl_status_t {
-    c->order = k.order;
-    c->item_bytes = k.item_bytes;
-    c->threads = k.threads;
-    hiccl_status_t st = replan(c, h, k.stripe, k.pipeline);
-    if (st != HICCL_OK) return st;
-    if ((st = dev_upload(c)) != HICCL_OK) return st;
-    c->state = hiccl_comm::READY;
-    float ts[4];
-    for (int r = 0; r < 4; ++r) {
-      cudaEventRecord(e0, s);
-      if ((st = hiccl_start(c, s)) != HICCL_OK) return st;
-      cudaEventRecord(e1, s);
-      if ((st = hiccl_wait(c)) != HICCL_OK) return st;
-      cudaEventSynchronize(e1);
-      cudaEventElapsedTime(&ts[r], e0, e1);
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c) return HICCL_ERR_INVALID;
+    if (c->group) return fail(c, HICCL_ERR_UNSUPPORTED, "tune the members, then group them");
+    if (c->state != hiccl_comm::READY || !c->dev) return fail(c, HICCL_ERR_STATE, "needs an idle initialized communicator");
+    const std::vector<int> h = c->plan.hierarchy;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      if (e0) cudaEventDestroy(e0);
+      return cuda_fail(c, cudaGetLastError(), "cudaEventCreate");
     }
-    std::sort(ts + 1, ts + 4);   // run 0 is the warm-up
-    us = ts[2] * 1000.f;
-    ++trials;
-    return HICCL_OK;
-  };
-  auto consider = [&](hiccl_tune_t k) -> hiccl_status_t {
-    float us = 0.f;
-    hiccl_status_t st = trial(k, us);
-    if (st != HICCL_OK) return st;
-    k.us = us;
-    if (us < top.us) top = k;
-    return HICCL_OK;
-  };
-  hiccl_status_t st = HICCL_OK;
-  if (flags & 1) {   // the paper's stripe and pipeline parameters first
-    std::vector<int> ss{cur.stripe, 1};
-    if (!h.empty() && h.back() > 1 && h.back() <= c->P) ss.push_back(h.back());
-    std::sort(ss.begin(), ss.end());
-    ss.erase(std::unique(ss.begin(), ss.end()), ss.end());
-    if (c->ring > 1)   // a ring keeps the stripe inside one node
-      ss.erase(std::remove_if(ss.begin(), ss.end(), [&](int v) { return v > c->P / c->ring; }), ss.end());
-    for (int sv : ss)
-      for (int mv : {1, 2, 4, 8}) {
-        hiccl_tune_t k = cur;
-        k.stripe = sv;
-        k.pipeline = mv;
-        if (st == HICCL_OK) st = consider(k);
+    hiccl_tune_t cur{c->plan.stripe, c->plan.pipeline, c->order, c->threads, c->item_bytes, 0.f, 0};
+    hiccl_tune_t top = cur;
+    top.us = 3.4e38f;
+    int trials = 0;
+    // time one configuration; the communicator is left initialized with it
+    auto trial = [&](const hiccl_tune_t &k, float &us) -> hiccl_status_t {
+      c->order = k.order;
+      c->item_bytes = k.item_bytes;
+      c->threads = k.threads;
+      hiccl_status_t st = replan(c, h, k.stripe, k.pipeline);
+      if (st != HICCL_OK) return st;
+      if ((st = dev_upload(c)) != HICCL_OK) return st;
+      c->state = hiccl_comm::READY;
+      float ts[4];
+      for (int r = 0; r < 4; ++r) {
+        cudaEventRecord(e0, s);
+        if ((st = hiccl_start(c, s)) != HICCL_OK) return st;
+        cudaEventRecord(e1, s);
+        if ((st = hiccl_wait(c)) != HICCL_OK) return st;
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ts[r], e0, e1);
       }
-  } else if (st == HICCL_OK) {
-    st = consider(cur);
-  }
-  const hiccl_tune_t base = top;
-  for (int order : {1, 0})
-    for (unsigned long long ib : {32768ull, 49152ull, 65536ull, 131072ull}) {
-      hiccl_tune_t k = base;
-      k.order = order;
-      k.item_bytes = ib;
-      if (st == HICCL_OK && !(order == base.order && ib == base.item_bytes)) st = consider(k);
+      std::sort(ts + 1, ts + 4);   // run 0 is the warm-up
+      us = ts[2] * 1000.f;
+      ++trials;
+      return HICCL_OK;
+    };
+    auto consider = [&](hiccl_tune_t k) -> hiccl_status_t {
+      float us = 0.f;
+      hiccl_status_t st = trial(k, us);
+      if (st != HICCL_OK) return st;
+      k.us = us;
+      if (us < top.us) top = k;
+      return HICCL_OK;
+    };
+    hiccl_status_t st = HICCL_OK;
+    if (flags & 1) {   // the paper's stripe and pipeline parameters first
+      std::vector<int> ss{cur.stripe, 1};
+      if (!h.empty() && h.back() > 1 && h.back() <= c->P) ss.push_back(h.back());
+      std::sort(ss.begin(), ss.end());
+      ss.erase(std::unique(ss.begin(), ss.end()), ss.end());
+      if (c->ring > 1)   // a ring keeps the stripe inside one node
+        ss.erase(std::remove_if(ss.begin(), ss.end(), [&](int v) { return v > c->P / c->ring; }), ss.end());
+      for (int sv : ss)
+        for (int mv : {1, 2, 4, 8}) {
+          hiccl_tune_t k = cur;
+          k.stripe = sv;
+          k.pipeline = mv;
+          if (st == HICCL_OK) st = consider(k);
+        }
+    } else if (st == HICCL_OK) {
+      st = consider(cur);
     }
-  if (st == HICCL_OK) {
-    float us = 0.f;
-    st = trial(top, us);   // leave the communicator on the best configuration
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (st != HICCL_OK) return st;
-  top.trials = trials;
-  if (best) *best = top;
-  return HICCL_OK;
+    const hiccl_tune_t base = top;
+    for (int order : {1, 0})
+      for (unsigned long long ib : {32768ull, 49152ull, 65536ull, 131072ull}) {
+        hiccl_tune_t k = base;
+        k.order = order;
+        k.item_bytes = ib;
+        if (st == HICCL_OK && !(order == base.order && ib == base.item_bytes)) st = consider(k);
+      }
+    if (st == HICCL_OK) {
+      float us = 0.f;
+      st = trial(top, us);   // leave the communicator on the best configuration
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != HICCL_OK) return st;
+    top.trials = trials;
+    if (best) *best = top;
+    return HICCL_OK;
+  });
 }
 
 hiccl_status_t hiccl_get_trace(hiccl_comm_t c, unsigned long long *out, size_t capacity, size_t *written) {
-  if (!c || !written) return HICCL_ERR_INVALID;
-  *written = 0;
-  if (c->state != hiccl_comm::READY || !c->dev) return fail(c, HICCL_ERR_STATE, "needs an idle initialized communicator");
-  DevState *d = c->dev;
-  if (!d->trace) return fail(c, HICCL_ERR_STATE, "tracing is off (HICCL_OPT_TRACE)");
-  const size_t n = std::min<size_t>(capacity, (size_t)d->t.nitems * 6);
-  if (n && out) {
-    cudaError_t e = cudaMemcpy(out, d->trace, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(c, e, "trace copy");
-  }
-  *written = n;
-  return HICCL_OK;
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c || !written) return HICCL_ERR_INVALID;
+    *written = 0;
+    if (c->state != hiccl_comm::READY || !c->dev) return fail(c, HICCL_ERR_STATE, "needs an idle initialized communicator");
+    DevState *d = c->dev;
+    if (!d->trace) return fail(c, HICCL_ERR_STATE, "tracing is off (HICCL_OPT_TRACE)");
+    const size_t n = std::min<size_t>(capacity, (size_t)d->t.nitems * 6);
+    if (n && out) {
+      cudaError_t e = cudaMemcpy(out, d->trace, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(c, e, "trace copy");
+    }
+    *written = n;
+    return HICCL_OK;
+  });
 }
 
 hiccl_status_t hiccl_debug_withhold(hiccl_comm_t c, unsigned long long index, int extra) {
-  if (!c) return HICCL_ERR_INVALID;
-  if (c->state != hiccl_comm::READY || !c->dev) return fail(c, HICCL_ERR_STATE, "needs an idle initialized communicator");
-  DevState *d = c->dev;
-  if (index >= d->indeg.size() || extra < 0 || extra > 1000) return fail(c, HICCL_ERR_INVALID, "bad step or count");
-  // the dependency count is stored in every record entry of the step
-  uint32_t v[1] = {d->indeg[index] + (uint32_t)extra};
-  const Plan &p = c->plan;
-  cudaError_t e = cudaSuccess;
-  for (size_t i = 0; i < d->items.size() && e == cudaSuccess; ++i)
-    for (uint32_t k = p.item_off[i]; k < p.item_off[i + 1] && e == cudaSuccess; ++k)
-      if (p.entries[k].step == index) {
-        char *at = d->recs_dev + (size_t)d->items[i].rec * 16 + (size_t)(k - p.item_off[i]) * sizeof(RecEnt) +
-                   offsetof(RecEnt, indeg);
-        e = cudaMemcpyAsync(at, v, sizeof(uint32_t), cudaMemcpyHostToDevice, d->upload);
-      }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(d->upload);
-  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync");
-  return HICCL_OK;
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c) return HICCL_ERR_INVALID;
+    if (c->state != hiccl_comm::READY || !c->dev) return fail(c, HICCL_ERR_STATE, "needs an idle initialized communicator");
+    DevState *d = c->dev;
+    if (index >= d->indeg.size() || extra < 0 || extra > 1000) return fail(c, HICCL_ERR_INVALID, "bad step or count");
+    // the dependency count is stored in every record entry of the step
+    uint32_t v[1] = {d->indeg[index] + (uint32_t)extra};
+    const Plan &p = c->plan;
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < d->items.size() && e == cudaSuccess; ++i)
+      for (uint32_t k = p.item_off[i]; k < p.item_off[i + 1] && e == cudaSuccess; ++k)
+        if (p.entries[k].step == index) {
+          char *at = d->recs_dev + (size_t)d->items[i].rec * 16 + (size_t)(k - p.item_off[i]) * sizeof(RecEnt) +
+                     offsetof(RecEnt, indeg);
+          e = cudaMemcpyAsync(at, v, sizeof(uint32_t), cudaMemcpyHostToDevice, d->upload);
+        }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->upload);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync");
+    return HICCL_OK;
+  });
 }
 
 }  // extern "C"
@@ -1411,85 +1421,87 @@ static void *g_static_addr[MAX_STATIC_DEVICES];   // device address of the arena
 }  // namespace hiccl
 
 extern "C" hiccl_status_t hiccl_run_static(hiccl_comm_t c, void *stream) {
-  if (!c) return HICCL_ERR_INVALID;
-  if (!c->plan.valid) return HICCL_ERR_STATE;
-  const Plan &p = c->plan;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const unsigned long long N = p.steps.size();
-  const unsigned long long NI = p.item_off.size() ? p.item_off.size() - 1 : 0, NS = p.succ.size();
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c) return HICCL_ERR_INVALID;
+    if (!c->plan.valid) return HICCL_ERR_STATE;
+    const Plan &p = c->plan;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const unsigned long long N = p.steps.size();
+    const unsigned long long NI = p.item_off.size() ? p.item_off.size() - 1 : 0, NS = p.succ.size();
 
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return HICCL_ERR_CUDA;
-  if (dev < 0 || dev >= MAX_STATIC_DEVICES) return HICCL_ERR_UNSUPPORTED;
-  if (!g_static_addr[dev]) {   // once per device, with that device current
-    void *addr = nullptr;
-    if (cudaGetSymbolAddress(&addr, g_static_arena) != cudaSuccess || !addr) {
-      cudaGetLastError();
-      return HICCL_ERR_CUDA;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HICCL_ERR_CUDA;
+    if (dev < 0 || dev >= MAX_STATIC_DEVICES) return HICCL_ERR_UNSUPPORTED;
+    if (!g_static_addr[dev]) {   // once per device, with that device current
+      void *addr = nullptr;
+      if (cudaGetSymbolAddress(&addr, g_static_arena) != cudaSuccess || !addr) {
+        cudaGetLastError();
+        return HICCL_ERR_CUDA;
+      }
+      g_static_addr[dev] = addr;
     }
-    g_static_addr[dev] = addr;
-  }
-  char *base = static_cast<char *>(g_static_addr[dev]);
+    char *base = static_cast<char *>(g_static_addr[dev]);
 
-  // arena layout: relay buffers first (their addresses go into the records),
-  // then the read-only arrays, then the counters
-  unsigned long long off = 0;
-  auto place = [&](unsigned long long bytes) {
-    const unsigned long long o = off;
-    off = (off + bytes + 255) & ~255ull;
-    return o;
-  };
-  const unsigned long long o_relay = place(p.scratch_bytes);
-  TableImage im;
-  build_image(p, (unsigned long long)(uintptr_t)(base + o_relay), im);
-  const unsigned long long o_recs = place(im.recs.size()), o_items = place(im.items.size() * sizeof(DevItem)),
-                           o_nent = place(N * 4), o_succoff = place((N + 1) * 4), o_succ = place(NS * 4),
-                           o_ptrs = place(im.ptrs.size() * 8), o_ctr = place(N * 16 + sizeof(DevCtl) + 8);
-  if (off > HICCL_STATIC_ARENA_BYTES) return HICCL_ERR_TOO_LARGE;
-  if (N == 0) return HICCL_OK;
+    // arena layout: relay buffers first (their addresses go into the records),
+    // then the read-only arrays, then the counters
+    unsigned long long off = 0;
+    auto place = [&](unsigned long long bytes) {
+      const unsigned long long o = off;
+      off = (off + bytes + 255) & ~255ull;
+      return o;
+    };
+    const unsigned long long o_relay = place(p.scratch_bytes);
+    TableImage im;
+    build_image(p, (unsigned long long)(uintptr_t)(base + o_relay), im);
+    const unsigned long long o_recs = place(im.recs.size()), o_items = place(im.items.size() * sizeof(DevItem)),
+                             o_nent = place(N * 4), o_succoff = place((N + 1) * 4), o_succ = place(NS * 4),
+                             o_ptrs = place(im.ptrs.size() * 8), o_ctr = place(N * 16 + sizeof(DevCtl) + 8);
+    if (off > HICCL_STATIC_ARENA_BYTES) return HICCL_ERR_TOO_LARGE;
+    if (N == 0) return HICCL_OK;
 
-  auto h2d = [&](unsigned long long o, const void *src, unsigned long long bytes) {
-    return bytes ? cudaMemcpyAsync(base + o, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
-  };
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = h2d(o_recs, im.recs.data(), im.recs.size());
-  if (e == cudaSuccess) e = h2d(o_items, im.items.data(), im.items.size() * sizeof(DevItem));
-  if (e == cudaSuccess) e = h2d(o_nent, p.nent.data(), N * 4);
-  if (e == cudaSuccess) e = h2d(o_succoff, p.succ_off.data(), (N + 1) * 4);
-  if (e == cudaSuccess) e = h2d(o_succ, p.succ.data(), NS * 4);
-  if (e == cudaSuccess) e = h2d(o_ptrs, im.ptrs.data(), im.ptrs.size() * 8);
-  // every call starts from zeroed counters: the arena keeps the last call's contents
-  if (e == cudaSuccess) e = cudaMemsetAsync(base + o_ctr, 0, N * 16 + sizeof(DevCtl) + 8, s);
-  if (e != cudaSuccess) return HICCL_ERR_CUDA;
+    auto h2d = [&](unsigned long long o, const void *src, unsigned long long bytes) {
+      return bytes ? cudaMemcpyAsync(base + o, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+    };
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = h2d(o_recs, im.recs.data(), im.recs.size());
+    if (e == cudaSuccess) e = h2d(o_items, im.items.data(), im.items.size() * sizeof(DevItem));
+    if (e == cudaSuccess) e = h2d(o_nent, p.nent.data(), N * 4);
+    if (e == cudaSuccess) e = h2d(o_succoff, p.succ_off.data(), (N + 1) * 4);
+    if (e == cudaSuccess) e = h2d(o_succ, p.succ.data(), NS * 4);
+    if (e == cudaSuccess) e = h2d(o_ptrs, im.ptrs.data(), im.ptrs.size() * 8);
+    // every call starts from zeroed counters: the arena keeps the last call's contents
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_ctr, 0, N * 16 + sizeof(DevCtl) + 8, s);
+    if (e != cudaSuccess) return HICCL_ERR_CUDA;
 
-  DevTable t{};
-  t.recs = reinterpret_cast<const unsigned char *>(base + o_recs);
-  t.items = reinterpret_cast<const DevItem *>(base + o_items);
-  t.nent = reinterpret_cast<const uint32_t *>(base + o_nent);
-  t.succ_off = reinterpret_cast<const uint32_t *>(base + o_succoff);
-  t.succ = reinterpret_cast<const uint32_t *>(base + o_succ);
-  t.ptrs = reinterpret_cast<const unsigned long long *>(base + o_ptrs);
-  t.dep = reinterpret_cast<unsigned long long *>(base + o_ctr);
-  t.done = reinterpret_cast<unsigned long long *>(base + o_ctr + N * 8);
-  t.ctl = reinterpret_cast<DevCtl *>(base + o_ctr + N * 16);
-  t.host_err = reinterpret_cast<unsigned long long *>(base + o_ctr + N * 16 + sizeof(DevCtl));
-  t.nitems = NI;
-  t.timeout_ns = c->timeout_ns;
-  t.seg = p.seg;
-  t.trace = nullptr;
-  if (NI > 0) {
-    int nsm = 0, occ = 0;
-    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HICCL_ERR_CUDA;
-    const int nt = c->threads;
-    if (exec_occupancy(nt, &occ) != cudaSuccess || occ < 1) return HICCL_ERR_CUDA;
-    const unsigned grid = (unsigned)std::min<unsigned long long>(NI, (unsigned long long)nsm * std::min(c->ctas_per_sm, occ));
-    exec_launch(nt, grid, s, t);
-    if (cudaGetLastError() != cudaSuccess) return HICCL_ERR_CUDA;
-  }
-  if (cudaStreamSynchronize(s) != cudaSuccess) return HICCL_ERR_CUDA;
-  unsigned long long err = 0;
-  if (cudaMemcpy(&err, base + o_ctr + N * 16 + offsetof(DevCtl, err), sizeof(err), cudaMemcpyDeviceToHost) !=
-      cudaSuccess)
-    return HICCL_ERR_CUDA;
-  return err ? HICCL_ERR_TIMEOUT : HICCL_OK;
+    DevTable t{};
+    t.recs = reinterpret_cast<const unsigned char *>(base + o_recs);
+    t.items = reinterpret_cast<const DevItem *>(base + o_items);
+    t.nent = reinterpret_cast<const uint32_t *>(base + o_nent);
+    t.succ_off = reinterpret_cast<const uint32_t *>(base + o_succoff);
+    t.succ = reinterpret_cast<const uint32_t *>(base + o_succ);
+    t.ptrs = reinterpret_cast<const unsigned long long *>(base + o_ptrs);
+    t.dep = reinterpret_cast<unsigned long long *>(base + o_ctr);
+    t.done = reinterpret_cast<unsigned long long *>(base + o_ctr + N * 8);
+    t.ctl = reinterpret_cast<DevCtl *>(base + o_ctr + N * 16);
+    t.host_err = reinterpret_cast<unsigned long long *>(base + o_ctr + N * 16 + sizeof(DevCtl));
+    t.nitems = NI;
+    t.timeout_ns = c->timeout_ns;
+    t.seg = p.seg;
+    t.trace = nullptr;
+    if (NI > 0) {
+      int nsm = 0, occ = 0;
+      if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HICCL_ERR_CUDA;
+      const int nt = c->threads;
+      if (exec_occupancy(nt, &occ) != cudaSuccess || occ < 1) return HICCL_ERR_CUDA;
+      const unsigned grid = (unsigned)std::min<unsigned long long>(NI, (unsigned long long)nsm * std::min(c->ctas_per_sm, occ));
+      exec_launch(nt, grid, s, t);
+      if (cudaGetLastError() != cudaSuccess) return HICCL_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return HICCL_ERR_CUDA;
+    unsigned long long err = 0;
+    if (cudaMemcpy(&err, base + o_ctr + N * 16 + offsetof(DevCtl, err), sizeof(err), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return HICCL_ERR_CUDA;
+    return err ? HICCL_ERR_TIMEOUT : HICCL_OK;
+  });
 }

@@ -130,3 +130,40 @@ def test_empty_program_plans():
     info = c.plan_info()
     assert info["steps"] == 0 and info["items"] == 0
     assert c.level_bytes() == [0]
+
+
+_NOMEM_CHILD = r"""
+import resource, sys
+sys.path.insert(0, sys.argv[1])
+from paper_2408_05962_gb300 import hiccl as H
+H.lib()                                   # load before the limit
+lim = int(sys.argv[2])
+resource.setrlimit(resource.RLIMIT_AS, (lim, lim))
+P, d = 1024, 1024
+base = 1 << 40
+send = [base + r * (d * P * 4 + 4096) for r in range(P)]
+recv = [base + (1 << 38) + r * (d * P * 4 + 4096) for r in range(P)]
+c = H.Comm(P, "f32")
+c.add_collective("allreduce", d, send, recv)
+try:
+    c.plan([32, 32], 32, 4)               # needs several GB of host memory
+    print("planned")
+except H.HicclError as e:
+    print("status", e.status, e.message)
+"""
+
+
+def test_host_memory_exhaustion_is_a_status_not_an_abort():
+    """No call of the C ABI lets a C++ exception escape: planning a schedule
+    of hundreds of millions of operands under a 1.5 GB address-space limit
+    returns HICCL_ERR_NOMEM (the process does not abort)."""
+    import subprocess
+    import sys
+    pytest.importorskip("resource")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    limit = 1536 << 20
+    r = subprocess.run([sys.executable, "-c", _NOMEM_CHILD, root, str(limit)], capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
+    out = r.stdout.strip().splitlines()[-1]
+    assert out.startswith(f"status {H.ERR_NOMEM} "), out
