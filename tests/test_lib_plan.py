@@ -305,3 +305,37 @@ def test_every_plan_passes_the_check(name):
 @pytest.mark.parametrize("P,h,ring,s,m", [(12, [4, 3], 4, 3, 2), (16, [4, 4], 16, 1, 2), (12, [2, 2, 3], 2, 3, 1)])
 def test_ring_fp8_collectives(name, P, h, ring, s, m):
     _check(PR.BUILDERS[name](P, 3, dtype="fp8"), h, s, m, seed=P + ring, ring=ring)
+
+
+def test_fuzz_random_programs_and_shapes():
+    """Seeded sweep beyond the exhaustive small cases: P up to 24, a random
+    factorization of P, random stripe, pipeline and (where a level allows
+    one) ring, random sparse programs in f32 and i32 -- the library's table
+    reproduces the oracle's semantics and accounting in every case."""
+    from oracle.hierarchy import ring_level
+    g = np.random.Generator(np.random.PCG64(20240805))
+    n = 0
+    for it in range(240):
+        P = int(g.choice([5, 6, 8, 9, 12, 16, 18, 24]))
+        hs = all_factorizations(P)
+        h = list(hs[int(g.integers(0, len(hs)))])
+        s = int(g.integers(1, P + 1))
+        m = int(g.integers(1, 5))
+        dtype = "f32" if it % 2 == 0 else "i32"
+        prog = random_program(P, 5000 + it, dtype, chunks=int(g.integers(1, 4)), max_n=24)
+        if S.find_race(prog) is not None:
+            continue
+        ring = 1
+        if it % 3 == 0:   # a ring over the groups of a level, when the stripe fits a node
+            def fits(r):
+                try:
+                    ring_level(h, r)
+                except ValueError:
+                    return False
+                return s <= P // r
+            cands = [r for r in range(2, P + 1) if P % r == 0 and fits(r)]
+            if cands:
+                ring = int(cands[int(g.integers(0, len(cands)))])
+        _check(prog, h, s, m, seed=it, ring=ring)
+        n += 1
+    assert n >= 160
