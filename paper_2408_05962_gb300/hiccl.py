@@ -29,6 +29,8 @@ def nbytes(dtype: int, elems: int) -> int:
             raise ValueError("FP8 counts must be multiples of 128")
         return elems // FP8_BLOCK * FP8_BLOCK_BYTES
     return elems * ESIZE[dtype]
+
+
 SUM, MAX, MIN, LOR = 0, 1, 2, 3
 OPS = {"sum": SUM, "max": MAX, "min": MIN, "lor": LOR}
 OP_NAMES = {v: k for k, v in OPS.items()}
