@@ -75,6 +75,27 @@ static bool to_units(hiccl_comm *c, size_t count, size_t &units) {
 
 namespace {
 
+// Run fn(0) .. fn(n - 1) on up to n host threads, fn(0) on the calling one;
+// the share of a thread that cannot be started runs on the calling thread.
+// fn must not throw.
+template <typename F>
+void run_parallel(int n, F &&fn) {
+  std::vector<std::thread> th;
+  std::vector<int> here;
+  th.reserve(n);
+  here.reserve(n);
+  for (int t = 1; t < n; ++t) {
+    try {
+      th.emplace_back(fn, t);
+    } catch (...) {
+      here.push_back(t);
+    }
+  }
+  fn(0);
+  for (int t : here) fn(t);
+  for (auto &x : th) x.join();
+}
+
 struct Builder {
   const hiccl_comm &c;
   std::vector<int> h;
@@ -795,9 +816,7 @@ void build_image(const Plan &p, unsigned long long relay_base, TableImage &im) {
   if (nthr <= 1) {
     fill(0, NI);
   } else {
-    std::vector<std::thread> th;
-    for (size_t t = 0; t < nthr; ++t) th.emplace_back(fill, NI * t / nthr, NI * (t + 1) / nthr);
-    for (auto &x : th) x.join();
+    run_parallel((int)nthr, [&](int t) { fill(NI * t / nthr, NI * (t + 1) / nthr); });
   }
 }
 
