@@ -339,3 +339,25 @@ def test_fuzz_random_programs_and_shapes():
         _check(prog, h, s, m, seed=it, ring=ring)
         n += 1
     assert n >= 160
+
+
+@pytest.mark.parametrize("m", [1, 2, 4, 5, 7])
+def test_pipeline_slots_of_fig7(m):
+    """Sec. 4.5 / Fig. 7: the m channels of a piece run the same stages, each
+    channel one slot behind the previous, so a schedule of S dependent stages
+    fills S + m - 1 pipeline slots (warm-up, overlapped middle, wind-down).
+    Fig. 6's examples on four nodes of three GPUs with stripe(3): the tree
+    over {2,2,3} has S = 4 stages, ring(4) over {4,3} has S = 5 (pipeline-slot
+    order, HICCL_OPT_ORDER = 0)."""
+    from paper_2408_05962_gb300 import hiccl as H
+    for hier, ring, stages in (([2, 2, 3], 1, 4), ([4, 3], 4, 5)):
+        prog = PR.broadcast(12, 600, root=0)
+        fake = FakeAddresses(prog)
+        comm = register(prog, fake.addr)
+        comm.set_option(H.OPT_ORDER, 0)
+        if ring > 1:
+            comm.set_option(H.OPT_RING, ring)
+        comm.plan(hier, 3, m)
+        info = comm.plan_info()
+        assert info["stages"] == stages
+        assert info["slots"] == stages + m - 1, (hier, ring, m, info)
