@@ -361,3 +361,31 @@ def test_pipeline_slots_of_fig7(m):
         info = comm.plan_info()
         assert info["stages"] == stages
         assert info["slots"] == stages + m - 1, (hier, ring, m, info)
+
+
+@pytest.mark.parametrize("m", [1, 3, 5])
+def test_pipeline_slots_of_eq1_eq2(m):
+    """Sec. 4.6, Eq. 1: a pipelined ring Broadcast over n nodes with no
+    hierarchy inside them takes n + m - 2 inter-node slots (n - 1 hops, each
+    channel one slot behind the previous); Eq. 2: the tree over n = 2^L nodes
+    has log n levels, i.e. log n + m - 1 slots."""
+    import math
+    from paper_2408_05962_gb300 import hiccl as H
+    for n in (3, 4, 6, 8):
+        prog = PR.broadcast(n, 480, root=0)
+        fake = FakeAddresses(prog)
+        comm = register(prog, fake.addr)
+        comm.set_option(H.OPT_ORDER, 0)
+        comm.set_option(H.OPT_RING, n)
+        comm.plan([n], 1, m)
+        info = comm.plan_info()
+        assert info["stages"] == n - 1 and info["slots"] == n + m - 2, (n, m, info)
+    for n in (2, 4, 8, 16):
+        L = int(math.log2(n))
+        prog = PR.broadcast(n, 480, root=0)
+        fake = FakeAddresses(prog)
+        comm = register(prog, fake.addr)
+        comm.set_option(H.OPT_ORDER, 0)
+        comm.plan([2] * L, 1, m)
+        info = comm.plan_info()
+        assert info["stages"] == L and info["slots"] == L + m - 1, (n, m, info)
