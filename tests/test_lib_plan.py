@@ -389,3 +389,25 @@ def test_pipeline_slots_of_eq1_eq2(m):
         comm.plan([2] * L, 1, m)
         info = comm.plan_info()
         assert info["stages"] == L and info["slots"] == L + m - 1, (n, m, info)
+
+
+def test_library_fence_is_dependency_not_barrier():
+    """Sec. 3.3 / Fig. 4 in the library's table: in the All-reduce program
+    (reductions R_0..R_7, fence, multicasts M_0..M_7), a step of M_i depends
+    across the fence only on steps of R_i of the same pipeline channel."""
+    P, d = 8, 16
+    prog = PR.allreduce(P, d)
+    fake = FakeAddresses(prog)
+    comm = register(prog, fake.addr)
+    comm.plan([2, 4], 1, 2)
+    steps = comm.steps()
+    crossing = 0
+    for st in steps:
+        if st["prim"] < P:
+            continue
+        for q in st["preds"]:
+            dep = steps[q]
+            if dep["prim"] < P:
+                assert dep["prim"] == st["prim"] - P and dep["channel"] == st["channel"], (st, dep)
+                crossing += 1
+    assert crossing > 0
