@@ -136,6 +136,16 @@ class Plan:
         of the unpipelined schedule, Sec. 4.5)."""
         return 1 + max(self.depths(), default=-1) if self.ops else 0
 
+    def slots(self) -> int:
+        """Slots of the overlapped pipeline (Sec. 4.5, Fig. 7): channel c of a
+        piece starts at slot c and an op runs one slot after its latest
+        dependency, so S dependent stages over m channels fill S + m - 1
+        slots (reading: the figure staggers the channels by one stage)."""
+        s = [0] * len(self.ops)
+        for i, op in enumerate(self.ops):        # ops are emitted after their deps
+            s[i] = max(op.channel, 1 + max((s[j] for j in op.deps), default=-1))
+        return 1 + max(s, default=-1) if self.ops else 0
+
 
 def piece_bounds(count: int, parts: int, quantum: int) -> list:
     """Reading 3: boundaries of ``parts`` pieces."""

@@ -411,3 +411,23 @@ def test_library_fence_is_dependency_not_barrier():
                 assert dep["prim"] == st["prim"] - P and dep["channel"] == st["channel"], (st, dep)
                 crossing += 1
     assert crossing > 0
+
+
+@pytest.mark.parametrize("name", PR.SEVEN + ("reduce",))
+@pytest.mark.parametrize("P,h,s,m,ring", [(8, [2, 4], 4, 3, 1), (12, [2, 2, 3], 3, 5, 1), (12, [4, 3], 3, 4, 4),
+                                          (16, [4, 4], 4, 2, 1), (16, [4, 4], 4, 3, 4)])
+def test_pipeline_slots_match_the_oracle(name, P, h, s, m, ring):
+    """In pipeline-slot order (HICCL_OPT_ORDER = 0) the library's number of
+    slots equals the oracle factorizer's (channel c starts at slot c, a step
+    runs one slot after its latest predecessor, fences included)."""
+    from paper_2408_05962_gb300 import hiccl as H
+    prog = PR.BUILDERS[name](P, 48)
+    fake = FakeAddresses(prog)
+    comm = register(prog, fake.addr)
+    comm.set_option(H.OPT_ORDER, 0)
+    if ring > 1:
+        comm.set_option(H.OPT_RING, ring)
+    comm.plan(h, s, m)
+    plan = factorize(prog, h, s, m, ring)
+    assert comm.plan_info()["slots"] == plan.slots()
+    assert comm.plan_info()["stages"] == plan.stages()

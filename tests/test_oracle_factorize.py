@@ -380,3 +380,15 @@ def _init_ops(prog, seed):
         for v in mem.values():
             v[...] = g.integers(-2, 3, size=v.shape)
     return mem
+
+
+@pytest.mark.parametrize("m", [1, 2, 5])
+def test_oracle_slots_of_fig7_and_eq1(m):
+    """Sec. 4.5 / Fig. 7 and Eq. 1: S dependent stages over m channels fill
+    S + m - 1 slots -- the tree and ring(4) examples of Fig. 6 (S = 4, 5) and
+    a ring over n single-GPU nodes (S = n - 1, Eq. 1's n + m - 2)."""
+    prog = PR.broadcast(12, 600, root=0)
+    assert factorize(prog, [2, 2, 3], 3, m).slots() == 4 + m - 1
+    assert factorize(prog, [4, 3], 3, m, ring=4).slots() == 5 + m - 1
+    for n in (3, 4, 6):
+        assert factorize(PR.broadcast(n, 480, root=0), [n], 1, m, ring=n).slots() == n + m - 2
