@@ -726,6 +726,38 @@ bool find_race(const hiccl_comm &c, std::string &msg) {
 // prefix sums of their segment counts, and the entries' operand pointers
 // inline while they fit.  Meta words carry the 16-byte alignment of every
 // resolved operand.
+// Shape of work item i's record (rec left 0): its entries' operand pointers
+// go inline, in entry order, while a step has at most PTR_STEP_MAX operands
+// and the item at most PTR_CAP; its steps' successors go inline up to
+// SUCC_CAP in all, else the item reads the global successor lists.
+static DevItem item_shape(const Plan &p, size_t i) {
+  uint32_t nptr = 0, nsucc = 0;
+  for (uint32_t e = p.item_off[i]; e < p.item_off[i + 1]; ++e) {
+    const uint32_t st_i = p.entries[e].step;
+    const HStep &st = p.steps[st_i];
+    const uint32_t np = st.nsrc + st.ndst;
+    if (np <= PTR_STEP_MAX && nptr + np <= PTR_CAP) nptr += np;
+    nsucc += p.succ_off[st_i + 1] - p.succ_off[st_i];
+  }
+  DevItem it{};
+  it.nent = p.item_off[i + 1] - p.item_off[i];
+  it.nrun = p.run_off[i + 1] - p.run_off[i];
+  it.nptr = nptr;
+  it.nsucc = nsucc <= SUCC_CAP ? nsucc : SUCC_GLOBAL;
+  return it;
+}
+
+// Bytes of the device table of plan p (records, item descriptors, per-step
+// targets and successor CSR, pointer array, control block), computed from
+// the record shapes without building the image.
+unsigned long long table_bytes(const Plan &p) {
+  const size_t NI = p.item_off.empty() ? 0 : p.item_off.size() - 1;
+  unsigned long long recs = 0;
+  for (size_t i = 0; i < NI; ++i) recs += rec_bytes(item_shape(p, i));
+  return recs + NI * sizeof(DevItem) + p.steps.size() * (4 + 4 + 16) + 4 + p.succ.size() * 4 +
+         p.locs.size() * 8 + sizeof(DevCtl);
+}
+
 void build_image(const Plan &p, unsigned long long relay_base, TableImage &im) {
   const size_t N = p.steps.size();
   im.ptrs.resize(p.locs.size());
@@ -746,23 +778,9 @@ void build_image(const Plan &p, unsigned long long relay_base, TableImage &im) {
   // in both passes: entries in order while the step's operands fit)
   std::vector<unsigned long long> at(NI + 1, 0);
   for (size_t i = 0; i < NI; ++i) {
-    uint32_t nptr = 0;
-    for (uint32_t e = p.item_off[i]; e < p.item_off[i + 1]; ++e) {
-      const HStep &st = p.steps[p.entries[e].step];
-      const uint32_t np = st.nsrc + st.ndst;
-      if (np <= PTR_STEP_MAX && nptr + np <= PTR_CAP) nptr += np;
-    }
-    uint32_t nsucc = 0;
-    for (uint32_t e = p.item_off[i]; e < p.item_off[i + 1]; ++e) {
-      const uint32_t st_i = p.entries[e].step;
-      nsucc += p.succ_off[st_i + 1] - p.succ_off[st_i];
-    }
     DevItem &it = im.items[i];
+    it = item_shape(p, i);
     it.rec = (uint32_t)(at[i] / 16);
-    it.nent = p.item_off[i + 1] - p.item_off[i];
-    it.nrun = p.run_off[i + 1] - p.run_off[i];
-    it.nptr = nptr;
-    it.nsucc = nsucc <= SUCC_CAP ? nsucc : SUCC_GLOBAL;
     at[i + 1] = at[i] + rec_bytes(it);
   }
   im.recs.assign(at[NI], 0);
@@ -1661,11 +1679,7 @@ hiccl_status_t hiccl_plan_info(hiccl_comm_t c, hiccl_plan_info_t *out) {
     out->slots = p.slots;
     out->runs = p.runs.size();
     out->scratch_bytes = p.scratch_bytes;
-    unsigned long long N = p.steps.size();
-    TableImage im;
-    build_image(p, 0, im);
-    out->table_bytes = im.recs.size() + im.items.size() * sizeof(DevItem) + N * (4 + 4 + 16) + 4 +
-                       p.succ.size() * 4 + im.ptrs.size() * 8 + sizeof(DevCtl);
+    out->table_bytes = table_bytes(p);
     return HICCL_OK;
   });
 }
