@@ -73,6 +73,9 @@ from .model import DTYPES, QUANTUM, Multicast, Program, Ref
 
 @dataclass
 class Op:
+    """One point-to-point step of a factorized primitive (Sec. 4): a copy of
+    n units to every destination, or an in-order fold of the sources into one
+    destination."""
     kind: str                 # "copy" | "reduce"
     srcs: list                # [(rank, Ref)]
     dsts: list                # [(rank, Ref)]
@@ -88,6 +91,8 @@ class Op:
 
 @dataclass
 class Plan:
+    """A factorized program (Sec. 4): its steps in emission order, each after
+    its dependencies, and its relay buffers."""
     P: int
     hierarchy: list
     stripe: int
@@ -100,6 +105,8 @@ class Plan:
 
     # ---- accounting -------------------------------------------------------
     def level_bytes(self) -> list:
+        """Bytes that cross each hierarchy level (Sec. 4.1; Table 3's per-node
+        volumes are the top-level entry)."""
         out = [0] * len(self.hierarchy)
         for op in self.ops:
             if op.kind == "copy":
@@ -115,6 +122,8 @@ class Plan:
         return out
 
     def hbm_bytes(self) -> tuple:
+        """Schedule bytes (read, written): a copy reads n and writes n per
+        destination; an f-input fold reads f*n and writes n."""
         rd = wr = 0
         for op in self.ops:
             if op.kind == "copy":
@@ -126,6 +135,7 @@ class Plan:
         return rd * self.esize, wr * self.esize
 
     def depths(self) -> list:
+        """Dependency depth of every step, i.e. its stage (Sec. 4.5)."""
         d = [0] * len(self.ops)
         for i, op in enumerate(self.ops):        # ops are emitted after their deps
             d[i] = 1 + max((d[j] for j in op.deps), default=-1)
@@ -158,6 +168,9 @@ def piece_bounds(count: int, parts: int, quantum: int) -> list:
 
 
 class Factorizer:
+    """The factorization of Sec. 4 in the paper's order: striping (Sec. 4.3),
+    ring (Sec. 4.4) and tree (Sec. 4.2) per primitive, pipeline channels
+    (Sec. 4.5), fence dependencies (Sec. 3.3)."""
     def __init__(self, prog: Program, hierarchy, stripe: int = 1, pipeline: int = 1, ring: int = 1):
         self.prog = prog
         self.h = check(hierarchy, prog.P)
@@ -397,6 +410,8 @@ class Factorizer:
 
     # ---- whole program -----------------------------------------------------------
     def run(self) -> Plan:
+        """Emit the steps of every primitive in program order, then the fence
+        dependencies between epochs (Sec. 3.3, reading 5 above)."""
         pid = 0
         for e, epoch in enumerate(self.prog.epochs):
             first = len(self.ops)
@@ -455,4 +470,6 @@ def _op_accesses(op: Op):
 
 
 def factorize(prog: Program, hierarchy, stripe: int = 1, pipeline: int = 1, ring: int = 1) -> Plan:
+    """Factorize ``prog`` over ``hierarchy`` with stripe s, pipeline depth m
+    and ring(n) (Sec. 4; readings 1-6 above)."""
     return Factorizer(prog, hierarchy, stripe, pipeline, ring).run()

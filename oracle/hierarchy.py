@@ -16,6 +16,8 @@ from math import prod
 
 
 def check(hierarchy, P: int) -> list[int]:
+    """The hierarchy vector as a list of factors whose product is P (Sec. 4.1,
+    the hierarchy argument of init)."""
     h = [int(f) for f in hierarchy]
     if not h or any(f < 1 for f in h) or prod(h) != P:
         raise ValueError(f"hierarchy {hierarchy} does not factor P={P}")
@@ -23,7 +25,7 @@ def check(hierarchy, P: int) -> list[int]:
 
 
 def group_sizes(hierarchy) -> list[int]:
-    """G[l] for l = 0..L; G[0] = P and G[L] = 1."""
+    """G[l] for l = 0..L; G[0] = P and G[L] = 1 (Sec. 4.2)."""
     h = list(hierarchy)
     return [prod(h[l:]) for l in range(len(h) + 1)]
 
@@ -31,7 +33,7 @@ def group_sizes(hierarchy) -> list[int]:
 def level_of(a: int, b: int, hierarchy) -> int | None:
     """The level at which ranks a and b first fall into different subgroups,
     i.e. the hierarchy level whose link a transfer a -> b crosses.  None when
-    a == b (a local, in-memory transfer)."""
+    a == b (a local, in-memory transfer).  Sec. 4.2."""
     if a == b:
         return None
     G = group_sizes(hierarchy)
@@ -57,7 +59,8 @@ def ring_level(hierarchy, ring: int) -> int:
 
 
 def all_factorizations(P: int, max_levels: int = 4) -> list[list[int]]:
-    """Every ordered factorization of P into factors >= 2 (plus [P] itself)."""
+    """Every ordered factorization of P into factors >= 2, plus [P] itself:
+    the hierarchies Sec. 4.1 allows for P ranks."""
     out = []
 
     def rec(rest, acc):

@@ -43,6 +43,8 @@ assert FP8_BLOCK_DTYPE.itemsize == FP8_BLOCK_BYTES
 # ---------------------------------------------------------------------------
 
 def bf16_to_f32(h: np.ndarray) -> np.ndarray:
+    """BF16 bit patterns -> binary32 values (a BF16 value is the upper half of
+    a binary32)."""
     return (np.asarray(h, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32)
 
 
@@ -81,6 +83,8 @@ _POS = E4M3_VALUES[:0x7F]          # codes 0x00..0x7E: the non-negative finite v
 
 
 def e4m3_decode(q: np.ndarray) -> np.ndarray:
+    """e4m3 codes -> binary32 values, from the code table of the format's
+    definition."""
     return E4M3_VALUES[np.asarray(q, dtype=np.uint8)]
 
 
@@ -135,6 +139,8 @@ def fp8_dequantize(b: np.ndarray) -> np.ndarray:
 # ---------------------------------------------------------------------------
 
 def to_acc(v: np.ndarray, dtype: str) -> np.ndarray:
+    """Payload -> binary32 accumulation values (every input of a reduce step
+    is decoded before the fold)."""
     if dtype == "bf16":
         return bf16_to_f32(v)
     if dtype == "fp8":
@@ -143,6 +149,8 @@ def to_acc(v: np.ndarray, dtype: str) -> np.ndarray:
 
 
 def from_acc(a: np.ndarray, dtype: str) -> np.ndarray:
+    """binary32 accumulation values -> payload (one encoding per reduce
+    step)."""
     if dtype == "bf16":
         return f32_to_bf16(a)
     if dtype == "fp8":

@@ -37,15 +37,20 @@ QUANTUM = {"f32": 4, "i32": 4, "bf16": 8, "fp8": 1}
 
 @dataclass(frozen=True)
 class Ref:
+    """A location: an element offset into a named buffer (the paper's
+    ``sendbuf + offset`` of Listing 1)."""
     key: tuple
     off: int
 
     def shift(self, k: int) -> "Ref":
+        """The location ``k`` elements further (pointer arithmetic of Listing 1)."""
         return Ref(self.key, self.off + k)
 
 
 @dataclass
 class Multicast:
+    """M(i, j, d) of Sec. 3.1: root i's source range replicated into every
+    leaf's destination range."""
     root: int
     leaves: tuple
     count: int
@@ -57,6 +62,8 @@ class Multicast:
 
 @dataclass
 class Reduction:
+    """R(i, j, d, op) of Sec. 3.1: the leaves' source ranges combined into
+    the root's destination range."""
     leaves: tuple
     root: int
     count: int
@@ -69,6 +76,8 @@ class Reduction:
 
 @dataclass
 class Program:
+    """A composed collective (Sec. 3.2, Listing 1): buffers and epochs of
+    primitives separated by fences."""
     P: int
     dtype: str = "f32"
     buffers: dict = field(default_factory=dict)     # key -> length (elements)
@@ -76,22 +85,27 @@ class Program:
 
     # -- registration (Listing 1) ------------------------------------------
     def buffer(self, key, length: int) -> Ref:
+        """A named per-rank buffer of ``n`` units (a user buffer of Listing 1)."""
         self.buffers[key] = int(length)
         return Ref(key, 0)
 
     def multicast(self, root: int, leaves, count: int, src: Ref, dsts: dict) -> None:
+        """Register M(root, leaves, count) in the current epoch (Sec. 3.1)."""
         self.epochs[-1].append(Multicast(int(root), tuple(sorted(int(j) for j in leaves)),
                                          int(count), src, dict(dsts)))
 
     def reduction(self, leaves, root: int, count: int, srcs: dict, dst: Ref, op: str = "sum") -> None:
+        """Register R(leaves, root, count, op) in the current epoch (Sec. 3.1)."""
         self.epochs[-1].append(Reduction(tuple(sorted(int(i) for i in leaves)), int(root),
                                          int(count), dict(srcs), dst, op))
 
     def fence(self) -> None:
+        """Close the current epoch (Sec. 3.3)."""
         self.epochs.append([])
 
     @property
     def primitives(self):
+        """All primitives with their epoch indices, in registration order."""
         return [p for ep in self.epochs for p in ep]
 
     def allocate(self, fill=None) -> dict:

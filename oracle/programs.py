@@ -29,7 +29,7 @@ def _all(P):
 # ---- single-step (Table 2, Single) --------------------------------------------
 
 def broadcast(P, d, root=0, dtype="f32"):
-    """M(i, U, dp)."""
+    """M(i, U, dp) (Table 2)."""
     prog = Program(P, dtype)
     send, recv = _bufs(prog, P, d * P, d * P)
     prog.multicast(root, _all(P), d * P, send[root], {r: recv[r] for r in range(P)})
@@ -37,7 +37,7 @@ def broadcast(P, d, root=0, dtype="f32"):
 
 
 def reduce(P, d, root=0, dtype="f32", op="sum"):
-    """R(U, j, dp, op)."""
+    """R(U, j, dp, op) (Table 2)."""
     prog = Program(P, dtype)
     send, recv = _bufs(prog, P, d * P, d * P)
     prog.reduction(_all(P), root, d * P, {r: send[r] for r in range(P)}, recv[root], op)
@@ -45,7 +45,7 @@ def reduce(P, d, root=0, dtype="f32", op="sum"):
 
 
 def allgather(P, d, dtype="f32"):
-    """sum_i M(i, U, d)."""
+    """sum_i M(i, U, d) (Table 2)."""
     prog = Program(P, dtype)
     send, recv = _bufs(prog, P, d, d * P)
     for i in range(P):
@@ -54,7 +54,7 @@ def allgather(P, d, dtype="f32"):
 
 
 def reducescatter(P, d, dtype="f32", op="sum"):
-    """sum_j R(U, j, d, op)."""
+    """sum_j R(U, j, d, op) (Table 2)."""
     prog = Program(P, dtype)
     send, recv = _bufs(prog, P, d * P, d)
     for j in range(P):
@@ -72,7 +72,7 @@ def allreduce_single(P, d, dtype="f32", op="sum"):
 
 
 def scatter(P, d, root=0, dtype="f32"):
-    """sum_j R(i, j, d): single-leaf reductions, i.e. point-to-point."""
+    """sum_j R(i, j, d): single-leaf reductions, i.e. point-to-point (Table 2)."""
     prog = Program(P, dtype)
     send, recv = _bufs(prog, P, d * P, d)
     for j in range(P):
@@ -81,7 +81,7 @@ def scatter(P, d, root=0, dtype="f32"):
 
 
 def gather(P, d, root=0, dtype="f32"):
-    """sum_i M(i, j, d)."""
+    """sum_i M(i, j, d) (Table 2)."""
     prog = Program(P, dtype)
     send, recv = _bufs(prog, P, d, d * P)
     for i in range(P):
@@ -90,7 +90,7 @@ def gather(P, d, root=0, dtype="f32"):
 
 
 def alltoall(P, d, dtype="f32"):
-    """sum_i sum_j M(i, j, d)."""
+    """sum_i sum_j M(i, j, d) (Table 2)."""
     prog = Program(P, dtype)
     send, recv = _bufs(prog, P, d * P, d * P)
     for i in range(P):

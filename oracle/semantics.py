@@ -189,7 +189,7 @@ def run_program(prog: Program, mem: dict, hierarchy, ring: int = 1) -> dict:
 # ---------------------------------------------------------------------------
 
 def accesses(p) -> tuple[list, list]:
-    """(reads, writes) of a primitive as (key, lo, hi) element ranges."""
+    """(reads, writes) of a primitive as (key, lo, hi) element ranges (Sec. 3.2)."""
     if isinstance(p, Multicast):
         reads = [(p.src.key, p.src.off, p.src.off + p.count)]
         writes = []
@@ -242,41 +242,50 @@ def _chunks(v: np.ndarray, P: int):
 
 
 def def_broadcast(x, root):
+    """Table 2, Broadcast: y_r = x_root for every r."""
     return [x[root].copy() for _ in range(len(x))]
 
 
 def def_reduce(x, root, hierarchy, dtype=None):
-    """Only the root's result is defined; other ranks' y are untouched (None)."""
+    """Table 2, Reduce: only the root's result is defined; other ranks' y are
+    untouched (None)."""
     y = [None] * len(x)
     y[root] = nested_fold({r: x[r] for r in range(len(x))}, hierarchy, dtype)
     return y
 
 
 def def_allgather(x):
+    """Table 2, All-gather: chunk i of y_r = x_i."""
     return [np.concatenate(x) for _ in range(len(x))]
 
 
 def def_reducescatter(x, hierarchy, dtype=None):
+    """Table 2, Reduce-scatter: y_j = sum over r of chunk j of x_r (the
+    nested fold)."""
     P = len(x)
     return [nested_fold({r: _chunks(x[r], P)[j] for r in range(P)}, hierarchy, dtype) for j in range(P)]
 
 
 def def_allreduce(x, hierarchy, dtype=None):
+    """Table 2, All-reduce: y_r = sum over r' of x_r' (the nested fold)."""
     s = nested_fold({r: x[r] for r in range(len(x))}, hierarchy, dtype)
     return [s.copy() for _ in range(len(x))]
 
 
 def def_scatter(x, root):
+    """Table 2, Scatter: y_j = chunk j of x_root."""
     return [c.copy() for c in _chunks(x[root], len(x))]
 
 
 def def_gather(x, root):
+    """Table 2, Gather: chunk i of y_root = x_i."""
     y = [None] * len(x)
     y[root] = np.concatenate(x)
     return y
 
 
 def def_alltoall(x):
+    """Table 2, All-to-all: chunk i of y_j = chunk j of x_i."""
     P = len(x)
     ch = [_chunks(x[i], P) for i in range(P)]
     return [np.concatenate([ch[i][j] for i in range(P)]) for j in range(P)]

@@ -39,6 +39,8 @@ def execute_op(op, mem: dict, dtype: str | None = None) -> None:
 
 
 def topo_order(plan: Plan, seed: int | None):
+    """A random order of the steps that respects every dependency (any such
+    order is a valid execution, Sec. 3.3); emission order for seed None."""
     n = len(plan.ops)
     if seed is None:
         return list(range(n))
