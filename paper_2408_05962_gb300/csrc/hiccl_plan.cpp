@@ -96,6 +96,9 @@ void run_parallel(int n, F &&fn) {
   for (auto &x : th) x.join();
 }
 
+// Emits the point-to-point steps of the registered primitives (Sec. 4):
+// striping, then the ring across nodes, then the tree inside them, one piece
+// (branch, pipeline channel) at a time.
 struct Builder {
   const hiccl_comm &c;
   std::vector<int> h;
@@ -288,13 +291,17 @@ struct Builder {
   }
   static Span span_of(const std::vector<int> &v) { return Span{v.data(), v.data() + v.size(), -1}; }
   // the representative of subgroup [qbase, qbase + sub) for `holder`: the rank
-  // at the holder's offset if it is a leaf, else the lowest leaf
+  // at the holder's offset if it is a leaf, else the lowest leaf (Sec. 4.2-4.3,
+  // the g0->g6, g0->g3, g6->g9 hops of the {2,2,3} example)
   static int pick_rep(long long qbase, long long sub, int holder, const Span &ql) {
     int cand = (int)(qbase + holder % sub);
     if (cand != ql.skip && holds(ql, cand)) return cand;
     return *ql.b != ql.skip ? *ql.b : ql.b[1];
   }
 
+  // the s branch roots of a primitive (Sec. 4.3): offsets o, o+1, ..., o+s-1
+  // (mod G) of the root's smallest enclosing group of G >= s ranks; a primitive
+  // whose leaves all lie in that group is not striped
   std::vector<int> stripe_ranks(int root, const std::vector<int> &leaves) const {
     if (s == 1) return {root};
     int l = L;
@@ -312,7 +319,7 @@ struct Builder {
 
   // ---- multicast tree: deliver from `holder` to every rank of `leaves` ---------
   // One hop per level from the holder to the representatives of its sibling
-  // subgroups (ascending), then the same inside every subgroup.
+  // subgroups (ascending), then the same inside every subgroup (Sec. 4.2).
   void mcast_tree(int l, long long base, int holder, Loc src, int src_step, Span leaves) {
     if (l == L || leaves.empty()) return;
     const long long sub = G[l + 1];
@@ -353,6 +360,9 @@ struct Builder {
   }
 
   // ---- reduction tree: fold `leaves` at `target`; returns (location, producer) ----
+  // The mirror of the multicast tree (Sec. 4.2): every subgroup's partial is
+  // formed at its representative, and a node folds its subgroups' partials
+  // in ascending order in one reduce step.
   std::pair<Loc, int> red_tree(int l, long long base, int target, Span leaves, const Loc *out) {
     if (l == L) {
       Loc ref = send_loc(target);
@@ -478,6 +488,8 @@ struct Builder {
     return {dst, emit(OP_COPY, &inc.first, 1, &dst, 1, level_of(inc_rank, target), &inc.second, 1)};
   }
 
+  // piece boundaries (Sec. 4.5): count cut into `parts` pieces at
+  // min(count, roundup(ceil(count * k / parts), q)), q the 16-byte quantum
   std::vector<unsigned long long> bounds(size_t count, int parts) const {
     unsigned long long q = quantum_of(c.dtype);
     std::vector<unsigned long long> b(parts + 1);
@@ -490,6 +502,8 @@ struct Builder {
     return b;
   }
 
+  // M(root, leaves, count) (Sec. 3.1) as s striped branches of m channels:
+  // stage 0 copies piece b to stripe rank k_b, which multicasts it (Sec. 4.3)
   void multicast(const Prim &pr) {
     std::vector<int> ks = stripe_ranks(pr.root, pr.leaves);
     int nb = (int)ks.size();
@@ -529,6 +543,8 @@ struct Builder {
     }
   }
 
+  // R(leaves, root, count) (Sec. 3.1), the mirror: piece b is reduced at
+  // stripe rank k_b and copied to the root (Sec. 4.3)
   void reduction(const Prim &pr) {
     std::vector<int> ks = stripe_ranks(pr.root, pr.leaves);
     int nb = (int)ks.size();
