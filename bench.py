@@ -126,6 +126,31 @@ class cpus_of_node:
         return False
 
 
+def host_copy_rates(h_send, h_recv, bufs, kinds, stream, device):
+    """GB/s of one plain pass of the end-to-end leg's copies, alone: every
+    send buffer host -> device, then every receive buffer device -> host
+    (CUDA events on one stream).  The end-to-end figure cannot exceed what the
+    host link gives here; None where the measurement fails."""
+    import torch
+    try:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize(device)
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            for k in kinds:
+                bufs[k].send.copy_(h_send[k], non_blocking=True)
+            ev[1].record(stream)
+            for k in kinds:
+                h_recv[k].copy_(bufs[k].recv, non_blocking=True)
+            ev[2].record(stream)
+        ev[2].synchronize()
+        hb = sum(t.numel() * t.element_size() for t in h_send.values())
+        db = sum(t.numel() * t.element_size() for t in h_recv.values())
+        return {"h2d_gbs": hb / (ev[0].elapsed_time(ev[1]) * 1e6), "d2h_gbs": db / (ev[1].elapsed_time(ev[2]) * 1e6)}
+    except Exception:   # a report field only: never fail the benchmark for it
+        return {"h2d_gbs": None, "d2h_gbs": None}
+
+
 # ---------------------------------------------------------------------------
 # multi-rank plumbing (replicas): barrier and max over ranks
 # ---------------------------------------------------------------------------
@@ -546,6 +571,7 @@ def run_ours(args):
         torch.cuda.synchronize(device)
     e2e_s = time.perf_counter() - t_e2e
     eb, es = aggregate(step_bytes * e2e_steps, e2e_s, device)
+    host_link = host_copy_rates(h_send, h_recv, bufs, kinds, s_in, device)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "seven":
@@ -584,7 +610,7 @@ def run_ours(args):
                      "schedule_bytes_per_launch": step_bytes / len(kinds), "kernel": "hiccl_exec_kernel"},
         "clocks": clk, "gpu_launches": len(kinds) * args.steps * world,
         "e2e": {"value": eb / es / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "host_numa_node": numa},
+                "host_numa_node": numa, **host_link},
         "collectives": coll, "wall_ms_per_step": wall / args.steps * 1e3,
         "cpu_baseline": cpu,
     }
