@@ -66,3 +66,15 @@ def test_affinity_set_and_restored(tmp_path):
         assert os.sched_getaffinity(0) == before
     with bench.cpus_of_node(7, sysfs=str(tmp_path)):      # no such node
         assert os.sched_getaffinity(0) == before
+
+
+def test_host_copy_rates_never_fail_the_bench():
+    """The host-link report is a side field: where it cannot be measured (here:
+    no GPU) it reports None instead of raising."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("measures on a GPU")
+    t = {"x": torch.zeros(4)}
+    bufs = {"x": types.SimpleNamespace(send=torch.zeros(4), recv=torch.zeros(4))}
+    out = bench.host_copy_rates(t, t, bufs, ["x"], None, "cpu")
+    assert out == {"h2d_gbs": None, "d2h_gbs": None}
