@@ -174,7 +174,11 @@ struct Builder {
     unsigned long long ns = 0, nl = 0;
     for (const Prim &pr : prims) {
       if (!pr.count) continue;
-      const unsigned long long n = pr.leaves.size(), pieces = (unsigned long long)s * (unsigned long long)m;
+      // at most s*m pieces, and no more than the count has quanta
+      const unsigned long long q = quantum_of(c.dtype);
+      const unsigned long long n = pr.leaves.size(),
+                               pieces = std::min<unsigned long long>((unsigned long long)s * (unsigned long long)m,
+                                                                     (pr.count + q - 1) / q);
       const unsigned long long st = std::min<unsigned long long>(n, nodes) + 2;
       ns += pieces * st;
       nl += pieces * (n + 2 * st + 4);
