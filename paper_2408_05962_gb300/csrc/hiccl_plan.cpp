@@ -779,20 +779,28 @@ unsigned long long table_bytes(const Plan &p) {
 }
 
 void build_image(const Plan &p, unsigned long long relay_base, TableImage &im) {
-  const size_t N = p.steps.size();
-  im.ptrs.resize(p.locs.size());
-  for (size_t k = 0; k < p.locs.size(); ++k)
-    im.ptrs[k] = p.locs[k].scratch ? relay_base + p.locs[k].addr : p.locs[k].addr;
+  const size_t N = p.steps.size(), NL = p.locs.size();
+  const size_t NI = p.item_off.empty() ? 0 : p.item_off.size() - 1;
+  // large plans fill the arrays on several host threads (disjoint ranges)
+  const int nthr = (NI >= 32768 || NL >= (1u << 22))
+                       ? (int)std::min<size_t>(8, std::max(1u, std::thread::hardware_concurrency()))
+                       : 1;
+  im.ptrs.resize(NL);
+  run_parallel(nthr, [&](int t) {
+    for (size_t k = NL * t / nthr; k < NL * (t + 1) / nthr; ++k)
+      im.ptrs[k] = p.locs[k].scratch ? relay_base + p.locs[k].addr : p.locs[k].addr;
+  });
   std::vector<uint32_t> meta(N);
   im.indeg.resize(N);
-  for (size_t i = 0; i < N; ++i) {
-    const HStep &st = p.steps[i];
-    im.indeg[i] = p.pred_off[i + 1] - p.pred_off[i];
-    bool al = true;
-    for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k) al = al && (im.ptrs[st.loc0 + k] % 16 == 0);
-    meta[i] = meta_pack(st.kind, st.dtype, al ? 1u : 0u, st.nsrc, st.ndst, st.rop);
-  }
-  const size_t NI = p.item_off.empty() ? 0 : p.item_off.size() - 1;
+  run_parallel(nthr, [&](int t) {
+    for (size_t i = N * t / nthr; i < N * (t + 1) / nthr; ++i) {
+      const HStep &st = p.steps[i];
+      im.indeg[i] = p.pred_off[i + 1] - p.pred_off[i];
+      bool al = true;
+      for (uint32_t k = 0; k < st.nsrc + st.ndst; ++k) al = al && (im.ptrs[st.loc0 + k] % 16 == 0);
+      meta[i] = meta_pack(st.kind, st.dtype, al ? 1u : 0u, st.nsrc, st.ndst, st.rop);
+    }
+  });
   im.items.assign(NI, DevItem{});
   // pass 1: record sizes and offsets (the inline-pointer decision is the same
   // in both passes: entries in order while the step's operands fit)
@@ -850,12 +858,7 @@ void build_image(const Plan &p, unsigned long long relay_base, TableImage &im) {
       }
     }
   };
-  const size_t nthr = NI >= 32768 ? std::min<size_t>(8, std::max(1u, std::thread::hardware_concurrency())) : 1;
-  if (nthr <= 1) {
-    fill(0, NI);
-  } else {
-    run_parallel((int)nthr, [&](int t) { fill(NI * t / nthr, NI * (t + 1) / nthr); });
-  }
+  run_parallel(nthr, [&](int t) { fill(NI * t / nthr, NI * (t + 1) / nthr); });
 }
 
 
