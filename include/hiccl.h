@@ -323,6 +323,22 @@ hiccl_status_t hiccl_get_trace(hiccl_comm_t comm, unsigned long long *out, size_
  * first violation in hiccl_last_error; HICCL_ERR_STATE without a plan. */
 hiccl_status_t hiccl_validate(hiccl_comm_t comm);
 
+/* Inspection: the executor's table image of a planned communicator, built on
+ * the host exactly as hiccl_init uploads it but with relay operands as
+ * offsets into the relay arena (relay base 0).  `recs` receives the
+ * work-item records (16-byte aligned, `*recs_bytes` in all) and `items` the
+ * 32-byte item descriptors in ticket order (`*nitems` of them); a record
+ * holds, at 16-byte aligned offsets: nent entries {step, meta, pointer
+ * offset, dependency count} (u32 each); nrun + 1 prefix sums of the runs'
+ * segment counts (u32); nrun runs {entry u32, pad u32, byte offset u64,
+ * bytes u64}; nptr inline operand pointers (u64); the completion section
+ * (u32): per entry its step's completion target, nent + 1 successor-list
+ * offsets, then the successors (absent when the item's descriptor says
+ * 0xffffffff).  With NULL buffers (or too small capacities, in bytes) only
+ * the sizes are returned.  HICCL_ERR_STATE without a plan. */
+hiccl_status_t hiccl_debug_image(hiccl_comm_t comm, void *recs, size_t recs_capacity, size_t *recs_bytes,
+                                 void *items, size_t items_capacity, size_t *nitems);
+
 /* Host-side fault injection for tests of hiccl_validate: corrupt the host
  * copy of a planned (hiccl_plan, not uploaded) table.  what = 0: make a step
  * depend on a later step (a cycle); 1: move a user-buffer operand out of its

@@ -1652,6 +1652,22 @@ hiccl_status_t hiccl_validate(hiccl_comm_t c) {
   });
 }
 
+hiccl_status_t hiccl_debug_image(hiccl_comm_t c, void *recs, size_t recs_capacity, size_t *recs_bytes,
+                                 void *items, size_t items_capacity, size_t *nitems) {
+  return guarded(c, [&]() -> hiccl_status_t {
+    if (!c) return HICCL_ERR_INVALID;
+    if (!c->plan.valid) return fail(c, HICCL_ERR_STATE, "not planned");
+    TableImage im;
+    build_image(c->plan, 0, im);
+    if (recs_bytes) *recs_bytes = im.recs.size();
+    if (nitems) *nitems = im.items.size();
+    if (recs && recs_capacity >= im.recs.size()) std::memcpy(recs, im.recs.data(), im.recs.size());
+    if (items && items_capacity >= im.items.size() * sizeof(DevItem))
+      std::memcpy(items, im.items.data(), im.items.size() * sizeof(DevItem));
+    return HICCL_OK;
+  });
+}
+
 hiccl_status_t hiccl_debug_corrupt(hiccl_comm_t c, int what) {
   return guarded(c, [&]() -> hiccl_status_t {
     if (!c) return HICCL_ERR_INVALID;

@@ -103,6 +103,9 @@ _SIGS = {
     "hiccl_level_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]),
     "hiccl_hbm_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong),
                                        ctypes.POINTER(ctypes.c_ulonglong)]),
+    "hiccl_debug_image": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                            ctypes.POINTER(ctypes.c_size_t), ctypes.c_void_p, ctypes.c_size_t,
+                                            ctypes.POINTER(ctypes.c_size_t)]),
     "hiccl_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]),
     "hiccl_get_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_ulonglong, ctypes.POINTER(StepDesc),
                                       ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_int),
@@ -246,6 +249,20 @@ def hiccl_plan_info(comm) -> dict:
     return info.as_dict()
 
 
+def hiccl_debug_image(comm):
+    """(records, items): the host-built table image of a planned communicator
+    as bytes and a (nitems, 8) uint32 array of item descriptors (rec, nent,
+    nrun, nptr, nsucc, pad...)."""
+    import numpy as np
+    rb, ni = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    _check(comm, lib().hiccl_debug_image(comm, None, 0, ctypes.byref(rb), None, 0, ctypes.byref(ni)))
+    recs = (ctypes.c_ubyte * max(rb.value, 1))()
+    items = (ctypes.c_uint32 * max(8 * ni.value, 1))()
+    _check(comm, lib().hiccl_debug_image(comm, recs, rb.value, ctypes.byref(rb), items, 32 * ni.value,
+                                         ctypes.byref(ni)))
+    return bytes(recs)[:rb.value], np.frombuffer(bytes(items), dtype=np.uint32)[:8 * ni.value].reshape(-1, 8)
+
+
 def hiccl_get_step(comm, index: int) -> dict:
     d = StepDesc()
     _check(comm, lib().hiccl_get_step(comm, int(index), ctypes.byref(d), None, None, None, None, None,
@@ -379,6 +396,9 @@ class Comm:
 
     def plan_info(self):
         return hiccl_plan_info(self.handle)
+
+    def image(self):
+        return hiccl_debug_image(self.handle)
 
     def step(self, i):
         return hiccl_get_step(self.handle, i)

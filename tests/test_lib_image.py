@@ -1,0 +1,144 @@
+"""The executor's table image, decoded on the host (no GPU): every work-item
+record built for upload is checked against the library's own step table --
+entries and their meta words, dependency counts, inline operand pointers,
+run prefix sums, completion targets and successor lists -- so that the
+encoding the kernel reads is tested without running the kernel."""
+import struct
+
+import numpy as np
+import pytest
+
+from oracle import programs as PR
+from paper_2408_05962_gb300 import build as B
+from paper_2408_05962_gb300 import hiccl as H
+from tests._bridge import FakeAddresses, register
+
+PTR_GLOBAL = 0x80000000
+SUCC_GLOBAL = 0xFFFFFFFF
+PTR_STEP_MAX, PTR_CAP, SUCC_CAP = 64, 160, 128
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def _r16(n):
+    return (n + 15) & ~15
+
+
+def _decode(recs, items):
+    """Per item: its entries, run prefix sums, runs, inline pointers and
+    completion section, from the layout the header documents."""
+    out = []
+    for rec, nent, nrun, nptr, nsucc, *_ in items.tolist():
+        o = rec * 16
+        ent = [struct.unpack_from("<4I", recs, o + 16 * k) for k in range(nent)]
+        o += nent * 16
+        rpre = list(struct.unpack_from(f"<{nrun + 1}I", recs, o))
+        o += _r16((nrun + 1) * 4)
+        runs = [struct.unpack_from("<IIQQ", recs, o + 24 * k) for k in range(nrun)]
+        o += _r16(nrun * 24)
+        ptr = list(struct.unpack_from(f"<{nptr}Q", recs, o))
+        o += _r16(nptr * 8)
+        ncmp = 2 * nent + 1 + (0 if nsucc == SUCC_GLOBAL else nsucc)
+        cmp = list(struct.unpack_from(f"<{ncmp}I", recs, o))
+        out.append(dict(ent=ent, rpre=rpre, runs=runs, ptr=ptr, cmp=cmp, nsucc=nsucc, nent=nent))
+    return out
+
+
+def _check_image(comm, dtype_code, seg):
+    steps = comm.steps()
+    N = len(steps)
+    recs, items = comm.image()
+    assert len(items) == comm.plan_info()["items"]
+    succ = [[] for _ in range(N)]
+    for i, st in enumerate(steps):
+        for q in st["preds"]:
+            succ[q].append(i)
+    dec = _decode(recs, items)
+    # every step is covered by its entries; count them (completion targets)
+    cover = np.zeros(N, dtype=np.int64)
+    for it in dec:
+        for e in it["ent"]:
+            cover[e[0]] += 1
+    assert (cover > 0).all()
+    last_slot = -1
+    for it in dec:
+        nent, nptr_used = it["nent"], 0
+        assert 1 <= nent <= 64
+        slots = {steps[e[0]]["slot"] for e in it["ent"]}
+        assert len(slots) == 1                         # one pipeline slot per item
+        assert min(slots) >= last_slot                 # tickets in slot order
+        last_slot = min(slots)
+        total_succ = 0
+        for k, (step, meta, poff, indeg) in enumerate(it["ent"]):
+            st = steps[step]
+            ops = [a for (_, a, _) in st["srcs"]] + [a for (_, a, _) in st["dsts"]]
+            assert meta & 3 == (0 if st["kind"] == "copy" else 1)
+            assert (meta >> 2) & 15 == dtype_code
+            assert (meta >> 6) & 1 == int(all(a % 16 == 0 for a in ops))
+            if st["kind"] == "reduce":                  # (a copy ignores the operator field)
+                assert (meta >> 7) & 7 == H.OPS[st["op"]]
+            assert (meta >> 10) & 2047 == len(st["srcs"]) and (meta >> 21) & 2047 == len(st["dsts"])
+            assert indeg == len(st["preds"])
+            if poff & PTR_GLOBAL:
+                # kept global: too many operands, or the item's inline space is used up
+                assert len(ops) > PTR_STEP_MAX or nptr_used + len(ops) > PTR_CAP
+            else:
+                assert poff == nptr_used
+                assert it["ptr"][poff:poff + len(ops)] == ops
+                nptr_used += len(ops)
+            assert it["cmp"][k] == cover[step]          # completion target
+            total_succ += len(succ[step])
+        assert len(it["ptr"]) == nptr_used
+        # runs: prefix sums of their segment counts; first entries in range
+        for r, (entry, _, off, nbytes) in enumerate(it["runs"]):
+            assert entry < nent and nbytes > 0
+            assert it["rpre"][r + 1] - it["rpre"][r] == -(-nbytes // seg)
+        assert it["rpre"][0] == 0
+        # successor section
+        if it["nsucc"] == SUCC_GLOBAL:
+            assert total_succ > SUCC_CAP
+        else:
+            assert it["nsucc"] == total_succ
+            soff = it["cmp"][nent:2 * nent + 1]
+            lists = it["cmp"][2 * nent + 1:]
+            assert soff[0] == 0 and soff[-1] == total_succ
+            for k, e in enumerate(it["ent"]):
+                assert lists[soff[k]:soff[k + 1]] == sorted(succ[e[0]])
+
+
+@pytest.mark.parametrize("name", PR.SEVEN + ("reduce",))
+@pytest.mark.parametrize("P,h,s,m", [(8, [2, 4], 2, 2), (16, [4, 4], 4, 3), (64, [4, 4, 4], 4, 8)])
+def test_table_image_matches_the_step_table(name, P, h, s, m):
+    prog = PR.BUILDERS[name](P, 4096 if P == 64 else 700)
+    fake = FakeAddresses(prog)
+    comm = register(prog, fake.addr)
+    comm.plan(h, s, m)
+    _check_image(comm, H.DTYPES["f32"], 4096)
+
+
+@pytest.mark.parametrize("dtype,seg", [("bf16", 4096), ("fp8", 4032), ("i32", 4096)])
+def test_table_image_payloads_and_operators(dtype, seg):
+    for name, op in (("allreduce", "sum"), ("reducescatter", "max" if dtype != "fp8" else "sum")):
+        if dtype == "fp8" and name != "allreduce":
+            continue
+        prog = PR.BUILDERS[name](16, 1024, dtype=dtype, op=op)
+        fake = FakeAddresses(prog)
+        comm = register(prog, fake.addr)
+        comm.plan([4, 4], 2, 2)
+        _check_image(comm, H.DTYPES[dtype], seg)
+
+
+def test_table_image_wide_steps_keep_pointers_global():
+    """A 64-way reduce has 65 operands: its pointers stay in the global array."""
+    prog = PR.reduce(64, 64)
+    fake = FakeAddresses(prog)
+    comm = register(prog, fake.addr)
+    comm.plan([64], 1, 1)
+    recs, items = comm.image()
+    dec = _decode(recs, items)
+    wide = [e for it in dec for e in it["ent"] if ((e[1] >> 10) & 2047) + ((e[1] >> 21) & 2047) > PTR_STEP_MAX]
+    assert wide and all(e[2] & PTR_GLOBAL for e in wide)
+    _check_image(comm, H.DTYPES["f32"], 4096)
