@@ -107,3 +107,74 @@ def interpret(comm: H.Comm, fake: FakeAddresses, mem: dict, dtype: str) -> dict:
                 acc = combine(acc, view(s, n).copy().view(dt), op)
             view(st["dsts"][0], n)[...] = acc.view(np.uint8)
     return mem
+
+
+def interpret_image(comm: H.Comm, fake: FakeAddresses, mem: dict, dtype: str) -> dict:
+    """Run the library's *table image* -- the work-item records the executor
+    reads (``hiccl_debug_image``) -- on the NumPy buffers ``mem``, the way the
+    kernel walks it: items in ticket order, each item's segments through its
+    runs (segment j lies in the run with the largest prefix sum <= j, at byte
+    run.off + (j - prefix) * seg of that run's first entry's step), each
+    segment copied or folded with the operator and payload its meta word
+    gives.  Operand pointers come from the record when inline, else from the
+    step table (the global pointer array holds the same values)."""
+    import struct
+    from oracle.model import DTYPES as _DT
+    info = comm.plan_info()
+    seg = 4032 if dtype == "fp8" else 4096
+    dt = _DT[dtype]
+    byte_views = {k: v.view(np.uint8) for k, v in mem.items()}
+    scratch = np.zeros(info["scratch_bytes"] + 16, dtype=np.uint8)
+    lo_user = min(fake.base.values())
+    recs, items = comm.image()
+    steps = {}
+
+    def view(addr, n):
+        if addr < lo_user:                      # relay arena offset (relay base 0)
+            return scratch[addr:addr + n]
+        key, off = fake.resolve(addr)
+        return byte_views[key][off:off + n]
+
+    for rec, nent, nrun, nptr, nsucc, *_ in items.tolist():
+        o = rec * 16
+        ent = [struct.unpack_from("<4I", recs, o + 16 * k) for k in range(nent)]
+        o += nent * 16
+        rpre = list(struct.unpack_from(f"<{nrun + 1}I", recs, o))
+        o += ((nrun + 1) * 4 + 15) & ~15
+        runs = [struct.unpack_from("<IIQQ", recs, o + 24 * k) for k in range(nrun)]
+        o += (nrun * 24 + 15) & ~15
+        ptr = list(struct.unpack_from(f"<{nptr}Q", recs, o))
+        for j in range(rpre[nrun]):
+            k = max(r for r in range(nrun) if rpre[r] <= j)
+            entry, _, off, nbytes = runs[k]
+            step, meta, poff, _ = ent[entry]
+            ns, nd = (meta >> 10) & 2047, (meta >> 21) & 2047
+            if poff & 0x80000000:
+                if step not in steps:
+                    st = comm.step(step)
+                    steps[step] = [a for (_, a, _) in st["srcs"]] + [a for (_, a, _) in st["dsts"]]
+                ops = steps[step]
+            else:
+                ops = ptr[poff:poff + ns + nd]
+            s = j - rpre[k]
+            lo = off + s * seg
+            n = min(seg, nbytes - s * seg)
+            srcs = [view(a + lo, n) for a in ops[:ns]]
+            dsts = [view(a + lo, n) for a in ops[ns:]]
+            if meta & 3 == 0:
+                data = srcs[0].copy()
+                for d in dsts:
+                    d[...] = data
+                continue
+            op = H.OP_NAMES[(meta >> 7) & 7]
+            if dtype in ("bf16", "fp8"):
+                acc = to_acc(srcs[0].copy().view(dt), dtype).copy()
+                for x in srcs[1:]:
+                    acc = combine(acc, to_acc(x.copy().view(dt), dtype), op).astype(np.float32)
+                dsts[0][...] = from_acc(acc, dtype).view(np.uint8)
+            else:
+                acc = srcs[0].copy().view(dt)
+                for x in srcs[1:]:
+                    acc = combine(acc, x.copy().view(dt), op)
+                dsts[0][...] = acc.view(np.uint8)
+    return mem

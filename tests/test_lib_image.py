@@ -142,3 +142,46 @@ def test_table_image_wide_steps_keep_pointers_global():
     wide = [e for it in dec for e in it["ent"] if ((e[1] >> 10) & 2047) + ((e[1] >> 21) & 2047) > PTR_STEP_MAX]
     assert wide and all(e[2] & PTR_GLOBAL for e in wide)
     _check_image(comm, H.DTYPES["f32"], 4096)
+
+
+@pytest.mark.parametrize("name", PR.SEVEN + ("reduce",))
+@pytest.mark.parametrize("P,h,s,m,dtype", [(8, [2, 4], 2, 2, "f32"), (16, [4, 4], 4, 3, "i32"),
+                                           (12, [2, 2, 3], 3, 2, "bf16"), (16, [4, 4], 4, 2, "fp8")])
+def test_table_image_executed_on_the_host_equals_the_oracle(name, P, h, s, m, dtype):
+    """The image, executed segment by segment the way the kernel walks it
+    (ticket order is topological), gives the oracle's plain semantics bit
+    for bit: runs, segment offsets and record pointers are right."""
+    from oracle import semantics as S
+    from tests._bridge import interpret_image
+    from tests._cases import fill
+    d = 3 if dtype == "fp8" else 1500     # FP8 counts are 128-value blocks
+    prog = PR.BUILDERS[name](P, d, dtype=dtype)
+    fake = FakeAddresses(prog)
+    comm = register(prog, fake.addr)
+    comm.plan(h, s, m)
+    mem0 = fill(prog, 7)
+    ref = {k: v.copy() for k, v in mem0.items()}
+    S.run_program(prog, ref, h)
+    got = interpret_image(comm, fake, {k: v.copy() for k, v in mem0.items()}, dtype)
+    for k in ref:
+        assert np.array_equal(ref[k].view(np.uint8), got[k].view(np.uint8)), k
+
+
+@pytest.mark.parametrize("name", ["allreduce", "alltoall", "broadcast"])
+def test_table_image_executed_three_levels(name):
+    """The bench's machine, {4,4,4} with stripe 4 and pipeline 8, at a
+    reduced size: merged runs across channels and relays, executed from the
+    image, equal the oracle."""
+    from oracle import semantics as S
+    from tests._bridge import interpret_image
+    from tests._cases import fill
+    prog = PR.BUILDERS[name](64, 512)
+    fake = FakeAddresses(prog)
+    comm = register(prog, fake.addr)
+    comm.plan([4, 4, 4], 4, 8)
+    mem0 = fill(prog, 3)
+    ref = {k: v.copy() for k, v in mem0.items()}
+    S.run_program(prog, ref, [4, 4, 4])
+    got = interpret_image(comm, fake, {k: v.copy() for k, v in mem0.items()}, "f32")
+    for k in ref:
+        assert np.array_equal(ref[k].view(np.uint8), got[k].view(np.uint8)), k
