@@ -109,15 +109,23 @@ def interpret(comm: H.Comm, fake: FakeAddresses, mem: dict, dtype: str) -> dict:
     return mem
 
 
-def interpret_image(comm: H.Comm, fake: FakeAddresses, mem: dict, dtype: str) -> dict:
+def interpret_image(comm: H.Comm, fake: FakeAddresses, mem: dict, dtype: str, seed=None) -> dict:
     """Run the library's *table image* -- the work-item records the executor
     reads (``hiccl_debug_image``) -- on the NumPy buffers ``mem``, the way the
-    kernel walks it: items in ticket order, each item's segments through its
-    runs (segment j lies in the run with the largest prefix sum <= j, at byte
-    run.off + (j - prefix) * seg of that run's first entry's step), each
-    segment copied or folded with the operator and payload its meta word
-    gives.  Operand pointers come from the record when inline, else from the
-    step table (the global pointer array holds the same values)."""
+    kernel walks it: each item's segments through its runs (segment j lies in
+    the run with the largest prefix sum <= j, at byte run.off + (j - prefix) *
+    seg of that run's first entry's step), each segment copied or folded with
+    the operator and payload its meta word gives.  Operand pointers come from
+    the record when inline, else from the step table (the global pointer
+    array holds the same values).
+
+    Items run in ticket order, or with ``seed`` in a random order that only
+    the image's own dependency data constrain, as concurrent CTAs could run
+    them: an item is ready when every entry's step has as many released
+    predecessors as its dependency count; a step is complete when as many
+    items as its completion target have finished it, and then releases the
+    successors its record lists (or, for an item whose lists stay global,
+    the step table's)."""
     import struct
     from oracle.model import DTYPES as _DT
     info = comm.plan_info()
@@ -135,6 +143,7 @@ def interpret_image(comm: H.Comm, fake: FakeAddresses, mem: dict, dtype: str) ->
         key, off = fake.resolve(addr)
         return byte_views[key][off:off + n]
 
+    decoded = []
     for rec, nent, nrun, nptr, nsucc, *_ in items.tolist():
         o = rec * 16
         ent = [struct.unpack_from("<4I", recs, o + 16 * k) for k in range(nent)]
@@ -144,6 +153,61 @@ def interpret_image(comm: H.Comm, fake: FakeAddresses, mem: dict, dtype: str) ->
         runs = [struct.unpack_from("<IIQQ", recs, o + 24 * k) for k in range(nrun)]
         o += (nrun * 24 + 15) & ~15
         ptr = list(struct.unpack_from(f"<{nptr}Q", recs, o))
+        o += (nptr * 8 + 15) & ~15
+        ncmp = 2 * nent + 1 + (0 if nsucc == 0xFFFFFFFF else nsucc)
+        cmp = list(struct.unpack_from(f"<{ncmp}I", recs, o))
+        decoded.append((ent, rpre, runs, ptr, cmp, nsucc))
+
+    order = list(range(len(decoded)))
+    if seed is not None:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        N = info["steps"]
+        succ_table = None
+        dep = np.zeros(N, dtype=np.int64)
+        done = np.zeros(N, dtype=np.int64)
+        indeg = np.zeros(N, dtype=np.int64)
+        step_items = [[] for _ in range(N)]
+        wait = []                                   # entries of an item whose step is not yet released
+        for i, d in enumerate(decoded):
+            for e in d[0]:
+                indeg[e[0]] = e[3]
+                step_items[e[0]].append(i)
+            wait.append(sum(1 for e in d[0] if e[3] > 0))
+        ready = [i for i in range(len(decoded)) if wait[i] == 0]
+        order = []
+        while ready:
+            r = int(rng.integers(0, len(ready)))
+            ready[r], ready[-1] = ready[-1], ready[r]
+            i = ready.pop()
+            order.append(i)
+            ent, _, _, _, cmp, nsucc = decoded[i]
+            nent = len(ent)
+            for k, e in enumerate(ent):
+                done[e[0]] += 1
+                if done[e[0]] != cmp[k]:
+                    continue
+                if nsucc != 0xFFFFFFFF:
+                    soff = cmp[nent:2 * nent + 1]
+                    lst = cmp[2 * nent + 1:][soff[k]:soff[k + 1]]
+                else:
+                    if succ_table is None:
+                        succ_table = [[] for _ in range(N)]
+                        for t in range(N):
+                            for q in comm.step(t)["preds"]:
+                                succ_table[q].append(t)
+                    lst = succ_table[e[0]]
+                for t in lst:
+                    dep[t] += 1
+                    if dep[t] == indeg[t]:
+                        for it2 in step_items[t]:
+                            wait[it2] -= 1
+                            if wait[it2] == 0:
+                                ready.append(it2)
+        assert len(order) == len(decoded), "some items never became ready: the image's dependencies cannot all be met"
+
+    for idx in order:
+        ent, rpre, runs, ptr, _, _ = decoded[idx]
+        nrun = len(runs)
         for j in range(rpre[nrun]):
             k = max(r for r in range(nrun) if rpre[r] <= j)
             entry, _, off, nbytes = runs[k]

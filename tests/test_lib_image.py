@@ -185,3 +185,63 @@ def test_table_image_executed_three_levels(name):
     got = interpret_image(comm, fake, {k: v.copy() for k, v in mem0.items()}, "f32")
     for k in ref:
         assert np.array_equal(ref[k].view(np.uint8), got[k].view(np.uint8)), k
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+@pytest.mark.parametrize("name,P,h,s,m,ring", [("allreduce", 16, [4, 4], 4, 3, 1), ("alltoall", 12, [2, 2, 3], 3, 2, 1),
+                                               ("allreduce", 12, [4, 3], 3, 2, 4), ("reducescatter", 64, [4, 4, 4], 4, 8, 1),
+                                               ("broadcast_ag_scatter", 8, [2, 4], 2, 2, 1)])
+def test_table_image_in_random_dependency_order(seed, name, P, h, s, m, ring):
+    """Items executed in random orders that only the image's own dependency
+    counts, completion targets and successor lists allow -- as concurrent
+    CTAs may run them -- still give the oracle's result: the image carries
+    every dependency the data needs (tree edges and fences)."""
+    from oracle import semantics as S
+    from tests._bridge import interpret_image
+    from tests._cases import fill
+    prog = PR.BUILDERS[name](P, 256)
+    fake = FakeAddresses(prog)
+    comm = register(prog, fake.addr)
+    if ring > 1:
+        comm.set_option(H.OPT_RING, ring)
+    comm.plan(h, s, m)
+    mem0 = fill(prog, seed)
+    ref = {k: v.copy() for k, v in mem0.items()}
+    S.run_program(prog, ref, h, ring)
+    got = interpret_image(comm, fake, {k: v.copy() for k, v in mem0.items()}, "f32", seed=seed)
+    for k in ref:
+        assert np.array_equal(ref[k].view(np.uint8), got[k].view(np.uint8)), k
+
+
+def test_random_order_catches_a_missing_dependency():
+    """Sanity of the check above: with one dependency withheld from the
+    successor lists the host execution can diverge from the oracle, so the
+    random-order test would notice a missing edge."""
+    import struct
+    from oracle import semantics as S
+    from tests import _bridge
+    from tests._cases import fill
+    prog = PR.BUILDERS["allreduce"](8, 256)
+    fake = FakeAddresses(prog)
+    comm = register(prog, fake.addr)
+    comm.plan([2, 4], 1, 1)
+    recs, items = comm.image()
+    # release every step's successors as soon as it is claimed: drop all
+    # dependency counts to zero in a copy of the image
+    recs = bytearray(recs)
+    for rec, nent, *_ in items.tolist():
+        for k in range(nent):
+            struct.pack_into("<I", recs, rec * 16 + 16 * k + 12, 0)
+    orig = comm.image
+    comm.image = lambda: (bytes(recs), items)
+    try:
+        mem0 = fill(prog, 5)
+        ref = {k: v.copy() for k, v in mem0.items()}
+        S.run_program(prog, ref, [2, 4])
+        differs = False
+        for seed in range(8):
+            got = _bridge.interpret_image(comm, fake, {k: v.copy() for k, v in mem0.items()}, "f32", seed=seed)
+            differs |= any(not np.array_equal(ref[k].view(np.uint8), got[k].view(np.uint8)) for k in ref)
+        assert differs
+    finally:
+        comm.image = orig
