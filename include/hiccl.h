@@ -213,6 +213,12 @@ hiccl_status_t hiccl_autotune(hiccl_comm_t comm, void *cuda_stream, int flags, h
  * device), and the caller synchronizes replays on its stream. */
 hiccl_status_t hiccl_group(const hiccl_comm_t *comms, int n, hiccl_comm_t *out);
 
+/* The host half of hiccl_group: the same combined, checked table, left
+ * planned (not uploaded, nothing allocated on a device) for inspection
+ * (hiccl_plan_info, hiccl_get_step, hiccl_debug_image); it cannot be
+ * started.  Same arguments and errors as hiccl_group. */
+hiccl_status_t hiccl_group_plan(const hiccl_comm_t *comms, int n, hiccl_comm_t *out);
+
 /* ---- accounting -------------------------------------------------------------- */
 
 /* Bytes that cross each hierarchy level per execution: for every copy

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <numeric>
 #include <string>
@@ -1508,108 +1509,116 @@ hiccl_status_t hiccl_init(hiccl_comm_t c, const int *hierarchy, int nlevels, int
   });
 }
 
+// The union of the planned members' tables (see hiccl_group), planned on the
+// host and checked; not uploaded.  *out receives the new communicator.
+static hiccl_status_t group_build(const hiccl_comm_t *comms, int n, hiccl_comm **out) {
+  if (!comms || n < 1) return HICCL_ERR_INVALID;
+  unsigned long long segb = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!comms[i] || !comms[i]->plan.valid) return HICCL_ERR_STATE;
+    if (segb && comms[i]->plan.seg != segb) return HICCL_ERR_UNSUPPORTED;   // FP8 with other payloads
+    segb = comms[i]->plan.seg;
+  }
+  std::unique_ptr<hiccl_comm, void (*)(hiccl_comm_t)> owner(new (std::nothrow) hiccl_comm(), hiccl_destroy);
+  hiccl_comm *g = owner.get();
+  if (!g) return HICCL_ERR_NOMEM;
+  g->group = true;
+  g->P = comms[0]->P;
+  g->dtype = comms[0]->dtype;
+  g->esize = comms[0]->esize;
+  g->timeout_ns = comms[0]->timeout_ns;
+  g->ctas_per_sm = comms[0]->ctas_per_sm;
+  g->threads = comms[0]->threads;
+  Plan &P = g->plan;
+  P.seg = segb;
+  P.pred_off.push_back(0);
+  P.succ_off.push_back(0);
+  // member tables, concatenated; every member's relays move to its own range
+  struct ItemRef { unsigned long long slot; uint32_t rank; int member; uint32_t item; };
+  std::vector<ItemRef> items;
+  std::vector<uint32_t> step_off(n), entry_off(n), run_off(n);
+  unsigned long long relay_off = 0;
+  for (int i = 0; i < n; ++i) {
+    const Plan &q = comms[i]->plan;
+    const uint32_t so = (uint32_t)P.steps.size(), lo = (uint32_t)P.locs.size();
+    step_off[i] = so;
+    entry_off[i] = (uint32_t)P.entries.size();
+    run_off[i] = (uint32_t)P.runs.size();
+    for (HStep st : q.steps) {
+      st.loc0 += lo;
+      P.steps.push_back(st);
+    }
+    for (Loc l : q.locs) {
+      if (l.scratch) l.addr += relay_off;
+      P.locs.push_back(l);
+    }
+    for (size_t k = 0; k < q.steps.size(); ++k) {
+      for (uint32_t x = q.pred_off[k]; x < q.pred_off[k + 1]; ++x) P.preds.push_back(q.preds[x] + so);
+      P.pred_off.push_back((uint32_t)P.preds.size());
+      for (uint32_t x = q.succ_off[k]; x < q.succ_off[k + 1]; ++x) P.succ.push_back(q.succ[x] + so);
+      P.succ_off.push_back((uint32_t)P.succ.size());
+    }
+    P.nent.insert(P.nent.end(), q.nent.begin(), q.nent.end());
+    for (DevEntry e : q.entries) {
+      e.step += so;
+      P.entries.push_back(e);
+    }
+    P.runs.insert(P.runs.end(), q.runs.begin(), q.runs.end());
+    // rank of each item inside its slot, for interleaving the members
+    unsigned long long prev_slot = ~0ull;
+    uint32_t rank = 0;
+    for (size_t t = 0; t + 1 < q.item_off.size(); ++t) {
+      const unsigned long long sl = q.steps[q.entries[q.item_off[t]].step].slot;
+      rank = sl == prev_slot ? rank + 1 : 0;
+      prev_slot = sl;
+      items.push_back(ItemRef{sl, rank, i, (uint32_t)t});
+    }
+    relay_off = (relay_off + q.scratch_bytes + 255ull) & ~255ull;
+    P.hbm_read += q.hbm_read;
+    P.hbm_write += q.hbm_write;
+    P.stages = std::max(P.stages, q.stages);
+    P.slots = std::max(P.slots, q.slots);
+  }
+  P.scratch_bytes = relay_off;
+  // one ticket order for all: by slot, then round-robin over the members;
+  // each member keeps its own (topological) item order
+  std::stable_sort(items.begin(), items.end(), [](const ItemRef &a, const ItemRef &b) {
+    if (a.slot != b.slot) return a.slot < b.slot;
+    if (a.rank != b.rank) return a.rank < b.rank;
+    return a.member < b.member;
+  });
+  std::vector<DevEntry> ents;
+  std::vector<DevRun> runs;
+  P.item_off.assign(1, 0);
+  P.run_off.assign(1, 0);
+  for (const ItemRef &it : items) {
+    const Plan &q = comms[it.member]->plan;
+    for (uint32_t x = q.item_off[it.item]; x < q.item_off[it.item + 1]; ++x)
+      ents.push_back(P.entries[entry_off[it.member] + x]);
+    for (uint32_t x = q.run_off[it.item]; x < q.run_off[it.item + 1]; ++x) runs.push_back(P.runs[run_off[it.member] + x]);
+    P.item_off.push_back((uint32_t)ents.size());
+    P.run_off.push_back((uint32_t)runs.size());
+  }
+  P.entries.swap(ents);
+  P.runs.swap(runs);
+  P.valid = true;
+  {
+    std::string why;
+    if (!validate_plan(*g, P, why)) return HICCL_ERR_INVALID;
+  }
+  g->state = hiccl_comm::PLANNED;
+  *out = owner.release();
+  return HICCL_OK;
+}
+
 hiccl_status_t hiccl_group(const hiccl_comm_t *comms, int n, hiccl_comm_t *out) {
   return guarded(nullptr, [&]() -> hiccl_status_t {
     if (!out) return HICCL_ERR_INVALID;
     *out = nullptr;
-    if (!comms || n < 1) return HICCL_ERR_INVALID;
-    unsigned long long segb = 0;
-    for (int i = 0; i < n; ++i) {
-      if (!comms[i] || !comms[i]->plan.valid) return HICCL_ERR_STATE;
-      if (segb && comms[i]->plan.seg != segb) return HICCL_ERR_UNSUPPORTED;   // FP8 with other payloads
-      segb = comms[i]->plan.seg;
-    }
-    hiccl_comm *g = new (std::nothrow) hiccl_comm();
-    if (!g) return HICCL_ERR_NOMEM;
-    g->group = true;
-    g->P = comms[0]->P;
-    g->dtype = comms[0]->dtype;
-    g->esize = comms[0]->esize;
-    g->timeout_ns = comms[0]->timeout_ns;
-    g->ctas_per_sm = comms[0]->ctas_per_sm;
-    g->threads = comms[0]->threads;
-    Plan &P = g->plan;
-    P.seg = segb;
-    P.pred_off.push_back(0);
-    P.succ_off.push_back(0);
-    // member tables, concatenated; every member's relays move to its own range
-    struct ItemRef { unsigned long long slot; uint32_t rank; int member; uint32_t item; };
-    std::vector<ItemRef> items;
-    std::vector<uint32_t> step_off(n), entry_off(n), run_off(n);
-    unsigned long long relay_off = 0;
-    for (int i = 0; i < n; ++i) {
-      const Plan &q = comms[i]->plan;
-      const uint32_t so = (uint32_t)P.steps.size(), lo = (uint32_t)P.locs.size();
-      step_off[i] = so;
-      entry_off[i] = (uint32_t)P.entries.size();
-      run_off[i] = (uint32_t)P.runs.size();
-      for (HStep st : q.steps) {
-        st.loc0 += lo;
-        P.steps.push_back(st);
-      }
-      for (Loc l : q.locs) {
-        if (l.scratch) l.addr += relay_off;
-        P.locs.push_back(l);
-      }
-      for (size_t k = 0; k < q.steps.size(); ++k) {
-        for (uint32_t x = q.pred_off[k]; x < q.pred_off[k + 1]; ++x) P.preds.push_back(q.preds[x] + so);
-        P.pred_off.push_back((uint32_t)P.preds.size());
-        for (uint32_t x = q.succ_off[k]; x < q.succ_off[k + 1]; ++x) P.succ.push_back(q.succ[x] + so);
-        P.succ_off.push_back((uint32_t)P.succ.size());
-      }
-      P.nent.insert(P.nent.end(), q.nent.begin(), q.nent.end());
-      for (DevEntry e : q.entries) {
-        e.step += so;
-        P.entries.push_back(e);
-      }
-      P.runs.insert(P.runs.end(), q.runs.begin(), q.runs.end());
-      // rank of each item inside its slot, for interleaving the members
-      unsigned long long prev_slot = ~0ull;
-      uint32_t rank = 0;
-      for (size_t t = 0; t + 1 < q.item_off.size(); ++t) {
-        const unsigned long long sl = q.steps[q.entries[q.item_off[t]].step].slot;
-        rank = sl == prev_slot ? rank + 1 : 0;
-        prev_slot = sl;
-        items.push_back(ItemRef{sl, rank, i, (uint32_t)t});
-      }
-      relay_off = (relay_off + q.scratch_bytes + 255ull) & ~255ull;
-      P.hbm_read += q.hbm_read;
-      P.hbm_write += q.hbm_write;
-      P.stages = std::max(P.stages, q.stages);
-      P.slots = std::max(P.slots, q.slots);
-    }
-    P.scratch_bytes = relay_off;
-    // one ticket order for all: by slot, then round-robin over the members;
-    // each member keeps its own (topological) item order
-    std::stable_sort(items.begin(), items.end(), [](const ItemRef &a, const ItemRef &b) {
-      if (a.slot != b.slot) return a.slot < b.slot;
-      if (a.rank != b.rank) return a.rank < b.rank;
-      return a.member < b.member;
-    });
-    std::vector<DevEntry> ents;
-    std::vector<DevRun> runs;
-    P.item_off.assign(1, 0);
-    P.run_off.assign(1, 0);
-    for (const ItemRef &it : items) {
-      const Plan &q = comms[it.member]->plan;
-      for (uint32_t x = q.item_off[it.item]; x < q.item_off[it.item + 1]; ++x)
-        ents.push_back(P.entries[entry_off[it.member] + x]);
-      for (uint32_t x = q.run_off[it.item]; x < q.run_off[it.item + 1]; ++x) runs.push_back(P.runs[run_off[it.member] + x]);
-      P.item_off.push_back((uint32_t)ents.size());
-      P.run_off.push_back((uint32_t)runs.size());
-    }
-    P.entries.swap(ents);
-    P.runs.swap(runs);
-    P.valid = true;
-    {
-      std::string why;
-      if (!validate_plan(*g, P, why)) {
-        hiccl_destroy(g);
-        return HICCL_ERR_INVALID;
-      }
-    }
-    g->state = hiccl_comm::PLANNED;
-    hiccl_status_t st = dev_upload(g);
+    hiccl_comm *g = nullptr;
+    hiccl_status_t st = group_build(comms, n, &g);
+    if (st != HICCL_OK) return st;
+    st = dev_upload(g);
     if (st != HICCL_OK) {
       hiccl_destroy(g);
       return st;
@@ -1617,6 +1626,14 @@ hiccl_status_t hiccl_group(const hiccl_comm_t *comms, int n, hiccl_comm_t *out) 
     g->state = hiccl_comm::READY;
     *out = g;
     return HICCL_OK;
+  });
+}
+
+hiccl_status_t hiccl_group_plan(const hiccl_comm_t *comms, int n, hiccl_comm_t *out) {
+  return guarded(nullptr, [&]() -> hiccl_status_t {
+    if (!out) return HICCL_ERR_INVALID;
+    *out = nullptr;
+    return group_build(comms, n, out);
   });
 }
 

@@ -119,6 +119,8 @@ _SIGS = {
     "hiccl_run_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "hiccl_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(TuneResult)]),
     "hiccl_group": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "hiccl_group_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
     "hiccl_get_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_size_t,
                                        ctypes.POINTER(ctypes.c_size_t)]),
     "hiccl_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -337,6 +339,16 @@ def hiccl_group(comms: Sequence) -> int:
     return out.value
 
 
+def hiccl_group_plan(comms: Sequence) -> int:
+    """The same combined table as hiccl_group, planned on the host only."""
+    arr = (ctypes.c_void_p * len(comms))(*[c.handle if isinstance(c, Comm) else c for c in comms])
+    out = ctypes.c_void_p()
+    st = lib().hiccl_group_plan(arr, len(comms), ctypes.byref(out))
+    if st != OK:
+        raise HicclError(st, "hiccl_group_plan")
+    return out.value
+
+
 def hiccl_last_error(comm) -> str:
     return lib().hiccl_last_error(comm).decode()
 
@@ -360,6 +372,11 @@ class Comm:
     def group(cls, comms: Sequence["Comm"]) -> "Comm":
         """One communicator executing all of ``comms`` in a single launch."""
         return cls(comms[0].P, comms[0].dtype, _handle=hiccl_group(comms))
+
+    @classmethod
+    def group_plan(cls, comms: Sequence["Comm"]) -> "Comm":
+        """The group's combined table, planned on the host only (inspection)."""
+        return cls(comms[0].P, comms[0].dtype, _handle=hiccl_group_plan(comms))
 
     def add_multicast(self, send, recv, count, root, leaves):
         hiccl_add_multicast(self.handle, send, recv, count, root, list(leaves), self.P)

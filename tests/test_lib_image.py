@@ -245,3 +245,63 @@ def test_random_order_catches_a_missing_dependency():
         assert differs
     finally:
         comm.image = orig
+
+
+class _Members:
+    """Fake addresses of several programs in disjoint ranges, resolvable as
+    one memory (keys (member, buffer key))."""
+
+    def __init__(self, progs):
+        self.fakes, self.base = [], {}
+        b = 0x7f0000000000
+        for m, prog in enumerate(progs):
+            f = FakeAddresses(prog, base=b)
+            self.fakes.append(f)
+            for k, a in f.base.items():
+                self.base[(m, k)] = a
+            b = (f.end + (1 << 20)) & ~255
+
+    def resolve(self, addr):
+        best = None
+        for key, b in self.base.items():
+            if b <= addr and (best is None or b > best[1]):
+                best = (key, b)
+        return best[0], addr - best[1]
+
+
+@pytest.mark.parametrize("seed", [None, 11, 12])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_group_image_executes_every_member(seed, dtype):
+    """hiccl_group's combined table (members interleaved by slot, relays
+    moved to disjoint ranges, successor lists shifted), planned on the host:
+    executed from its image -- in ticket order or in random dependency
+    orders -- every member's buffers equal that member's oracle result."""
+    from oracle import semantics as S
+    from tests._bridge import interpret_image
+    from tests._cases import fill
+    shapes = [("allreduce", [4, 4], 2, 3), ("allgather", [2, 8], 4, 2), ("reducescatter", [16], 1, 1),
+              ("alltoall", [4, 4], 4, 1)]
+    progs = [PR.BUILDERS[name](16, 300, dtype=dtype) for name, *_ in shapes]
+    mm = _Members(progs)
+    members = []
+    for prog, fake, (name, h, s, m) in zip(progs, mm.fakes, shapes):
+        c = register(prog, fake.addr)
+        c.plan(h, s, m)
+        members.append(c)
+    g = H.Comm.group_plan(members)
+    info = g.plan_info()
+    assert info["steps"] == sum(c.plan_info()["steps"] for c in members)
+    assert info["items"] == sum(c.plan_info()["items"] for c in members)
+    mem0, ref = {}, {}
+    for i, prog in enumerate(progs):
+        m0 = fill(prog, 100 + i)
+        r = {k: v.copy() for k, v in m0.items()}
+        S.run_program(prog, r, shapes[i][1])
+        for k in m0:
+            mem0[(i, k)] = m0[k]
+            ref[(i, k)] = r[k]
+    got = interpret_image(g, mm, {k: v.copy() for k, v in mem0.items()}, dtype, seed=seed)
+    for k in ref:
+        assert np.array_equal(ref[k].view(np.uint8), got[k].view(np.uint8)), k
+    with pytest.raises(H.HicclError):
+        g.start()                                # planned only: not startable
