@@ -270,7 +270,7 @@ class _Members:
 
 
 @pytest.mark.parametrize("seed", [None, 11, 12])
-@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
 def test_group_image_executes_every_member(seed, dtype):
     """hiccl_group's combined table (members interleaved by slot, relays
     moved to disjoint ranges, successor lists shifted), planned on the host:
@@ -281,7 +281,7 @@ def test_group_image_executes_every_member(seed, dtype):
     from tests._cases import fill
     shapes = [("allreduce", [4, 4], 2, 3), ("allgather", [2, 8], 4, 2), ("reducescatter", [16], 1, 1),
               ("alltoall", [4, 4], 4, 1)]
-    progs = [PR.BUILDERS[name](16, 300, dtype=dtype) for name, *_ in shapes]
+    progs = [PR.BUILDERS[name](16, 3 if dtype == "fp8" else 300, dtype=dtype) for name, *_ in shapes]
     mm = _Members(progs)
     members = []
     for prog, fake, (name, h, s, m) in zip(progs, mm.fakes, shapes):
