@@ -305,3 +305,23 @@ def test_group_image_executes_every_member(seed, dtype):
         assert np.array_equal(ref[k].view(np.uint8), got[k].view(np.uint8)), k
     with pytest.raises(H.HicclError):
         g.start()                                # planned only: not startable
+
+
+def test_group_plan_errors():
+    """hiccl_group's checks, on the host: unplanned members are refused
+    (HICCL_ERR_STATE) and FP8 members cannot join other payloads
+    (HICCL_ERR_UNSUPPORTED)."""
+    a = PR.BUILDERS["allreduce"](8, 256)
+    b = PR.BUILDERS["allreduce"](8, 2, dtype="fp8")
+    mm = _Members([a, b])
+    ca, cb = register(a, mm.fakes[0].addr), register(b, mm.fakes[1].addr)
+    with pytest.raises(H.HicclError) as e:
+        H.Comm.group_plan([ca, cb])
+    assert e.value.status == H.ERR_STATE
+    ca.plan([2, 4], 1, 1)
+    cb.plan([2, 4], 1, 1)
+    with pytest.raises(H.HicclError) as e:
+        H.Comm.group_plan([ca, cb])
+    assert e.value.status == H.ERR_UNSUPPORTED
+    g = H.Comm.group_plan([ca])
+    assert g.plan_info()["steps"] == ca.plan_info()["steps"]
