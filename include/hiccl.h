@@ -221,17 +221,26 @@ hiccl_status_t hiccl_group_plan(const hiccl_comm_t *comms, int n, hiccl_comm_t *
 
 /* ---- accounting -------------------------------------------------------------- */
 
-/* Bytes that cross each hierarchy level per execution: for every copy
- * destination and every reduce input on another rank, the step's bytes are
- * added to the level at which the two ranks first fall into different
+/* Bytes that cross each hierarchy level per execution (Sec. 4.1 and Fig. 1:
+ * the factorization exists to cut the volume on the upper, slower levels;
+ * Table 3 gives the per-node top-level volume of each collective): for every
+ * copy destination and every reduce input on another rank, the step's bytes
+ * are added to the level at which the two ranks first fall into different
  * subgroups.  per_level receives nlevels values (top level first); nlevels
- * must equal the hierarchy's.  Valid after hiccl_init or hiccl_plan. */
+ * must equal the hierarchy's.  Valid after hiccl_init or hiccl_plan;
+ * HICCL_ERR_INVALID for a NULL array or a wrong nlevels, HICCL_ERR_STATE
+ * before planning, HICCL_ERR_UNSUPPORTED for a group (query its members). */
 hiccl_status_t hiccl_level_bytes(hiccl_comm_t comm, unsigned long long *per_level,
                                  int nlevels);
 
 /* Device-memory bytes one execution reads and writes by the schedule's
  * definition: a copy reads its bytes once and writes them once per
- * destination; an f-input reduce reads f times its bytes and writes them once. */
+ * destination; an f-input reduce reads f times its bytes and writes them once.
+ * This is the numerator of the executor's bandwidth figure; Sec. 6.2 measures
+ * throughput as buffer bytes (d*p) over time, which is the volume the
+ * schedule moves here once every relay and destination is counted.  Either
+ * output may be NULL.  Valid after hiccl_init or hiccl_plan; HICCL_ERR_STATE
+ * before planning. */
 hiccl_status_t hiccl_hbm_bytes(hiccl_comm_t comm, unsigned long long *read,
                                unsigned long long *write);
 
