@@ -236,9 +236,10 @@ hiccl_status_t hiccl_level_bytes(hiccl_comm_t comm, unsigned long long *per_leve
 /* Device-memory bytes one execution reads and writes by the schedule's
  * definition: a copy reads its bytes once and writes them once per
  * destination; an f-input reduce reads f times its bytes and writes them once.
- * This is the numerator of the executor's bandwidth figure; Sec. 6.2 measures
- * throughput as buffer bytes (d*p) over time, which is the volume the
- * schedule moves here once every relay and destination is counted.  Either
+ * Sec. 6.2 defines throughput as the buffer bytes d*p over time; this call
+ * gives, for the same execution, the bytes the factorized schedule moves
+ * through device memory (relay buffers and every destination included),
+ * the numerator of a bandwidth compared with the HBM roofline.  Either
  * output may be NULL.  Valid after hiccl_init or hiccl_plan; HICCL_ERR_STATE
  * before planning. */
 hiccl_status_t hiccl_hbm_bytes(hiccl_comm_t comm, unsigned long long *read,
