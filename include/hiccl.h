@@ -385,16 +385,20 @@ hiccl_status_t hiccl_debug_withhold(hiccl_comm_t comm, unsigned long long index,
  * file-scope device array of HICCL_STATIC_ARENA_BYTES that every GPU loading
  * this library holds until the process exits; no cudaMalloc, cudaFree or
  * other allocating routine is called.  The first call on a device, with that
- * device current, looks the array's address up (cudaGetSymbolAddress); make
- * that first call before any stream capture.  The call uploads the plan,
+ * device current, looks the array's address up (cudaGetSymbolAddress, once
+ * per device and process, safe from several host threads); make that first
+ * call before any stream capture.  A cudaDeviceReset of the device
+ * invalidates the address: do not call this again in that process after
+ * one.  The call uploads the plan,
  * zeroes the counters (the array keeps the previous call's contents), runs
  * the executor and blocks until the stream reaches the end of the run.
  * Every call, from any communicator, uses the same array: calls that overlap
  * on the GPU (other host threads, other streams) race and must be serialized
- * by the caller.  Returns HICCL_ERR_TOO_LARGE, before touching the GPU, when
+ * by the caller.  Returns HICCL_ERR_TOO_LARGE, before any CUDA call, when
  * the plan needs more than HICCL_STATIC_ARENA_BYTES; HICCL_ERR_STATE without a
- * plan; HICCL_ERR_TIMEOUT if a dependency wait ran out; HICCL_ERR_CUDA on a
- * CUDA error.  It does not set the hiccl_last_error message. */
+ * plan; HICCL_ERR_TIMEOUT if a wait of the executor ran out; HICCL_ERR_CUDA on
+ * a CUDA error or any other executor error (as hiccl_wait decodes them).  It
+ * does not set the hiccl_last_error message. */
 hiccl_status_t hiccl_run_static(hiccl_comm_t comm, void *cuda_stream);
 
 /* Message of the last failed call on `comm` ("" if none); a static string

@@ -206,6 +206,8 @@ struct TableImage {
   std::vector<DevItem> items;             // per work item
 };
 void build_image(const Plan &p, unsigned long long relay_base, TableImage &im);
+// bytes of TableImage::recs for plan p, without building the image
+unsigned long long record_bytes(const Plan &p);
 
 }  // namespace hiccl
 

@@ -768,14 +768,21 @@ static DevItem item_shape(const Plan &p, size_t i) {
   return it;
 }
 
+// Bytes of the work-item records of plan p (the size of TableImage::recs),
+// from the record shapes without building the image.
+unsigned long long record_bytes(const Plan &p) {
+  const size_t NI = p.item_off.empty() ? 0 : p.item_off.size() - 1;
+  unsigned long long recs = 0;
+  for (size_t i = 0; i < NI; ++i) recs += rec_bytes(item_shape(p, i));
+  return recs;
+}
+
 // Bytes of the device table of plan p (records, item descriptors, per-step
 // targets and successor CSR, pointer array, control block), computed from
 // the record shapes without building the image.
 unsigned long long table_bytes(const Plan &p) {
   const size_t NI = p.item_off.empty() ? 0 : p.item_off.size() - 1;
-  unsigned long long recs = 0;
-  for (size_t i = 0; i < NI; ++i) recs += rec_bytes(item_shape(p, i));
-  return recs + NI * sizeof(DevItem) + p.steps.size() * (4 + 4 + 16) + 4 + p.succ.size() * 4 +
+  return record_bytes(p) + NI * sizeof(DevItem) + p.steps.size() * (4 + 4 + 16) + 4 + p.succ.size() * 4 +
          p.locs.size() * 8 + sizeof(DevCtl);
 }
 

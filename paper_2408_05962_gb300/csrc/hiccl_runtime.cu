@@ -1416,7 +1416,15 @@ namespace hiccl {
 static __device__ __align__(256) unsigned char g_static_arena[HICCL_STATIC_ARENA_BYTES];
 
 constexpr int MAX_STATIC_DEVICES = 64;
-static void *g_static_addr[MAX_STATIC_DEVICES];   // device address of the arena, per device
+// device address of the arena, looked up once per device with that device
+// current; a cudaDeviceReset of the device invalidates it (the lookup is not
+// repeated in this process)
+struct StaticAddr {
+  std::once_flag once;
+  cudaError_t status = cudaSuccess;
+  void *addr = nullptr;
+};
+static StaticAddr g_static_addr[MAX_STATIC_DEVICES];
 
 }  // namespace hiccl
 
@@ -1429,35 +1437,41 @@ extern "C" hiccl_status_t hiccl_run_static(hiccl_comm_t c, void *stream) {
     const unsigned long long N = p.steps.size();
     const unsigned long long NI = p.item_off.size() ? p.item_off.size() - 1 : 0, NS = p.succ.size();
 
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return HICCL_ERR_CUDA;
-    if (dev < 0 || dev >= MAX_STATIC_DEVICES) return HICCL_ERR_UNSUPPORTED;
-    if (!g_static_addr[dev]) {   // once per device, with that device current
-      void *addr = nullptr;
-      if (cudaGetSymbolAddress(&addr, g_static_arena) != cudaSuccess || !addr) {
-        cudaGetLastError();
-        return HICCL_ERR_CUDA;
-      }
-      g_static_addr[dev] = addr;
-    }
-    char *base = static_cast<char *>(g_static_addr[dev]);
-
     // arena layout: relay buffers first (their addresses go into the records),
-    // then the read-only arrays, then the counters
+    // then the read-only arrays, then the counters, the control block and the
+    // error word.  The sizes do not depend on where the arena lies, so a plan
+    // that does not fit is rejected before any CUDA call.
     unsigned long long off = 0;
     auto place = [&](unsigned long long bytes) {
       const unsigned long long o = off;
       off = (off + bytes + 255) & ~255ull;
       return o;
     };
+    const unsigned long long rec_b = record_bytes(p);
     const unsigned long long o_relay = place(p.scratch_bytes);
-    TableImage im;
-    build_image(p, (unsigned long long)(uintptr_t)(base + o_relay), im);
-    const unsigned long long o_recs = place(im.recs.size()), o_items = place(im.items.size() * sizeof(DevItem)),
-                             o_nent = place(N * 4), o_succoff = place((N + 1) * 4), o_succ = place(NS * 4),
-                             o_ptrs = place(im.ptrs.size() * 8), o_ctr = place(N * 16 + sizeof(DevCtl) + 8);
+    const unsigned long long o_recs = place(rec_b), o_items = place(NI * sizeof(DevItem)), o_nent = place(N * 4),
+                             o_succoff = place((N + 1) * 4), o_succ = place(NS * 4), o_ptrs = place(p.locs.size() * 8),
+                             ctr_bytes = N * 16 + sizeof(DevCtl) + 8, o_ctr = place(ctr_bytes);
     if (off > HICCL_STATIC_ARENA_BYTES) return HICCL_ERR_TOO_LARGE;
     if (N == 0) return HICCL_OK;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HICCL_ERR_CUDA;
+    if (dev < 0 || dev >= MAX_STATIC_DEVICES) return HICCL_ERR_UNSUPPORTED;
+    StaticAddr &sa = g_static_addr[dev];
+    std::call_once(sa.once, [&]() {   // once per device, with that device current
+      void *addr = nullptr;
+      sa.status = cudaGetSymbolAddress(&addr, g_static_arena);
+      if (sa.status == cudaSuccess && !addr) sa.status = cudaErrorInvalidSymbol;
+      if (sa.status != cudaSuccess) cudaGetLastError();
+      sa.addr = addr;
+    });
+    if (sa.status != cudaSuccess) return HICCL_ERR_CUDA;
+    char *base = static_cast<char *>(sa.addr);
+
+    TableImage im;
+    build_image(p, (unsigned long long)(uintptr_t)(base + o_relay), im);
+    if (im.recs.size() != rec_b || im.items.size() != NI || im.ptrs.size() != p.locs.size()) return HICCL_ERR_INVALID;
 
     auto h2d = [&](unsigned long long o, const void *src, unsigned long long bytes) {
       return bytes ? cudaMemcpyAsync(base + o, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
@@ -1470,7 +1484,7 @@ extern "C" hiccl_status_t hiccl_run_static(hiccl_comm_t c, void *stream) {
     if (e == cudaSuccess) e = h2d(o_succ, p.succ.data(), NS * 4);
     if (e == cudaSuccess) e = h2d(o_ptrs, im.ptrs.data(), im.ptrs.size() * 8);
     // every call starts from zeroed counters: the arena keeps the last call's contents
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_ctr, 0, N * 16 + sizeof(DevCtl) + 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_ctr, 0, ctr_bytes, s);
     if (e != cudaSuccess) return HICCL_ERR_CUDA;
 
     DevTable t{};
@@ -1502,6 +1516,10 @@ extern "C" hiccl_status_t hiccl_run_static(hiccl_comm_t c, void *stream) {
     if (cudaMemcpy(&err, base + o_ctr + N * 16 + offsetof(DevCtl, err), sizeof(err), cudaMemcpyDeviceToHost) !=
         cudaSuccess)
       return HICCL_ERR_CUDA;
-    return err ? HICCL_ERR_TIMEOUT : HICCL_OK;
+    if (!err) return HICCL_OK;
+    // the same decoding as hiccl_wait: a wait that ran out is a timeout, any
+    // other executor error a CUDA-side failure
+    const unsigned code = (unsigned)(err >> 32);
+    return (code == ERR_TIMEOUT || code == ERR_STALL) ? HICCL_ERR_TIMEOUT : HICCL_ERR_CUDA;
   });
 }

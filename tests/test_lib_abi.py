@@ -167,3 +167,23 @@ def test_host_memory_exhaustion_is_a_status_not_an_abort():
     assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
     out = r.stdout.strip().splitlines()[-1]
     assert out.startswith(f"status {H.ERR_NOMEM} "), out
+
+
+def test_static_size_check_precedes_any_cuda_call():
+    """hiccl_run_static rejects a plan larger than its fixed device array
+    before any CUDA call: on a host without a GPU it still answers
+    HICCL_ERR_TOO_LARGE (a CUDA call there would fail with HICCL_ERR_CUDA)."""
+    import torch
+
+    from oracle import programs as PR
+    from tests._bridge import FakeAddresses, register
+    if torch.cuda.is_available():
+        pytest.skip("checks the order of the checks on a host without a GPU")
+    prog = PR.reducescatter(64, 1 << 18)
+    fake = FakeAddresses(prog)
+    comm = register(prog, fake.addr)
+    comm.plan([4, 4, 4], 1, 1)
+    with pytest.raises(H.HicclError) as e:
+        comm.run_static()
+    assert e.value.status == H.ERR_TOO_LARGE
+    comm.destroy()
