@@ -5,6 +5,9 @@ fixed order and encodes the step's result once (BF16: nearest even; FP8: a
 fresh per-128-value scale amax/448 and nearest-even, saturating codes).  The
 results must equal the oracle bit for bit, and stay within 1e-2 (BF16) and
 6e-2 (FP8) relative L2 error of the FP64 sum of the decoded inputs."""
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 
@@ -58,10 +61,11 @@ def test_bf16_unaligned_element_path():
 @pytest.mark.parametrize("dtype,tol", [("f32", 1e-6), ("bf16", 1e-2), ("fp8", 6e-2)])
 def test_config3_allreduce_three_variants(dtype, tol):
     """All-reduce, P = 32 over {4, 8}, the same 16,777,216 values per rank
-    (N(0,1) * 10**U(-3,3) per rank) as FP32, BF16 and FP8 payloads; sampled
-    elements (whole FP8 blocks) are compared with the oracle's fold bit for
-    bit, and the relative L2 error against the FP64 sum of the decoded inputs
-    is within the stated bound."""
+    (N(0,1) * 10**U(-3,3) per rank) as FP32, BF16 and FP8 payloads, in the
+    launch configuration of the benchmark (stripe 1, pipeline 4).  The oracle
+    folds all 16,777,216 values; every one of the 32 receive buffers equals it
+    byte for byte, and the relative L2 error of each result buffer against
+    the FP64 sum of the decoded inputs is within the stated bound."""
     import torch
     from paper_2408_05962_gb300 import collectives as C
     from paper_2408_05962_gb300 import hiccl as H
@@ -71,38 +75,27 @@ def test_config3_allreduce_three_variants(dtype, tol):
     n = 16 << 20
     d = n // P
     x = scaled_normal_ranks(P, n, seed=3)
-    enc = [LP.encode(x[r], dtype) for r in range(P)]
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as pool:
+        enc = list(pool.map(lambda r: LP.encode(x[r], dtype), range(P)))
+    del x
     tdt = {"f32": torch.float32, "bf16": torch.int16, "fp8": torch.uint8}[dtype]
     bufs = C.Buffers("allreduce", P, d, tdt)
-    host = np.stack([e.view(np.uint8) for e in enc])
-    bufs.send.view(torch.uint8).copy_(torch.from_numpy(host))
+    for r in range(P):
+        bufs.send[r].view(torch.uint8).copy_(torch.from_numpy(enc[r].view(np.uint8)))
     bufs.recv.zero_()
     comm = H.Comm(P, dtype)
     C.compose(comm, "allreduce", d, bufs.send_ptrs(), bufs.recv_ptrs())
     comm.init(h, 1, 4)
     comm.start()
     comm.wait()
-    y = bufs.recv.view(torch.uint8).cpu().numpy()
     comm.destroy()
-    g = np.random.Generator(np.random.PCG64(7))
-    if dtype == "fp8":
-        blk = np.unique(np.concatenate([g.integers(0, n // 128, 512), np.arange(0, n // 128, d // 128)]))
-        vals = {r: enc[r][blk] for r in range(P)}
-        expect = S.nested_fold(vals, h, dtype)
-        for r in (0, 5, 31):
-            got = y[r].view(LP.FP8_BLOCK_DTYPE)[blk]
-            assert np.array_equal(got.view(np.uint8), expect.view(np.uint8)), r
-        yv = LP.payload_to_f32(expect, dtype)
-        ref = S.fsum64([LP.payload_to_f32(v, dtype) for v in vals.values()])
-    else:
-        idx = np.unique(np.concatenate([g.integers(0, n, 65536), np.arange(0, n, d), [n - 1]]))
-        vals = {r: enc[r][idx] for r in range(P)}
-        expect = S.nested_fold(vals, h, None if dtype == "f32" else dtype)
-        view = np.float32 if dtype == "f32" else np.uint16
-        for r in (0, 5, 31):
-            got = y[r].view(view)[idx]
-            assert np.array_equal(got.view(np.uint8), expect.view(np.uint8)), r
-        yv = LP.payload_to_f32(expect, dtype)
-        ref = S.fsum64([LP.payload_to_f32(v, dtype) for v in vals.values()])
-    err = float(np.linalg.norm(yv - ref) / np.linalg.norm(ref))
-    assert err <= tol, err
+    expect = S.nested_fold({r: enc[r] for r in range(P)}, h, None if dtype == "f32" else dtype)
+    ref = S.fsum64([LP.payload_to_f32(e, dtype) for e in enc])
+    del enc
+    want = expect.view(np.uint8)
+    nref = np.linalg.norm(ref)
+    for r in range(P):
+        got = bufs.recv[r].view(torch.uint8).cpu().numpy()
+        assert np.array_equal(got, want), r
+        err = float(np.linalg.norm(LP.payload_to_f32(got.view(expect.dtype), dtype).astype(np.float64) - ref) / nref)
+        assert err <= tol, (r, err)
