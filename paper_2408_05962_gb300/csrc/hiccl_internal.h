@@ -109,12 +109,15 @@ HICCL_HD inline uint32_t rec_bytes(const DevItem &it) {
          rec_cmp_bytes(it.nent, it.nsucc);
 }
 
-// per-launch control block (device memory, zeroed at upload)
+// control block (device memory, zeroed at upload).  Launch e (counted from
+// 1) claims work items from ticket[e & 1]; the last of its CTAs to read the
+// epoch resets `started` and the other ticket and sets `epoch` to e, so the
+// next launch finds everything armed and no CTA does any work at exit.
 struct DevCtl {
-  unsigned long long ticket;   // next work item to claim
-  unsigned long long exited;   // CTAs that left the item loop
-  unsigned long long epoch;    // completed launches; counter targets scale with it
-  unsigned long long err;      // nonzero: abort (code << 32 | step)
+  unsigned long long ticket[2];   // next work item to claim, by launch parity
+  unsigned long long started;     // CTAs of the current launch that have read the epoch
+  unsigned long long epoch;       // launches started so far; counter targets scale with it
+  unsigned long long err;         // nonzero: abort (code << 32 | step)
 };
 
 struct DevTable {

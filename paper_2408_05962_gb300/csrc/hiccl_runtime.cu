@@ -568,6 +568,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
   __shared__ __align__(8) unsigned long long full_bar[NBUF], done_bar[NBUF], empty_bar[NBUF], rec_bar[NBUF];
   __shared__ __align__(8) unsigned long long ld_bar[D][NS];
   __shared__ __align__(8) unsigned long long red_bar[D];
+  __shared__ unsigned long long s_epoch;
   extern __shared__ __align__(128) unsigned char stage[];   // D x NS x SEG_BYTES
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -587,7 +588,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
   __syncthreads();
   // the previous kernel of the stream has completed and its writes are visible
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  const unsigned long long epoch = ld_relaxed(&T.ctl->epoch) + 1;   // this launch
+  // one read of the epoch per CTA, before the CTA counts itself as started
+  if (tid == 0) s_epoch = ld_acquire(&T.ctl->epoch) + 1;
+  __syncthreads();
+  const unsigned long long epoch = s_epoch;   // this launch
+  unsigned long long *const ticket = &T.ctl->ticket[epoch & 1];
 
   if (warp == 0) {
     // ---- control: claim, stage, wait for predecessors ----
@@ -596,7 +601,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
     // in flight and its predecessors are awaited.
     unsigned long long nxt = 0;
     DevItem nd{0, 0, 0, 0, 0, {0, 0, 0}};
-    if (lane == 0) nxt = atomicAdd(&T.ctl->ticket, 1ull);
+    if (lane == 0) nxt = atomicAdd(ticket, 1ull);
     nxt = __shfl_sync(0xffffffffu, nxt, 0);
     if (nxt < T.nitems) nd = T.items[nxt];
     for (uint32_t r = 0;; ++r) {
@@ -632,7 +637,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
           B.nent = it.nent;
           B.nrun = it.nrun;
           B.nsucc = it.nsucc;
-          nxt = atomicAdd(&T.ctl->ticket, 1ull);
+          nxt = atomicAdd(ticket, 1ull);
         }
         nxt = __shfl_sync(0xffffffffu, nxt, 0);
         if (nxt < T.nitems) {
@@ -693,6 +698,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
     }
   } else if (warp == 1) {
     // ---- completion: release the successors of finished steps ----
+    // (first, the last CTA of the launch to start arms the next launch: every
+    // CTA has read the epoch by now, and the other ticket is not in use)
+    if (lane == 0 && atom_acq_rel_add(&T.ctl->started, 1ull) == gridDim.x - 1ull) {
+      T.ctl->started = 0;
+      T.ctl->ticket[(epoch + 1) & 1] = 0;
+      T.ctl->epoch = epoch;
+    }
     for (uint32_t r = 0;; ++r) {
       const int b = r % NBUF;
       const uint32_t ph = (r / NBUF) & 1u;
@@ -961,18 +973,6 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
     }
   }
 
-  // the last CTA out re-arms the control block for the next launch
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    const unsigned long long prev = atomicAdd(&T.ctl->exited, 1ull);
-    if (prev == gridDim.x - 1) {
-      T.ctl->ticket = 0;
-      T.ctl->exited = 0;
-      __threadfence();
-      if (ld_relaxed(&T.ctl->err) == 0ull) T.ctl->epoch = epoch;
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------
