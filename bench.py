@@ -1,18 +1,27 @@
 """Benchmark of the hierarchical collective path on GB300.
 
-Workload (one "step"): the seven standard collectives -- Broadcast, Scatter,
-Gather, All-gather, Reduce-scatter, All-reduce (Listing 2) and All-to-all --
-over P = 64 virtual ranks with hierarchy {4,4,4}, 4 MiB of fp32 per rank
-(uniform[-1, 1], seed 0), stripe 4, pipeline 8; each collective is one start
-of its own persistent communicator, all seven enqueued back to back.
+Headline workload (one "step"): the seven standard collectives --
+Broadcast, Scatter, Gather, All-gather, Reduce-scatter, All-reduce (Listing
+2) and All-to-all -- over P = 64 virtual ranks with hierarchy {4,4,4}, 4 MiB
+of fp32 per rank (uniform[-1, 1], seed 0), stripe 4, pipeline 8; each
+collective is one start of its own persistent communicator.  The seven
+starts of a step are captured once in a CUDA graph; the timed region is a
+series of blocks of K graph replays (at least one second in all) and the
+median block gives the step time (Sec. 6.2 reports the median of its
+measured rounds).  The same steps through start / wait on the host are
+reported beside it ("eager").
 
 Metric: device-memory GB/s of the schedule (each copy reads its bytes once
 and writes them once per destination; an f-input reduce reads f times and
-writes once), summed over the seven collectives and divided by their summed
-kernel time, with the fraction of the measured HBM bandwidth; per-collective
-GB/s and the paper-style d*p/t are reported beside it.
+writes once), with the fraction of the measured HBM bandwidth; per
+collective GB/s, the semantic-minimum bytes and the paper-style d*p/t are
+reported beside it.  The default line also carries, each under its own
+timing: the 64 MiB-per-rank All-reduce as FP32, BF16 and FP8 payloads with
+their FP64 errors; the batch of 256 mixed collectives (one launch each,
+grouped, graph); and a short served run with p50 / p99 latency.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload seven|allreduce64]
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload seven|allreduce64|batch256|serve] [--no-extras]
 Under torchrun each rank runs an independent replica on its own GPU
 ("replicas only": the virtual-rank path does not shard across devices).
 """
@@ -37,7 +46,6 @@ METRIC = "HBM GB/s (% of GB300 peak) per collective; p50/p99 latency of served r
 KINDS = ("broadcast", "scatter", "gather", "allgather", "reducescatter", "allreduce", "alltoall")
 P, HIER, STRIPE, PIPE = 64, [4, 4, 4], 4, 8
 BYTES_PER_RANK = 4 << 20
-STRIDE = 1          # oracle sample: every STRIDE-th primitive of each collective
 KERNEL_SRC = os.path.join(ROOT, "paper_2408_05962_gb300", "csrc", "hiccl_runtime.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "executor_traffic_seven_p64.txt")
 
@@ -58,11 +66,12 @@ WORKLOADS = {
 }
 
 
-def workload_config(extra=None, w="seven"):
+def workload_config(w="seven", world=1, dtype="f32", extra=None):
+    """The ``config`` of a line: the same dict in both arms."""
     W = WORKLOADS[w]
     cfg = {"workload": W["name"], "ranks": W["ranks"], "hierarchy": W["hierarchy"], "stripe": W["stripe"],
            "pipeline": W["pipeline"], "bytes_per_rank": W["bytes_per_rank"], "collectives": list(W["kinds"]),
-           "inputs": W["data"], "l2": W["l2"]}
+           "inputs": W["data"], "l2": W["l2"], "payload": dtype, "parallelism": f"replicas{world}"}
     if extra:
         cfg.update(extra)
     return cfg
@@ -285,54 +294,104 @@ def recorded_traffic():
 _ORACLE_CACHE = {}
 
 
-def _oracle_plans(seed: int = 0):
-    """The oracle's factorized schedules of the workload and their buffers
-    (built once; factorization is initialization, not part of a step)."""
-    if seed in _ORACLE_CACHE:
-        return _ORACLE_CACHE[seed]
+def _oracle_plan(kind: str, seed: int = 0):
+    """The oracle's factorized schedule of one collective of the headline
+    workload and its buffers (built once; factorization is initialization,
+    not part of a step)."""
+    key = (kind, seed)
+    if key in _ORACLE_CACHE:
+        return _ORACLE_CACHE[key]
     import numpy as np
 
     from oracle import programs as PR
     from oracle.factorize import factorize
-    from oracle.model import Program
     from synth import uniform_ranks
 
     d = BYTES_PER_RANK // 4 // P
     x = uniform_ranks(P, d * P, seed=seed)
-    out = []
-    for kind in KINDS:
-        full = PR.BUILDERS[kind](P, d)
-        prog = Program(P, full.dtype, dict(full.buffers), [ep[::STRIDE] for ep in full.epochs])
-        plan = factorize(prog, HIER, STRIPE, PIPE)
-        mem = prog.allocate()
-        for r in range(P):
-            mem[("send", r)][...] = x[r][:mem[("send", r)].shape[0]]
-        for k, n in plan.scratch.items():
-            mem[k] = np.zeros(n, dtype=np.float32)
-        out.append((kind, plan, mem))
-    _ORACLE_CACHE[seed] = out
-    return out
+    prog = PR.BUILDERS[kind](P, d)
+    plan = factorize(prog, HIER, STRIPE, PIPE)
+    mem = prog.allocate()
+    for r in range(P):
+        mem[("send", r)][...] = x[r][:mem[("send", r)].shape[0]]
+    for k, n in plan.scratch.items():
+        mem[k] = np.zeros(n, dtype=np.float32)
+    _ORACLE_CACHE[key] = (plan, mem)
+    return plan, mem
 
 
-def oracle_sample(budget_s: float, seed: int = 0):
-    """Simulate the oracle's factorized schedule of the workload (all seven
-    collectives) for at most ``budget_s`` seconds in all.
-    Returns (schedule bytes simulated, seconds, description)."""
+def _simulate_for(kind: str, budget_s: float, seed: int = 0):
+    """Run the oracle's schedule simulator on one collective for about
+    ``budget_s`` seconds: complete executions in dependency order, repeated,
+    the last one cut off when the time is up.  Returns (schedule bytes, s)."""
     from oracle.simulate import execute_op
 
-    total_b, total_t = 0, 0.0
-    per = budget_s / len(KINDS)
-    for kind, plan, mem in _oracle_plans(seed):
-        t0 = time.perf_counter()
+    plan, mem = _oracle_plan(kind, seed)
+    total_b, t0 = 0, time.perf_counter()
+    while True:
         for op in plan.ops:
             execute_op(op, mem)
             total_b += op.n * 4 * (1 + len(op.dsts) if op.kind == "copy" else len(op.srcs) + 1)
-            if time.perf_counter() - t0 > per:
-                break
-        total_t += time.perf_counter() - t0
-    kept = "every primitive" if STRIDE == 1 else f"every {STRIDE}-th primitive"
-    return total_b, total_t, (f"oracle schedule simulator (NumPy, 1 thread) on {kept} of each of the seven "
-                              f"collectives, at most {per:.1f} s of simulation each (factorization untimed)")
+            if time.perf_counter() - t0 > budget_s:
+                return total_b, time.perf_counter() - t0
+
+
+def oracle_sample(budget_s: float, seed: int = 0):
+    """The oracle's schedule simulator on one thread over the seven
+    collectives, ``budget_s`` seconds in all.  Returns (bytes, s, description)."""
+    per = budget_s / len(KINDS)
+    bs, ts = 0, 0.0
+    for kind in KINDS:
+        b, t = _simulate_for(kind, per, seed)
+        bs += b
+        ts += t
+    return bs, ts, (f"oracle schedule simulator (NumPy, 1 thread) on each of the seven collectives for "
+                    f"{per:.1f} s (complete executions in dependency order, repeated; factorization untimed)")
+
+
+_BARRIER = None
+
+
+def _worker_init(barrier):
+    global _BARRIER
+    _BARRIER = barrier
+
+
+def _oracle_worker(job):
+    kind, budget_s, seed = job
+    _oracle_plan(kind, seed)   # untimed set-up
+    _BARRIER.wait()            # every worker simulates in the same time window
+    return _simulate_for(kind, budget_s, seed)
+
+
+def oracle_all_cores(budget_s: float, cores: int, seed: int = 0):
+    """The same simulator on ``cores`` worker processes at once (spawned:
+    nothing is forked from a process that has used the GPU), worker i
+    simulating its own copy of collective i mod 7.  Returns (bytes summed over
+    the workers, the longest worker's time, description)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(cores)
+    jobs = [(KINDS[i % len(KINDS)], budget_s, seed) for i in range(cores)]
+    with ctx.Pool(cores, initializer=_worker_init, initargs=(barrier,)) as pool:
+        res = pool.map(_oracle_worker, jobs, chunksize=1)
+    return (sum(b for b, _ in res), max(t for _, t in res),
+            f"oracle schedule simulator in {cores} processes at once, process i running its own copy of "
+            f"collective i mod 7 for {budget_s:.1f} s (complete executions, repeated; factorization untimed)")
+
+
+def cpu_baseline(budget_s: float):
+    """Single-thread and all-cores legs of the oracle on this host."""
+    cores = os.cpu_count() or 1
+    b1, t1, d1 = oracle_sample(budget_s)
+    out = {"unit": "GB/s", "kind": "oracle", "nproc": cores,
+           "single_thread": {"value": b1 / t1 / 1e9, "cores": 1, "sample": d1}}
+    try:
+        bn, tn, dn = oracle_all_cores(budget_s / 2, cores)
+        out.update({"value": bn / tn / 1e9, "cores": cores, "sample": dn})
+    except Exception as e:   # a report field only
+        out.update({"value": b1 / t1 / 1e9, "cores": 1, "sample": d1, "all_cores_error": repr(e)[:200]})
+    return out
 
 
 def run_reference(args):
@@ -343,17 +402,20 @@ def run_reference(args):
             return
     for _ in range(args.warmup):
         oracle_sample(0.5)
+    per_step = []
     bs, ts = 0, 0.0
     for _ in range(args.steps):
         b, t, desc = oracle_sample(args.ref_budget)
         bs += b
         ts += t
+        per_step.append(t)
     gbs = bs / ts / 1e9
     line = {"metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ts / args.steps * 1e3, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": statistics.median(per_step) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(), "impl": "reference",
-            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "config": workload_config("seven", world, "f32"), "impl": "reference",
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc,
+                             "nproc": os.cpu_count()},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -380,6 +442,14 @@ def _fp8_blocks(x):
     return out.reshape(P, -1)
 
 
+def _bf16_rows(x):
+    """binary32 rows (host) -> BF16 bit patterns, round to nearest even on the
+    upper 16 bits (payload encoding, set-up)."""
+    import torch
+    t = torch.from_numpy(x).view(torch.int32)
+    return ((t + 0x7FFF + ((t >> 16) & 1)) >> 16).to(torch.int16)
+
+
 def min_bytes(kind: str, P: int, B: int) -> int:
     """HBM bytes a collective cannot avoid on one device: every input byte it
     needs read once and every output byte written once (B = the largest
@@ -402,10 +472,11 @@ def _decode_rows(t, dtype):
 
 
 def _lowprec_accuracy(b, dtype, xs, device):
-    """Error of the reduced-precision All-reduce result, measured after the
-    timed region with plain torch arithmetic: relative L2 and max-norm errors
-    against the FP64 sum of the decoded inputs, and the relative L2 error
-    against the FP64 sum of the unquantized binary32 sources."""
+    """Error of the reduced-precision All-reduce results, measured after the
+    timed region with plain torch arithmetic, per result buffer: relative L2
+    and max-norm errors against the FP64 sum of the decoded inputs, and the
+    relative L2 error against the FP64 sum of the unquantized binary32
+    sources (the worst over the P result buffers is reported)."""
     import torch
     P = b.send.shape[0]
     y64 = torch.zeros(_decode_rows(b.send[:1], dtype).shape[1], dtype=torch.float64, device=device)
@@ -413,47 +484,86 @@ def _lowprec_accuracy(b, dtype, xs, device):
     for r in range(P):
         y64 += _decode_rows(b.send[r:r + 1], dtype)[0].double()
         x64 += torch.from_numpy(xs[r]).to(device).double()
-    y = _decode_rows(b.recv[:1], dtype)[0].double()
-    return {"rel_l2_vs_fp64_of_decoded": float((y - y64).norm() / y64.norm()),
-            "rel_max_vs_fp64_of_decoded": float((y - y64).abs().max() / y64.abs().max()),
-            "rel_l2_vs_fp64_of_unquantized": float((y - x64).norm() / x64.norm()),
-            "bound_rel_l2": 1e-2 if dtype == "bf16" else 6e-2}
+    n64, m64, nx = y64.norm(), y64.abs().max(), x64.norm()
+    l2, mx, lx = 0.0, 0.0, 0.0
+    for r in range(P):
+        y = _decode_rows(b.recv[r:r + 1], dtype)[0].double()
+        l2 = max(l2, float((y - y64).norm() / n64))
+        mx = max(mx, float((y - y64).abs().max() / m64))
+        lx = max(lx, float((y - x64).norm() / nx))
+    return {"rel_l2_vs_fp64_of_decoded": l2, "rel_max_vs_fp64_of_decoded": mx,
+            "rel_l2_vs_fp64_of_unquantized": lx, "bound_rel_l2": 1e-2 if dtype == "bf16" else 6e-2,
+            "result_buffers": P}
 
 
-def run_ours(args):
+def _time_blocks(fn, k, min_s, stream):
+    """Blocks of ``k`` calls of fn, each bracketed by CUDA events on
+    ``stream``, until at least ``min_s`` seconds and three blocks have been
+    timed; returns the block times in ms."""
+    import torch
+    blocks, total = [], 0.0
+    while total < min_s or len(blocks) < 3:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        blocks.append(ms)
+        total += ms / 1e3
+    return blocks
+
+
+def _make_comm(H, P, dtype, args):
+    comm = H.Comm(P, dtype)
+    if args.item_bytes:
+        comm.set_option(H.OPT_ITEM_BYTES, args.item_bytes)
+    if args.order is not None:
+        comm.set_option(H.OPT_ORDER, args.order)
+    if args.ctas_per_sm:
+        comm.set_option(H.OPT_CTAS_PER_SM, args.ctas_per_sm)
+    if args.threads:
+        comm.set_option(H.OPT_THREADS, args.threads)
+    if args.ring > 1:
+        comm.set_option(H.OPT_RING, args.ring)
+    return comm
+
+
+def _graph_of(comms, kinds, device):
+    """One CUDA graph holding one start of every communicator (a start under
+    capture records only the executor launch; each replay is a complete
+    execution)."""
+    import torch
+    gs = torch.cuda.Stream(device)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gs):
+        for kind in kinds:
+            comms[kind].start(gs)
+    return graph
+
+
+def measure_collectives(args, device, world, workload, dtype, xs=None, e2e=True):
+    """The headline measurement of a single-GPU workload (the seven
+    collectives, or one All-reduce payload of the 64 MiB workload)."""
     import torch
 
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    device = torch.device("cuda", local)
-    if world > 1:
-        dist_init("nccl")
-
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_2408_05962_gb300 import collectives as C
     from paper_2408_05962_gb300 import hiccl as H
     from synth import uniform_ranks
 
-    W = WORKLOADS[args.workload]
+    W = WORKLOADS[workload]
     Pw, hier, stripe, pipe = W["ranks"], W["hierarchy"], W["stripe"], W["pipeline"]
     bpr = args.bytes_per_rank or W["bytes_per_rank"]
     d = bpr // 4 // Pw                            # values per chunk (bytes of fp32 values per rank / P)
-    dtype = args.dtype
-    if args.workload == "seven":
-        if dtype != "f32":
-            raise SystemExit("the seven-collective workload is fp32")
+    if workload == "seven":
         x = torch.from_numpy(uniform_ranks(Pw, d * Pw, seed=0))
+    elif dtype == "bf16":
+        x = _bf16_rows(xs)
+    elif dtype == "fp8":
+        x = None
     else:
-        from synth import scaled_normal_ranks
-        xs = scaled_normal_ranks(Pw, d * Pw, seed=0)
-        if dtype == "bf16":       # round to nearest even on the upper 16 bits (payload encoding)
-            t = torch.from_numpy(xs).view(torch.int32)
-            x = ((t + 0x7FFF + ((t >> 16) & 1)) >> 16).to(torch.int16)
-        elif dtype == "fp8":      # per-128-value block scales, e4m3 codes (payload encoding on the GPU)
-            x = None
-        else:
-            x = torch.from_numpy(xs)
+        x = torch.from_numpy(xs)
     comms, bufs, nbytes, pbytes, mbytes = {}, {}, {}, {}, {}
     kinds = tuple(args.kinds.split(",")) if args.kinds else W["kinds"]
     tdt = {"f32": torch.float32, "bf16": torch.int16, "fp8": torch.uint8}[dtype]
@@ -464,31 +574,22 @@ def run_ours(args):
         else:
             b.send.copy_(x[:, :b.send.shape[1]].to(device))
         b.recv.zero_()
-        comm = H.Comm(Pw, dtype)
-        if args.item_bytes:
-            comm.set_option(H.OPT_ITEM_BYTES, args.item_bytes)
-        if args.order is not None:
-            comm.set_option(H.OPT_ORDER, args.order)
-        if args.ctas_per_sm:
-            comm.set_option(H.OPT_CTAS_PER_SM, args.ctas_per_sm)
-        if args.threads:
-            comm.set_option(H.OPT_THREADS, args.threads)
-        if args.ring > 1:
-            comm.set_option(H.OPT_RING, args.ring)
+        comm = _make_comm(H, Pw, dtype, args)
         C.compose(comm, kind, d, b.send_ptrs(), b.recv_ptrs())
         comm.init(hier, stripe, pipe)
         rd, wr = comm.hbm_bytes()
         comms[kind], bufs[kind], nbytes[kind] = comm, b, rd + wr
         pbytes[kind] = H.nbytes(H.DTYPES[dtype], d * Pw)   # the paper's d*p per collective
         mbytes[kind] = min_bytes(kind, Pw, pbytes[kind])
+    del x
     stream = torch.cuda.current_stream(device)
     step_bytes = sum(nbytes.values())
 
-    def one_step(evs=None):
-        """All collectives back to back on one stream.  With ``evs`` (one
-        event per collective plus one) each launch is bracketed; without,
-        consecutive launches overlap their launch latency (programmatic
-        dependent launch)."""
+    def eager_step(evs=None):
+        """All collectives back to back on one stream through start / wait.
+        With ``evs`` (one event per collective plus one) each launch is
+        bracketed; without, consecutive launches overlap their launch latency
+        (programmatic dependent launch)."""
         for i, kind in enumerate(kinds):
             if evs is not None:
                 evs[i].record(stream)
@@ -498,42 +599,79 @@ def run_ours(args):
         for kind in kinds:
             comms[kind].wait()
 
-    for _ in range(max(args.warmup, 3)):
-        one_step()
+    warm = max(args.warmup, 3)
+    for _ in range(warm):
+        eager_step()
     torch.cuda.synchronize(device)
 
     # per-collective breakdown (untimed pass, events between the launches)
     per_kind = {kind: [] for kind in kinds}
-    for _ in range(min(args.steps, 10)):
+    for _ in range(10):
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(kinds) + 1)]
-        one_step(evs)
+        eager_step(evs)
         torch.cuda.synchronize(device)
         for i, kind in enumerate(kinds):
             per_kind[kind].append(evs[i].elapsed_time(evs[i + 1]))
 
-    clocks = ClockSampler(local)
+    graph = _graph_of(comms, kinds, device)
+    for _ in range(warm):
+        graph.replay()
+    torch.cuda.synchronize(device)
+
+    clocks = ClockSampler(device.index)
     clocks.start()
     time.sleep(0.3)
-    step_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier(device)
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        step_evs[k][0].record(stream)
-        one_step()
-        step_evs[k][1].record(stream)
-    torch.cuda.synchronize(device)
+    blocks = _time_blocks(graph.replay, args.steps, args.min_seconds, stream)
     wall = time.perf_counter() - t0
     barrier(device)
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in step_evs]
-    dev_s = sum(step_ms) / 1e3
-    tot_bytes, tot_s = aggregate(step_bytes * args.steps, dev_s, device)
+    # the same steps through start / wait on the host, one block
+    torch.cuda.synchronize(device)
+    eager_blocks = _time_blocks(eager_step, args.steps, 0.0, stream)
+    block_ms = statistics.median(blocks)
+    tot_bytes, tot_s = aggregate(step_bytes * args.steps, block_ms / 1e3, device)
     gbs = tot_bytes / tot_s / 1e9
     peak, peak_kind = measured_peak()
 
-    # end to end through the public API with host buffers (pinned), placed on
-    # the NUMA node of the GPU's host link where sysfs names one
+    e2e_line = None
+    if e2e:
+        e2e_line = _end_to_end(comms, bufs, kinds, tdt, step_bytes, args, device, stream)
+
+    coll = {}
+    for kind in kinds:
+        med = statistics.median(per_kind[kind])
+        coll[kind] = {"ms": med, "gbs": nbytes[kind] / med / 1e6, "frac": nbytes[kind] / med / 1e6 / peak,
+                      "dp_over_t_gbs": pbytes[kind] / med / 1e6, "schedule_bytes": nbytes[kind],
+                      "min_bytes": mbytes[kind], "min_gbs": mbytes[kind] / med / 1e6,
+                      "level_bytes": comms[kind].level_bytes(), "steps": comms[kind].plan_info()["steps"]}
+    accuracy = None
+    if dtype in ("bf16", "fp8") and "allreduce" in bufs:
+        accuracy = _lowprec_accuracy(bufs["allreduce"], dtype, xs, device)
+    out = {"value": gbs, "frac": gbs / world / peak, "peak": peak, "peak_kind": peak_kind,
+           "ms_per_step": block_ms / args.steps, "blocks": len(blocks), "steps_per_block": args.steps,
+           "block_ms": blocks, "timed_s": sum(blocks) / 1e3, "wall_s": wall, "clocks": clk,
+           "launches": len(kinds) * args.steps * len(blocks), "step_bytes": step_bytes,
+           "eager": {"value": step_bytes * args.steps / (statistics.median(eager_blocks) / 1e3) / 1e9,
+                     "ms_per_step": statistics.median(eager_blocks) / args.steps},
+           "collectives": coll, "e2e": e2e_line, "accuracy": accuracy}
+    for c in comms.values():
+        c.destroy()
+    del bufs, graph
+    torch.cuda.empty_cache()
+    return out
+
+
+def _end_to_end(comms, bufs, kinds, tdt, step_bytes, args, device, stream):
+    """End to end through the public API with host buffers (pinned), placed on
+    the NUMA node of the GPU's host link where sysfs names one: every step
+    copies each send buffer host -> device, starts and waits on every
+    collective, and copies each receive buffer device -> host.  The copies
+    overlap the collectives: H2D of collective k+1 and D2H of collective k-1
+    run on their own streams while collective k executes."""
+    import torch
     numa = host_node_of(device)
     with cpus_of_node(numa):
         h_send = {k: torch.empty(bufs[k].send.shape, dtype=tdt, pin_memory=True) for k in kinds}
@@ -543,8 +681,6 @@ def run_ours(args):
             h_recv[k].zero_()
     h2d = sum(t.numel() * t.element_size() for t in h_send.values())
     d2h = sum(t.numel() * t.element_size() for t in h_recv.values())
-    # copies overlap the collectives: H2D of collective k+1 and D2H of
-    # collective k-1 run on their own streams while collective k executes
     e2e_steps = max(1, min(args.steps, 3))
     s_in, s_out = torch.cuda.Stream(device), torch.cuda.Stream(device)
     t_e2e = 0.0
@@ -572,57 +708,30 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t_e2e
     eb, es = aggregate(step_bytes * e2e_steps, e2e_s, device)
     host_link = host_copy_rates(h_send, h_recv, bufs, kinds, s_in, device)
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "seven":
-        b, t, desc = oracle_sample(args.cpu_budget)
-        cpu = {"value": b / t / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc}
-
-    accuracy = None
-    if dtype in ("bf16", "fp8") and "allreduce" in bufs:
-        accuracy = _lowprec_accuracy(bufs["allreduce"], dtype, xs, device)
-
-    coll = {}
-    for kind in kinds:
-        med = statistics.median(per_kind[kind])
-        coll[kind] = {"ms": med, "gbs": nbytes[kind] / med / 1e6, "frac": nbytes[kind] / med / 1e6 / peak,
-                      "dp_over_t_gbs": pbytes[kind] / med / 1e6, "schedule_bytes": nbytes[kind],
-                      "min_bytes": mbytes[kind], "min_gbs": mbytes[kind] / med / 1e6,
-                      "level_bytes": comms[kind].level_bytes(), "steps": comms[kind].plan_info()["steps"]}
-    # DRAM bytes of an average executor launch of the default workload, from
-    # the committed ncu capture (null for other workloads or options, or once
-    # the executor sources have changed since the capture)
-    default_run = (args.workload == "seven" and not args.kinds and args.ring == 1 and not args.bytes_per_rank
-                   and not args.item_bytes and not args.ctas_per_sm and not args.threads and args.order is None)
-    step_traffic = recorded_traffic() if default_run else None
-    traffic = step_traffic / len(kinds) if step_traffic else None
-    line = {
-        "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": statistics.mean(step_ms),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
-        "data": "synthetic", "config": workload_config(
-            {"parallelism": f"replicas{world}", "payload": dtype, **({"ring": args.ring} if args.ring > 1 else {}),
-             **({"bytes_per_rank": bpr} if args.bytes_per_rank else {})},
-            args.workload),
-        "roofline": {"bound": "hbm", "achieved": gbs / world, "peak": peak, "unit": "GB/s",
-                     "frac": gbs / world / peak, "peak_source": peak_kind,
-                     "traffic": traffic, "traffic_per_step": step_traffic,
-                     "schedule_bytes_per_launch": step_bytes / len(kinds), "kernel": "hiccl_exec_kernel"},
-        "clocks": clk, "gpu_launches": len(kinds) * args.steps * world,
-        "e2e": {"value": eb / es / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "host_numa_node": numa, **host_link},
-        "collectives": coll, "wall_ms_per_step": wall / args.steps * 1e3,
-        "cpu_baseline": cpu,
-    }
-    if accuracy:
-        line["accuracy"] = accuracy
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    for c in comms.values():
-        c.destroy()
+    return {"value": eb / es / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "host_numa_node": numa, **host_link}
 
 
-def run_batch(args):
+def measure_allreduce64(args, device, dtypes=("f32", "bf16", "fp8")):
+    """The 64 MiB-per-rank All-reduce (P = 32 over {4, 8}, s = 1, m = 4) on
+    the same synthetic values as FP32, BF16 and FP8 payloads, each timed on
+    its own (graph-replayed blocks, as the headline) with its FP64 errors."""
+    from synth import scaled_normal_ranks
+    W = WORKLOADS["allreduce64"]
+    xs = scaled_normal_ranks(W["ranks"], W["bytes_per_rank"] // 4, seed=0)
+    sub = argparse.Namespace(**vars(args))
+    sub.kinds, sub.bytes_per_rank, sub.steps, sub.min_seconds = "", 0, 10, 0.25
+    out = {}
+    for dt in dtypes:
+        r = measure_collectives(sub, device, 1, "allreduce64", dt, xs=xs, e2e=False)
+        out[dt] = {"gbs": r["value"], "frac": r["frac"], "ms": r["ms_per_step"],
+                   "schedule_bytes": r["step_bytes"], "eager_gbs": r["eager"]["value"],
+                   **({"accuracy": r["accuracy"]} if r["accuracy"] else {})}
+    out["config"] = workload_config("allreduce64", 1, "f32+bf16+fp8")
+    return out
+
+
+def measure_batch(args, device, steps):
     """Batched workload: 256 collectives (All-gather / Reduce-scatter /
     All-reduce drawn uniformly, P from {8, 16, 32} with two-level
     hierarchies, per-rank sizes log-uniform 4 KiB .. 16 MiB, fp32 and bf16
@@ -631,17 +740,8 @@ def run_batch(args):
     octave).  Timed three ways on one stream: one launch per collective (all
     256 enqueued, then waited), one grouped launch, and the grouped launch
     replayed from a CUDA graph."""
-    import math
-
     import torch
 
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    device = torch.device("cuda", local)
-    if world > 1:
-        dist_init("nccl")
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_2408_05962_gb300 import collectives as C
     from paper_2408_05962_gb300 import hiccl as H
     from synth import batch_mix
@@ -652,6 +752,7 @@ def run_batch(args):
     comms, bufs, tuned = [], [], {}
     stream = torch.cuda.current_stream(device)
     total_bytes = 0
+    t_setup = time.perf_counter()
     for dsc in descs:
         P, h, dt = dsc["P"], dsc["hierarchy"], dsc["dtype"]
         es = 4 if dt == "f32" else 2
@@ -675,6 +776,7 @@ def run_batch(args):
         total_bytes += rd + wr
         comms.append(comm)
         bufs.append(b)
+    t_setup = time.perf_counter() - t_setup
 
     def separate():
         for c in comms:
@@ -699,59 +801,186 @@ def run_batch(args):
     for _ in range(3):
         graph.replay()
     torch.cuda.synchronize(device)
+    t_sep = statistics.median(_time_blocks(separate, steps, 0.2, stream)) / steps / 1e3
+    t_grp = statistics.median(_time_blocks(grouped, steps, 0.2, stream)) / steps / 1e3
+    t_graph = statistics.median(_time_blocks(graph.replay, steps, 0.2, stream)) / steps / 1e3
+    out = {"schedule_bytes": total_bytes, "one_launch_each_ms": t_sep * 1e3,
+           "grouped_ms": t_grp * 1e3, "graph_ms": t_graph * 1e3,
+           "one_launch_each_gbs": total_bytes / t_sep / 1e9, "grouped_gbs": total_bytes / t_grp / 1e9,
+           "graph_gbs": total_bytes / t_graph / 1e9, "speedup_vs_one_launch_each": t_sep / t_graph,
+           "tuned_configs": len(tuned), "setup_s": t_setup,
+           "config": "256 collectives (All-gather/Reduce-scatter/All-reduce), P in {8,16,32}, two-level "
+                     "hierarchies, 4 KiB..16 MiB per rank log-uniform, fp32/bf16, one persistent launch "
+                     "replayed from a CUDA graph; stripe, pipeline and executor knobs autotuned"}
+    for c in comms:
+        c.destroy()
+    grp.destroy()
+    del bufs, graph
+    torch.cuda.empty_cache()
+    return out
 
-    def timed(fn, k):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier(device)
-        torch.cuda.synchronize(device)
-        e0.record(stream)
-        for _ in range(k):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize(device)
-        return e0.elapsed_time(e1) / 1e3 / k
 
+def serve_trace(rate, duration, budget_gb, slots, max_batch, seed=0):
+    """Serve one Poisson arrival trace (synth.poisson_requests) with
+    serving.Server; returns its latency and throughput summary."""
+    from paper_2408_05962_gb300.serving import Request, Server, latency_stats
+    from synth import poisson_requests
+
+    descs = poisson_requests(rate, duration, seed=seed)
+    srv = Server(budget_gb << 30, slots=slots, max_batch=max_batch, planners=8)
+    t0 = time.perf_counter()
+    k = 0
+    while k < len(descs) or srv.busy():
+        now = time.perf_counter() - t0
+        while k < len(descs) and descs[k]["t"] <= now:
+            dsc = descs[k]
+            srv.submit(Request(kind=dsc["kind"], P=dsc["P"], hierarchy=dsc["hierarchy"],
+                               bytes_per_rank=dsc["bytes_per_rank"], dtype=dsc["dtype"],
+                               t_arrival=t0 + dsc["t"]))
+            k += 1
+        srv.poll()
+    wall = time.perf_counter() - t0
+    srv.close()
+    done = [r for r in srv.done if not r.error]
+    st = latency_stats(done)
+    total = sum(r.hbm_bytes for r in done)
+    out = {"rate_per_s": rate, "duration_s": duration, "requests": len(descs), "completed": len(done),
+           "errors": len(srv.done) - len(done), "wall_s": wall, "achieved_req_per_s": len(done) / wall,
+           "gbs": total / wall / 1e9, "launches": srv.launches, **st}
+    for key in ("plan_cache_hits", "plan_cache_misses"):
+        if hasattr(srv, key):
+            out[key] = getattr(srv, key)
+    return out
+
+
+def measure_serving_short(args):
+    """Config 5's serving loop (concurrent launch slots) for a short run at
+    the offered 2000 requests/s and at a sub-saturating 100 requests/s."""
+    out = {}
+    for rate in (args.rate, args.low_rate):
+        out[f"{rate:g}/s"] = serve_trace(rate, args.extras_serve_s, args.budget_gb, 8, 1)
+    out["config"] = (f"serving: Poisson arrivals of the seven collectives, P in {{8,16,64}}, 1 KiB..256 MiB per "
+                     f"rank, fp32/bf16/int32, {args.budget_gb} GB budget, 8 concurrent launch slots, "
+                     f"{args.extras_serve_s:g} s of arrivals per rate (the 60 s run: --workload serve)")
+    return out
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        dist_init("nccl")
+
+    import __graft_entry__
+    __graft_entry__.build()
+
+    xs = None
+    if args.workload == "allreduce64":
+        from synth import scaled_normal_ranks
+        xs = scaled_normal_ranks(WORKLOADS["allreduce64"]["ranks"],
+                                 (args.bytes_per_rank or WORKLOADS["allreduce64"]["bytes_per_rank"]) // 4, seed=0)
+    elif args.dtype != "f32":
+        raise SystemExit("the seven-collective workload is fp32")
+    r = measure_collectives(args, device, world, args.workload, args.dtype, xs=xs)
+    peak = r["peak"]
+
+    extras = {}
+    if world == 1 and rank == 0 and args.workload == "seven" and not args.no_extras and not args.kinds:
+        t = time.perf_counter()
+        extras["allreduce64"] = measure_allreduce64(args, device)
+        extras["batch256"] = measure_batch(args, device, 3)
+        extras["serving"] = measure_serving_short(args)
+        extras["extras_wall_s"] = time.perf_counter() - t
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "seven":
+        cpu = cpu_baseline(args.cpu_budget)
+
+    default_run = (args.workload == "seven" and not args.kinds and args.ring == 1 and not args.bytes_per_rank
+                   and not args.item_bytes and not args.ctas_per_sm and not args.threads and args.order is None)
+    # DRAM bytes of an average executor launch of the default workload, from
+    # the committed ncu capture (null for other workloads or options, or once
+    # the executor sources have changed since the capture)
+    step_traffic = recorded_traffic() if default_run else None
+    nk = len(r["collectives"])
+    traffic = step_traffic / nk if step_traffic else None
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
+        "data": "synthetic",
+        "config": workload_config(args.workload, world, args.dtype,
+                                  {**({"ring": args.ring} if args.ring > 1 else {}),
+                                   **({"bytes_per_rank": args.bytes_per_rank} if args.bytes_per_rank else {}),
+                                   **({"collectives": args.kinds.split(",")} if args.kinds else {})}),
+        "timing": {"method": "CUDA graph of one step (one start per collective), replayed; blocks of "
+                             f"{args.steps} replays bracketed by CUDA events until >= {args.min_seconds:g} s; "
+                             "median block", "blocks": r["blocks"], "timed_s": r["timed_s"],
+                   "block_ms": r["block_ms"], "eager": r["eager"]},
+        "roofline": {"bound": "hbm", "achieved": r["value"] / world, "peak": peak, "unit": "GB/s",
+                     "frac": r["frac"], "peak_source": r["peak_kind"],
+                     "traffic": traffic, "traffic_per_step": step_traffic,
+                     "schedule_bytes_per_launch": r["step_bytes"] / nk, "kernel": "hiccl_exec_kernel"},
+        "clocks": r["clocks"], "gpu_launches": r["launches"] * world,
+        "e2e": r["e2e"], "collectives": r["collectives"], "cpu_baseline": cpu,
+    }
+    if r["accuracy"]:
+        line["accuracy"] = r["accuracy"]
+    if extras:
+        line["allreduce64"] = extras["allreduce64"]
+        line["batch256"] = extras["batch256"]
+        line["serving"] = extras["serving"]
+        head = extras["serving"].get(f"{args.rate:g}/s", {})
+        line["p50_ms"], line["p99_ms"] = head.get("p50_ms"), head.get("p99_ms")
+        line["extras_wall_s"] = extras["extras_wall_s"]
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        dist_init("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
     clocks = ClockSampler(local)
     clocks.start()
-    time.sleep(0.3)
-    t_sep = timed(separate, args.steps)
-    t_grp = timed(grouped, args.steps)
-    t_graph = timed(graph.replay, args.steps)
+    b = measure_batch(args, device, args.steps)
     clk = clocks.stop()
-    tb, tg = aggregate(total_bytes * args.steps, t_graph * args.steps, device)
+    tb, tg = aggregate(b["schedule_bytes"] * args.steps, b["graph_ms"] / 1e3 * args.steps, device)
     peak, peak_kind = measured_peak()
     gbs = tb / tg / 1e9
     line = {
         "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-        "warmup": 3, "ms_per_step": t_graph * 1e3, "higher_is_better": True, "scaling": "weak",
+        "warmup": 3, "ms_per_step": b["graph_ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
-        "config": {"workload": "256 collectives (All-gather/Reduce-scatter/All-reduce), P in {8,16,32}, "
-                               "two-level hierarchies, 4 KiB..16 MiB per rank log-uniform, fp32/bf16, "
-                               "one persistent launch replayed from a CUDA graph; stripe, pipeline and "
-                               "executor knobs autotuned", "collectives": 256, "parallelism": f"replicas{world}",
-                   "tuned_configs": len(tuned)},
+        "config": {"workload": b["config"], "collectives": 256, "parallelism": f"replicas{world}",
+                   "tuned_configs": b["tuned_configs"]},
         "roofline": {"bound": "hbm", "achieved": gbs / world, "peak": peak, "unit": "GB/s",
                      "frac": gbs / world / peak, "peak_source": peak_kind, "traffic": None,
                      "kernel": "hiccl_exec_kernel"},
-        "clocks": clk, "gpu_launches": args.steps * world,
-        "batch": {"schedule_bytes": total_bytes, "one_launch_each_ms": t_sep * 1e3,
-                  "grouped_ms": t_grp * 1e3, "graph_ms": t_graph * 1e3,
-                  "one_launch_each_gbs": total_bytes / t_sep / 1e9, "grouped_gbs": total_bytes / t_grp / 1e9,
-                  "graph_gbs": total_bytes / t_graph / 1e9, "speedup_vs_one_launch_each": t_sep / t_graph},
+        "clocks": clk, "gpu_launches": args.steps * world, "batch": b,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
 def run_serve(args):
-    """Serving workload: Poisson arrivals (synth.poisson_requests seed 0) of the
-    seven collectives, P in {8, 16, 64} ({2,4}, {4,4}, {4,4,4}), per-rank sizes
-    log-uniform 1 KiB .. 256 MiB, fp32 / bf16 / int32, admitted under a 64 GB
-    device-memory budget with continuous batching (serving.Server: 8 launch
-    slots, requests overlapping on the device; and grouped launches of up to
-    16 requests on 2 slots).  The same arrival trace is also served one
-    launch at a time (1 slot).  Reports p50 / p99 latency and the aggregate
-    schedule GB/s of each."""
+    """Serving workload (config 5): Poisson arrivals (synth.poisson_requests
+    seed 0) of the seven collectives, P in {8, 16, 64} ({2,4}, {4,4},
+    {4,4,4}), per-rank sizes log-uniform 1 KiB .. 256 MiB, fp32 / bf16 /
+    int32, admitted under a 64 GB device-memory budget with continuous
+    batching (serving.Server: 8 launch slots, requests overlapping on the
+    device; and grouped launches of up to 16 requests on 2 slots).  The same
+    arrival trace is also served one launch at a time (1 slot).  Reports p50
+    / p99 latency and the aggregate schedule GB/s of each."""
     import torch
 
     world, rank, local = dist_env()
@@ -760,36 +989,15 @@ def run_serve(args):
         dist_init("nccl")
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2408_05962_gb300.serving import Request, Server, latency_stats
-    from synth import poisson_requests
-
-    def serve(descs, slots, max_batch):
-        srv = Server(args.budget_gb << 30, slots=slots, max_batch=max_batch, planners=8)
-        t0 = time.perf_counter()
-        k = 0
-        while k < len(descs) or srv.busy():
-            now = time.perf_counter() - t0
-            while k < len(descs) and descs[k]["t"] <= now:
-                dsc = descs[k]
-                srv.submit(Request(kind=dsc["kind"], P=dsc["P"], hierarchy=dsc["hierarchy"],
-                                   bytes_per_rank=dsc["bytes_per_rank"], dtype=dsc["dtype"],
-                                   t_arrival=t0 + dsc["t"]))
-                k += 1
-            srv.poll()
-        wall = time.perf_counter() - t0
-        srv.close()
-        done = [r for r in srv.done if not r.error]
-        st = latency_stats(done)
-        total = sum(r.hbm_bytes for r in done)
-        return {"requests": len(descs), "completed": len(done), "errors": len(srv.done) - len(done),
-                "wall_s": wall, "achieved_req_per_s": len(done) / wall, "gbs": total / wall / 1e9,
-                "launches": srv.launches, **st}
 
     out = {}
+    clocks = ClockSampler(local)
+    clocks.start()
     for rate in (args.rate, args.low_rate):
-        descs = poisson_requests(rate, args.duration, seed=0)
-        out[f"{rate:g}/s"] = {"batched": serve(descs, 8, 1), "grouped": serve(descs, 2, 16),
-                              "one_launch_at_a_time": serve(descs, 1, 1)}
+        out[f"{rate:g}/s"] = {"batched": serve_trace(rate, args.duration, args.budget_gb, 8, 1),
+                              "grouped": serve_trace(rate, args.duration, args.budget_gb, 2, 16),
+                              "one_launch_at_a_time": serve_trace(rate, args.duration, args.budget_gb, 1, 1)}
+    clk = clocks.stop()
     head = out[f"{args.rate:g}/s"]["batched"]
     peak, peak_kind = measured_peak()
     line = {
@@ -802,7 +1010,7 @@ def run_serve(args):
         "roofline": {"bound": "hbm", "achieved": head["gbs"], "peak": peak, "unit": "GB/s",
                      "frac": head["gbs"] / peak, "peak_source": peak_kind, "traffic": None,
                      "kernel": "hiccl_exec_kernel"},
-        "serving": out, "p50_ms": head.get("p50_ms"), "p99_ms": head.get("p99_ms"),
+        "clocks": clk, "serving": out, "p50_ms": head.get("p50_ms"), "p99_ms": head.get("p99_ms"),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -811,18 +1019,22 @@ def run_serve(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20, help="steps (graph replays) per timed block")
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--min-seconds", type=float, default=1.0, help="length of the timed region (blocks of --steps)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=14.0)
     ap.add_argument("--ref-budget", type=float, default=7.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline only (no 64 MiB All-reduce payloads, batch of 256, served run)")
+    ap.add_argument("--extras-serve-s", type=float, default=5.0, help="seconds of arrivals per rate in the default line")
     ap.add_argument("--item-bytes", type=int, default=0, help="executor work-item size (0: library default)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="executor CTAs per SM (0: library default)")
     ap.add_argument("--workload", default="seven", choices=sorted(WORKLOADS) + ["batch256", "serve"])
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: offered requests per second")
     ap.add_argument("--low-rate", type=float, default=100.0, help="serve: a sub-saturating rate")
-    ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     ap.add_argument("--budget-gb", type=int, default=64, help="serve: device-memory budget")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8"],
                     help="payload of the allreduce64 workload (accumulation is FP32)")

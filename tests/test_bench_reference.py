@@ -45,3 +45,24 @@ def test_reference_arm_two_ranks():
     assert len(lines) == 1
     _check(lines[0])
     assert lines[0]["n_gpus"] == 2
+
+
+def test_reference_config_matches_the_gpu_arm():
+    """Both arms describe the workload with the same dict."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = subprocess.run([sys.executable, "bench.py", *ARGS], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    line = _lines(r.stdout)[0]
+    assert line["config"] == bench.workload_config("seven", 1, "f32")
+
+
+def test_cpu_baseline_all_cores_leg():
+    """The oracle on several spawned processes at once: every process plans
+    and simulates its own collective; the bytes add up and the line states
+    the process count."""
+    sys.path.insert(0, ROOT)
+    import bench
+    b, t, desc = bench.oracle_all_cores(0.3, 2)
+    assert b > 0 and 0.3 <= t < 5.0 and "2 processes" in desc
+    b1, t1 = bench._simulate_for("scatter", 0.2)
+    assert b1 > 0 and t1 >= 0.2
