@@ -820,13 +820,14 @@ def measure_batch(args, device, steps):
     return out
 
 
-def serve_trace(rate, duration, budget_gb, slots, max_batch, seed=0):
-    """Serve one Poisson arrival trace (synth.poisson_requests) with
+def serve_trace(rate, duration, budget_gb, slots, max_batch, seed=0, shapes=0):
+    """Serve one Poisson arrival trace (synth.poisson_requests; ``shapes`` > 0:
+    arrivals drawn from that many recurring request shapes) with
     serving.Server; returns its latency and throughput summary."""
     from paper_2408_05962_gb300.serving import Request, Server, latency_stats
     from synth import poisson_requests
 
-    descs = poisson_requests(rate, duration, seed=seed)
+    descs = poisson_requests(rate, duration, seed=seed, shapes=shapes)
     srv = Server(budget_gb << 30, slots=slots, max_batch=max_batch, planners=8)
     t0 = time.perf_counter()
     k = 0
@@ -844,7 +845,8 @@ def serve_trace(rate, duration, budget_gb, slots, max_batch, seed=0):
     done = [r for r in srv.done if not r.error]
     st = latency_stats(done)
     total = sum(r.hbm_bytes for r in done)
-    out = {"rate_per_s": rate, "duration_s": duration, "requests": len(descs), "completed": len(done),
+    out = {"rate_per_s": rate, "duration_s": duration, "shapes": shapes or "all distinct", "requests": len(descs),
+           "completed": len(done),
            "errors": len(srv.done) - len(done), "wall_s": wall, "achieved_req_per_s": len(done) / wall,
            "gbs": total / wall / 1e9, "launches": srv.launches, **st}
     for key in ("plan_cache_hits", "plan_cache_misses"):
@@ -859,9 +861,12 @@ def measure_serving_short(args):
     out = {}
     for rate in (args.rate, args.low_rate):
         out[f"{rate:g}/s"] = serve_trace(rate, args.extras_serve_s, args.budget_gb, 8, 1)
+        out[f"{rate:g}/s recurring shapes"] = serve_trace(rate, args.extras_serve_s, args.budget_gb, 8, 1,
+                                                          shapes=args.shapes)
     out["config"] = (f"serving: Poisson arrivals of the seven collectives, P in {{8,16,64}}, 1 KiB..256 MiB per "
                      f"rank, fp32/bf16/int32, {args.budget_gb} GB budget, 8 concurrent launch slots, "
-                     f"{args.extras_serve_s:g} s of arrivals per rate (the 60 s run: --workload serve)")
+                     f"{args.extras_serve_s:g} s of arrivals per rate; 'recurring shapes': the same arrivals drawn "
+                     f"from {args.shapes} shapes (memoized plans reused); the 60 s run: --workload serve")
     return out
 
 
@@ -996,7 +1001,9 @@ def run_serve(args):
     for rate in (args.rate, args.low_rate):
         out[f"{rate:g}/s"] = {"batched": serve_trace(rate, args.duration, args.budget_gb, 8, 1),
                               "grouped": serve_trace(rate, args.duration, args.budget_gb, 2, 16),
-                              "one_launch_at_a_time": serve_trace(rate, args.duration, args.budget_gb, 1, 1)}
+                              "one_launch_at_a_time": serve_trace(rate, args.duration, args.budget_gb, 1, 1),
+                              "batched_recurring_shapes": serve_trace(rate, args.duration, args.budget_gb, 8, 1,
+                                                                      shapes=args.shapes)}
     clk = clocks.stop()
     head = out[f"{args.rate:g}/s"]["batched"]
     peak, peak_kind = measured_peak()
@@ -1036,6 +1043,7 @@ def main(argv=None):
     ap.add_argument("--low-rate", type=float, default=100.0, help="serve: a sub-saturating rate")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     ap.add_argument("--budget-gb", type=int, default=64, help="serve: device-memory budget")
+    ap.add_argument("--shapes", type=int, default=64, help="serve: request shapes of the recurring-shape runs")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8"],
                     help="payload of the allreduce64 workload (accumulation is FP32)")
     ap.add_argument("--kinds", default="", help="comma-separated subset of the seven collectives (profiling)")

@@ -146,7 +146,10 @@ hiccl_status_t hiccl_init(hiccl_comm_t comm, const int *hierarchy, int nlevels,
 
 /* Host-only variant of hiccl_init: factorize and validate without touching
  * any GPU, so that the plan queries below work on a machine without one.
- * Pointers are only compared, never dereferenced.  hiccl_init may follow. */
+ * Pointers are only compared, never dereferenced.  hiccl_init may follow:
+ * with the same hierarchy, stripe and pipeline it uploads this plan without
+ * factorizing again (a caller can plan on one thread, check the plan's
+ * device footprint with hiccl_plan_info, and upload it later). */
 hiccl_status_t hiccl_plan(hiccl_comm_t comm, const int *hierarchy, int nlevels,
                           int stripe, int pipeline);
 

@@ -1506,7 +1506,12 @@ hiccl_status_t hiccl_init(hiccl_comm_t c, const int *hierarchy, int nlevels, int
     if (!c) return HICCL_ERR_INVALID;
     if (c->state == hiccl_comm::READY || c->state == hiccl_comm::RUNNING)
       return fail(c, HICCL_ERR_STATE, "already initialized");
-    hiccl_status_t st = build_plan(c, hierarchy, nlevels, stripe, pipeline);
+    // a plan made by hiccl_plan with the same parameters is uploaded as it is:
+    // nothing that feeds the factorizer can change in the planned state
+    const bool same = c->state == hiccl_comm::PLANNED && c->plan.valid && hierarchy && nlevels >= 1 &&
+                      c->plan.hierarchy == std::vector<int>(hierarchy, hierarchy + nlevels) &&
+                      c->plan.stripe == stripe && c->plan.pipeline == pipeline;
+    hiccl_status_t st = same ? HICCL_OK : build_plan(c, hierarchy, nlevels, stripe, pipeline);
     if (st != HICCL_OK) return st;
     c->state = hiccl_comm::PLANNED;
     st = dev_upload(c);

@@ -6,25 +6,34 @@ payload) arrive at any time.  The server
 * admits a request when its buffers fit in the device-memory budget (one
   device arena, first-fit; FIFO, so a large request is never starved by later
   small ones), keeping buffers and step tables on the device;
-* plans admitted requests on a pool of host threads (the native factorizer
-  and the table upload; ctypes releases the GIL during the calls);
+* memoizes plans (Sec. 5.2: a schedule is optimized once and reused): a
+  finished request leaves its communicator -- step table, counters, relay
+  buffers -- and its arena buffers resident, keyed by the request's shape; a
+  later request of the same shape takes them over with no factorization, no
+  upload and no allocation.  Idle entries are evicted, least recently used
+  first, when the budget needs their memory;
+* plans the other admitted requests on a pool of host threads (the native
+  factorizer), counts each plan's device footprint (table, counters, relay
+  buffers) against the budget together with the buffers, then uploads it on
+  the pool;
 * launches planned requests on whichever of its ``slots`` CUDA streams is
   free -- each request alone (``group_max`` 1), or up to ``group_max``
   waiting requests together as one grouped persistent launch
   (``hiccl_group``); requests that arrive while others run take the next free
   slot, and launches on different slots overlap on the device;
-* retires a launch when its event completes, freeing its memory and recording
-  each request's latency (completion observed minus arrival).
+* retires a launch when its event completes, recording each request's
+  latency (completion observed minus arrival).
 
 Planning uses stripe 1 and pipeline 1 for every request: on one GPU every
-level is HBM, and the cost of planning is paid per request.
+level is HBM.  The polling loop yields the interpreter lock once per round,
+so the planner threads run as soon as their native calls return.
 """
 from __future__ import annotations
 
 import bisect
 import threading
 import time
-from collections import deque
+from collections import OrderedDict, deque
 from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
@@ -71,6 +80,57 @@ class DeviceArena:
             self.free_list.pop(k)
 
 
+class PlanCache:
+    """Idle memoized plans by request shape, least recently used first.
+
+    An entry is whatever the server stores for a finished request (its
+    communicator, arena region, buffer pointers, footprint); ``take`` hands an
+    idle entry of a shape to a new request (the oldest of that shape), ``put``
+    returns one after use, ``evict_lru`` removes the least recently used idle
+    entry of any shape.  Every operation is O(1).  ``hits`` and ``misses``
+    count admitted requests (the server updates them)."""
+
+    def __init__(self, max_entries: int = 4096):
+        self.max_entries = max_entries
+        self.by_shape = {}             # shape -> deque of serials, oldest first
+        self.lru = OrderedDict()       # serial -> (shape, entry), oldest first
+        self.serial = 0
+        self.hits = 0
+        self.misses = 0
+
+    def __len__(self):
+        return len(self.lru)
+
+    def take(self, shape):
+        q = self.by_shape.get(shape)
+        if not q:
+            return None
+        entry = self.lru.pop(q.popleft())[1]
+        if not q:
+            del self.by_shape[shape]
+        return entry
+
+    def put(self, shape, entry):
+        """Store an idle entry; returns the entries pushed out by the size cap."""
+        self.serial += 1
+        self.by_shape.setdefault(shape, deque()).append(self.serial)
+        self.lru[self.serial] = (shape, entry)
+        out = []
+        while len(self.lru) > self.max_entries:
+            out.append(self.evict_lru())
+        return out
+
+    def evict_lru(self):
+        if not self.lru:
+            return None
+        serial, (shape, entry) = self.lru.popitem(last=False)
+        q = self.by_shape[shape]
+        q.popleft()                    # serials grow, so the oldest overall is the oldest of its shape
+        if not q:
+            del self.by_shape[shape]
+        return entry
+
+
 @dataclass
 class Request:
     kind: str
@@ -88,6 +148,9 @@ class Request:
     region: tuple = ()
     comm: object = None
     hbm_bytes: int = 0
+    dev_bytes: int = 0           # table, counters and relays of its communicator
+    cached: bool = False         # served from a memoized plan
+    reserved: bool = False       # dev_bytes counted against the budget
     t_admit: float = 0.0
     t_launch: float = 0.0
     t_done: float = 0.0
@@ -95,23 +158,56 @@ class Request:
 
 
 class Server:
+    """The serving loop; ``poll`` makes one round of progress.
+
+    budget_bytes bounds the device memory of everything the server keeps:
+    the requests' buffers (in one arena of that size) plus the tables,
+    counters and relay buffers of their communicators, memoized ones
+    included (a grouped launch's combined table is counted while it runs).
+    ``cache_entries`` caps the memoized plans (0 disables them);
+    ``comm_options`` ({hiccl option: value}) is applied to every request's
+    communicator before planning."""
+
     def __init__(self, budget_bytes: int, slots: int = 8, max_batch: int = 1, planners: int = 4,
-                 device="cuda", on_admit=None, on_done=None):
+                 device="cuda", on_admit=None, on_done=None, cache_entries: int = 4096, comm_options=None):
         import torch
         self.device = torch.device(device)
+        self.budget = budget_bytes
         self.arena = DeviceArena(budget_bytes, self.device)
-        self.slots = [{"stream": torch.cuda.Stream(self.device), "event": None, "group": None, "reqs": []}
-                      for _ in range(slots)]
+        # a server on the CPU admits, plans and memoizes but launches nothing
+        # (its host logic is tested that way on machines without a GPU)
+        cuda = self.device.type == "cuda"
+        self.slots = [{"stream": torch.cuda.Stream(self.device) if cuda else None, "event": None, "group": None,
+                       "reqs": [], "group_bytes": 0} for _ in range(slots)]
         self.max_batch = max_batch
         self.pool = ThreadPoolExecutor(max_workers=planners)
         self.waiting: deque = deque()     # submitted, not admitted
-        self.planning: list = []          # (future, request)
-        self.ready: deque = deque()       # planned, not launched
+        self.planning: list = []          # (future, request): host planning
+        self.to_upload: deque = deque()   # planned, waiting for device memory
+        self.uploading: list = []         # (future, request)
+        self.ready: deque = deque()       # on the device, not launched
         self.done: list = []
         self.on_admit, self.on_done = on_admit, on_done
         self.lock = threading.Lock()
         self.next_id = 0
         self.launches = 0
+        # memoized plans apply to requests launched alone; grouped launches
+        # build one combined table per group and keep no per-request state
+        self.cache = PlanCache(cache_entries if max_batch == 1 else 0)
+        self.dev_bytes = 0                # tables, counters, relays of live communicators
+        self.comm_options = dict(comm_options or {})
+
+    @property
+    def plan_cache_hits(self):
+        return self.cache.hits
+
+    @property
+    def plan_cache_misses(self):
+        return self.cache.misses
+
+    def device_bytes(self) -> int:
+        """Device memory held against the budget (buffers + communicators)."""
+        return self.arena.used + self.dev_bytes
 
     # -- requests ---------------------------------------------------------------
     def submit(self, req: Request) -> int:
@@ -129,14 +225,56 @@ class Server:
         ls, lr = buffer_lengths(req.kind, req.P, req.d)
         return ls * es, lr * es
 
+    @staticmethod
+    def _shape(req: Request):
+        return (req.kind, req.P, tuple(req.hierarchy), req.d, req.dtype, req.root)
+
+    def _release_entry(self, e):
+        """Free a memoized entry: its communicator and its arena region."""
+        e["comm"].destroy()
+        self.dev_bytes -= e["dev_bytes"]
+        self.arena.free(*e["region"])
+
+    def _fits(self, extra: int) -> bool:
+        return self.arena.used + self.dev_bytes + extra <= self.budget
+
+    def _make_room(self, need: int) -> bool:
+        """Evict idle memoized plans (least recently used first) until
+        ``need`` more bytes fit in the budget."""
+        while not self._fits(need):
+            e = self.cache.evict_lru()
+            if e is None:
+                return False
+            self._release_entry(e)
+        return True
+
     def _admit(self):
         while self.waiting:
             req = self.waiting[0]
             sb, rb = self._layout(req)
-            got = self.arena.alloc(req.P * (sb + rb))
+            if self.max_batch == 1:
+                e = self.cache.take(self._shape(req))
+                if e is not None:                      # memoized: nothing to plan, upload or allocate
+                    self.cache.hits += 1
+                    self.waiting.popleft()
+                    req.comm, req.region = e["comm"], e["region"]
+                    req.send_ptrs, req.recv_ptrs = e["send_ptrs"], e["recv_ptrs"]
+                    req.hbm_bytes, req.dev_bytes, req.cached = e["hbm_bytes"], e["dev_bytes"], True
+                    req.reserved = True
+                    req.t_admit = time.perf_counter()
+                    if self.on_admit:
+                        self.on_admit(req)
+                    self.ready.append(req)
+                    continue
+            need = req.P * (sb + rb)
+            got = self.arena.alloc(need) if self._make_room(need) else None
+            while got is None and len(self.cache):     # fragmentation: free idle regions until it fits
+                self._release_entry(self.cache.evict_lru())
+                got = self.arena.alloc(need)
             if got is None:
                 return                     # FIFO: wait until memory frees
             self.waiting.popleft()
+            self.cache.misses += 1
             off, n = got
             req.region = (off, n)
             base = self.arena.base + off
@@ -145,35 +283,67 @@ class Server:
             req.t_admit = time.perf_counter()
             if self.on_admit:
                 self.on_admit(req)
-            self.planning.append((self.pool.submit(self._plan, req, self.max_batch == 1), req))
+            self.planning.append((self.pool.submit(self._plan, req, self.comm_options), req))
 
     @staticmethod
-    def _plan(req: Request, upload: bool):
+    def _plan(req: Request, options: dict):
+        """Host planning (pool thread): factorize, and note the plan's device footprint."""
         comm = H.Comm(req.P, req.dtype)
+        req.comm = comm
+        for opt, val in options.items():
+            comm.set_option(opt, val)
         comm.add_collective(req.kind, req.d, req.send_ptrs, req.recv_ptrs, req.root)
-        if upload:     # launched alone: its own table, uploaded here on the planner thread
-            comm.init(req.hierarchy, 1, 1)
-        else:          # joins a group, which uploads one combined table
-            comm.plan(req.hierarchy, 1, 1)
+        comm.plan(req.hierarchy, 1, 1)
         rd, wr = comm.hbm_bytes()
         req.hbm_bytes = rd + wr
-        req.comm = comm
+        info = comm.plan_info()
+        req.dev_bytes = info["table_bytes"] + info["scratch_bytes"]
 
-    def _collect_planned(self):
+    @staticmethod
+    def _upload(req: Request):
+        """Upload of a host plan (pool thread; the plan is not factorized again)."""
+        req.comm.init(req.hierarchy, 1, 1)
+
+    def _collect(self, pending, on_ok):
         keep = []
-        for fut, req in self.planning:
+        for fut, req in pending:
             if fut.done():
                 err = fut.exception()
                 if err is not None:
                     req.error = str(err)
                     self._finish(req, time.perf_counter())
                 else:
-                    self.ready.append(req)
+                    on_ok(req)
             else:
                 keep.append((fut, req))
-        self.planning = keep
+        return keep
+
+    def _reserve_uploads(self):
+        """Count planned requests' tables and relays against the budget (in
+        order) and upload those that fit."""
+        while self.to_upload:
+            req = self.to_upload[0]
+            if self.max_batch > 1:                     # group members stay host plans
+                self.to_upload.popleft()
+                req.dev_bytes = 0
+                self.ready.append(req)
+                continue
+            if not self._make_room(req.dev_bytes):
+                if any(s["event"] is not None for s in self.slots) or self.uploading:
+                    return                             # memory frees as launches retire
+                # nothing else holds memory: the request alone exceeds the budget
+                self.to_upload.popleft()
+                req.error = "device footprint exceeds the budget"
+                self._finish(req, time.perf_counter())
+                continue
+            self.to_upload.popleft()
+            self.dev_bytes += req.dev_bytes
+            req.reserved = True
+            self.uploading.append((self.pool.submit(self._upload, req), req))
 
     def _launch(self):
+        if self.device.type != "cuda":
+            return
         for sl in self.slots:
             if not self.ready:
                 return
@@ -182,7 +352,14 @@ class Server:
             batch = []
             while self.ready and len(batch) < self.max_batch:
                 batch.append(self.ready.popleft())
-            grp = batch[0].comm if len(batch) == 1 and self.max_batch == 1 else H.Comm.group([r.comm for r in batch])
+            if len(batch) == 1 and self.max_batch == 1:
+                grp, gb = batch[0].comm, 0
+            else:
+                grp = H.Comm.group([r.comm for r in batch])
+                info = grp.plan_info()
+                gb = info["table_bytes"] + info["scratch_bytes"]
+            self.dev_bytes += gb
+            sl["group_bytes"] = gb
             now = time.perf_counter()
             for r in batch:
                 r.t_launch = now
@@ -202,6 +379,8 @@ class Server:
             sl["group"].wait()
             if not (len(sl["reqs"]) == 1 and sl["group"] is sl["reqs"][0].comm):
                 sl["group"].destroy()
+            self.dev_bytes -= sl["group_bytes"]
+            sl["group_bytes"] = 0
             for r in sl["reqs"]:
                 self._finish(r, now)
             sl["event"], sl["group"], sl["reqs"] = None, None, []
@@ -210,25 +389,41 @@ class Server:
         req.t_done = now
         if self.on_done:
             self.on_done(req)
-        if req.comm is not None:
-            req.comm.destroy()
-            req.comm = None
-        if req.region:
-            self.arena.free(*req.region)
-            req.region = ()
+        if req.comm is not None and req.reserved and not req.error and self.cache.max_entries > 0:
+            # memoize: the communicator and its buffers stay resident
+            e = {"comm": req.comm, "region": req.region, "send_ptrs": req.send_ptrs, "recv_ptrs": req.recv_ptrs,
+                 "hbm_bytes": req.hbm_bytes, "dev_bytes": req.dev_bytes}
+            for old in self.cache.put(self._shape(req), e):
+                self._release_entry(old)
+        else:
+            if req.comm is not None:
+                req.comm.destroy()
+            if req.reserved:
+                self.dev_bytes -= req.dev_bytes
+                req.reserved = False
+            if req.region:
+                self.arena.free(*req.region)
+        req.comm = None
+        req.region = ()
         self.done.append(req)
 
     def poll(self):
-        """One round of progress: retire finished launches, admit and plan
-        waiting requests, launch planned ones on free slots."""
+        """One round of progress: retire finished launches, admit waiting
+        requests (memoized plans directly, the others to the planners), upload
+        planned ones that fit, launch ready ones on free slots; then yield the
+        interpreter lock to the planner threads."""
         self._retire()
         with self.lock:
             self._admit()
-        self._collect_planned()
+        self.planning = self._collect(self.planning, self.to_upload.append)
+        self._reserve_uploads()
+        self.uploading = self._collect(self.uploading, self.ready.append)
         self._launch()
+        time.sleep(0)
 
     def busy(self) -> bool:
-        return bool(self.waiting or self.planning or self.ready or any(s["event"] for s in self.slots))
+        return bool(self.waiting or self.planning or self.to_upload or self.uploading or self.ready
+                    or any(s["event"] for s in self.slots))
 
     def drain(self, timeout_s: float = 600.0):
         t0 = time.perf_counter()
@@ -236,11 +431,13 @@ class Server:
             self.poll()
             if time.perf_counter() - t0 > timeout_s:
                 raise TimeoutError("server did not drain")
-            time.sleep(0)
 
     def close(self):
+        """Drain, stop the planners and free every memoized plan."""
         self.drain()
         self.pool.shutdown()
+        while len(self.cache):
+            self._release_entry(self.cache.evict_lru())
 
 
 def latency_stats(done: list) -> dict:

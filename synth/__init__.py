@@ -86,26 +86,30 @@ def poisson_requests(rate_hz: float, duration_s: float, seed: int = 0,
                      kinds=("broadcast", "scatter", "gather", "allgather", "reducescatter",
                             "allreduce", "alltoall"),
                      ranks=(8, 16, 64), min_bytes: int = 1024, max_bytes: int = 256 << 20,
-                     dtypes=("f32", "bf16", "i32")) -> list[dict]:
-    """Arrival times (Poisson process) and descriptions of served requests."""
+                     dtypes=("f32", "bf16", "i32"), shapes: int = 0) -> list[dict]:
+    """Arrival times (Poisson process) and descriptions of served requests.
+    With ``shapes`` > 0, that many request shapes are drawn first (from the
+    same distributions) and every arrival takes one of them uniformly, so
+    that shapes recur as they do in a service that runs a fixed model."""
     g = rng(seed)
-    t = 0.0
-    out = []
     hier = {8: [2, 4], 16: [4, 4], 64: [4, 4, 4]}
-    while True:
-        t += float(g.exponential(1.0 / rate_hz))
-        if t >= duration_s:
-            break
+
+    def draw():
         P = int(g.choice(ranks))
         b = float(np.exp(g.uniform(np.log(min_bytes), np.log(max_bytes))))
         quantum = 16 * P
         nbytes = max(quantum, int(b) // quantum * quantum)
-        out.append({
-            "t": t,
-            "kind": str(kinds[int(g.integers(0, len(kinds)))]),
-            "P": P,
-            "hierarchy": list(hier[P]),
-            "bytes_per_rank": nbytes,
-            "dtype": str(dtypes[int(g.integers(0, len(dtypes)))]),
-        })
+        return {"kind": str(kinds[int(g.integers(0, len(kinds)))]), "P": P, "hierarchy": list(hier[P]),
+                "bytes_per_rank": nbytes, "dtype": str(dtypes[int(g.integers(0, len(dtypes)))])}
+
+    pool = [draw() for _ in range(shapes)]
+    t = 0.0
+    out = []
+    while True:
+        t += float(g.exponential(1.0 / rate_hz))
+        if t >= duration_s:
+            break
+        d = dict(pool[int(g.integers(0, shapes))]) if shapes else draw()
+        d["t"] = t
+        out.append(d)
     return out

@@ -133,3 +133,55 @@ def test_tight_budget_admits_in_order():
     for k, req in enumerate(reqs):
         for r in range(req.P):
             assert np.array_equal(results[k][r], expected[k][r].view(np.uint8))
+
+
+def test_memoized_plans_equal_fresh(monkeypatch):
+    """Six shapes, each requested four times with new inputs: every shape is
+    factorized once (later requests reuse the resident table and buffers),
+    and every result equals the oracle's for the request alone."""
+    from paper_2408_05962_gb300 import hiccl as H
+    planned = []
+    orig = H.Comm.plan
+
+    def counting_plan(self, *a, **k):
+        planned.append(1)
+        return orig(self, *a, **k)
+
+    monkeypatch.setattr(H.Comm, "plan", counting_plan)
+    shapes = _requests(6, seed=21)
+    reqs = []
+    for rep in range(4):
+        for s in shapes:
+            from paper_2408_05962_gb300.serving import Request
+            reqs.append(Request(kind=s.kind, P=s.P, hierarchy=s.hierarchy, bytes_per_rank=s.bytes_per_rank,
+                                dtype=s.dtype, root=s.root))
+    srv, expected, results, index = _serve(reqs, budget=256 << 20, slots=1, max_batch=1, burst=1, gap_s=0.002)
+    assert len(srv.done) == len(reqs) and not any(r.error for r in srv.done)
+    assert len(planned) == len(shapes) and srv.plan_cache_hits == len(reqs) - len(shapes)
+    assert sum(r.cached for r in srv.done) == len(reqs) - len(shapes)
+    for k, req in enumerate(reqs):
+        for r in range(req.P):
+            assert np.array_equal(results[k][r], expected[k][r].view(np.uint8)), (k, req.kind, req.dtype, r)
+
+
+def test_slots_overlap_on_the_device():
+    """Two requests launched on two slots run at the same time: the executor
+    trace (global timestamps of every work item) of one launch overlaps the
+    other's.  Large work items keep each launch on a part of the GPU."""
+    from paper_2408_05962_gb300 import hiccl as H
+    from paper_2408_05962_gb300.serving import Request, Server
+    spans = {}
+
+    def on_done(req):
+        t = np.array(req.comm.trace(), dtype=np.uint64).reshape(-1, 6)
+        spans[req.id] = (int(t[:, 0].min()), int(t[:, 3].max()))
+
+    srv = Server(8 << 30, slots=2, max_batch=1, planners=2, on_done=on_done, cache_entries=0,
+                 comm_options={H.OPT_TRACE: 1, H.OPT_ITEM_BYTES: 8 << 20})
+    for _ in range(2):
+        srv.submit(Request(kind="allgather", P=8, hierarchy=[2, 4], bytes_per_rank=256 << 20, dtype="f32"))
+    srv.drain()
+    srv.close()
+    assert len(spans) == 2 and not any(r.error for r in srv.done)
+    (a0, a1), (b0, b1) = spans.values()
+    assert max(a0, b0) < min(a1, b1), spans       # the two intervals intersect
