@@ -162,7 +162,9 @@ hiccl_status_t hiccl_plan(hiccl_comm_t comm, const int *hierarchy, int nlevels,
  * may become resident while the previous kernel of the stream drains
  * (programmatic dependent launch) but touches no memory before that kernel
  * has completed.  Under CUDA-graph capture only the launch is recorded; each
- * replay is a complete execution. */
+ * replay is a complete execution, and replays may be interleaved with other
+ * starts of the communicator as long as its CTAS_PER_SM and THREADS options
+ * are those it had at capture. */
 hiccl_status_t hiccl_start(hiccl_comm_t comm, void *cuda_stream);
 
 /* Block until the last start has finished and its buffers may be reused
@@ -306,7 +308,10 @@ typedef enum {
   HICCL_OPT_RING = 7          /* ring(n) of Sec. 4.4: n nodes chained (default 1, tree)    */
 } hiccl_option_t;
 
-/* Set an option.  TIMEOUT_NS, CTAS_PER_SM and THREADS apply to the next start;
+/* Set an option.  TIMEOUT_NS, CTAS_PER_SM and THREADS apply to the next start
+ * (a start whose grid differs from the previous start's begins from zeroed
+ * dependency counters; a CUDA graph that recorded a start before such a
+ * change must be captured again);
  * ITEM_BYTES, ORDER, SLOT_ITEMS and RING must be set before hiccl_init /
  * hiccl_plan, TRACE before hiccl_init.  A work item holds at most
  * max(4096, min(ITEM_BYTES, bytes of its slot / SLOT_ITEMS)) bytes of steps.

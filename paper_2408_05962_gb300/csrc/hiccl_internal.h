@@ -109,15 +109,15 @@ HICCL_HD inline uint32_t rec_bytes(const DevItem &it) {
          rec_cmp_bytes(it.nent, it.nsucc);
 }
 
-// control block (device memory, zeroed at upload).  Launch e (counted from
-// 1) claims work items from ticket[e & 1]; the last of its CTAs to read the
-// epoch resets `started` and the other ticket and sets `epoch` to e, so the
-// next launch finds everything armed and no CTA does any work at exit.
+// control block (device memory, zeroed at upload).  Work items are claimed
+// from one ticket counter that is never reset between launches: launch e
+// (from 0) makes exactly nitems + grid claims (every CTA claims until it
+// draws a ticket past the last item), so ticket t belongs to launch
+// t / (nitems + grid) and names item t mod (nitems + grid).  The launch index
+// scales the dependency targets; no CTA does any work at exit.
 struct DevCtl {
-  unsigned long long ticket[2];   // next work item to claim, by launch parity
-  unsigned long long started;     // CTAs of the current launch that have read the epoch
-  unsigned long long epoch;       // launches started so far; counter targets scale with it
-  unsigned long long err;         // nonzero: abort (code << 32 | step)
+  unsigned long long ticket;   // claims so far, over all launches
+  unsigned long long err;      // nonzero: abort (code << 32 | step)
 };
 
 struct DevTable {

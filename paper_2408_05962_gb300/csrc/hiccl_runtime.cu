@@ -15,8 +15,9 @@
 // launch) and stores; a copy reads its source once and writes every
 // destination; a reduce folds its inputs in the fixed order in FP32 (or int32)
 // without fused multiply-add.  Counters accumulate over launches: the targets
-// of launch e are e times the per-launch counts, so no reset kernel runs
-// between starts.
+// of launch e are e times the per-launch counts, and the launch index comes
+// from the ticket counter itself (see DevCtl), so nothing is reset between
+// starts.
 
 #include <cuda_runtime.h>
 
@@ -50,6 +51,7 @@ struct DevState {
   unsigned long long *trace = nullptr;   // [nitems][6] when tracing
   int err_slot = -1;
   cudaStream_t upload = nullptr;         // internal stream of the device (not owned)
+  unsigned last_grid = 0;                // grid of the previous launch (its ticket arithmetic)
 };
 
 // ---------------------------------------------------------------------------
@@ -586,13 +588,17 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
     }
   }
   __syncthreads();
-  // the previous kernel of the stream has completed and its writes are visible
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  // one read of the epoch per CTA, before the CTA counts itself as started
-  if (tid == 0) s_epoch = ld_acquire(&T.ctl->epoch) + 1;
-  __syncthreads();
-  const unsigned long long epoch = s_epoch;   // this launch
-  unsigned long long *const ticket = &T.ctl->ticket[epoch & 1];
+  // tickets of this launch: [launch0, launch0 + per_launch), the first nitems
+  // of them naming work items (see DevCtl)
+  const unsigned long long per_launch = T.nitems + gridDim.x;
+  unsigned long long epoch = 0;   // this launch, counted from 1 (dependency targets scale with it)
+  // Everything but the control warp waits here until the previous kernel of
+  // the stream has completed and its writes are visible.  The control warp
+  // first claims its first item and stages its record (read-only table data
+  // and the ticket counter, which no other kernel uses while this one may
+  // start), overlapping the previous kernel's tail, and waits before it reads
+  // a dependency counter or hands the item to the data warps.
+  if (warp != 0) asm volatile("griddepcontrol.wait;" ::: "memory");
 
   if (warp == 0) {
     // ---- control: claim, stage, wait for predecessors ----
@@ -601,8 +607,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
     // in flight and its predecessors are awaited.
     unsigned long long nxt = 0;
     DevItem nd{0, 0, 0, 0, 0, {0, 0, 0}};
-    if (lane == 0) nxt = atomicAdd(ticket, 1ull);
+    if (lane == 0) nxt = atomicAdd(&T.ctl->ticket, 1ull);
     nxt = __shfl_sync(0xffffffffu, nxt, 0);
+    const unsigned long long launch0 = nxt / per_launch * per_launch;
+    epoch = nxt / per_launch + 1;
+    if (lane == 0) s_epoch = epoch;   // read by the completion warp after the first hand-over
+    nxt -= launch0;
     if (nxt < T.nitems) nd = T.items[nxt];
     for (uint32_t r = 0;; ++r) {
       const int b = r % NBUF;
@@ -637,9 +647,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
           B.nent = it.nent;
           B.nrun = it.nrun;
           B.nsucc = it.nsucc;
-          nxt = atomicAdd(ticket, 1ull);
+          nxt = atomicAdd(&T.ctl->ticket, 1ull);
         }
-        nxt = __shfl_sync(0xffffffffu, nxt, 0);
+        nxt = __shfl_sync(0xffffffffu, nxt, 0) - launch0;
         if (nxt < T.nitems) {
           nd = T.items[nxt];
           const unsigned char *q = T.recs + (size_t)nd.rec * 16;
@@ -651,6 +661,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
           stop = true;
         }
       }
+      if (r == 0) asm volatile("griddepcontrol.wait;" ::: "memory");
       if (!stop) {
         bool bad = false;
 #pragma unroll
@@ -698,13 +709,6 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
     }
   } else if (warp == 1) {
     // ---- completion: release the successors of finished steps ----
-    // (first, the last CTA of the launch to start arms the next launch: every
-    // CTA has read the epoch by now, and the other ticket is not in use)
-    if (lane == 0 && atom_acq_rel_add(&T.ctl->started, 1ull) == gridDim.x - 1ull) {
-      T.ctl->started = 0;
-      T.ctl->ticket[(epoch + 1) & 1] = 0;
-      T.ctl->epoch = epoch;
-    }
     for (uint32_t r = 0;; ++r) {
       const int b = r % NBUF;
       const uint32_t ph = (r / NBUF) & 1u;
@@ -714,6 +718,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hiccl_exec_kernel(const DevTable
         break;
       }
       if (B.end) break;
+      if (r == 0) epoch = s_epoch;   // written by the control warp before its first hand-over
       if (!mbar_wait(&rec_bar[b], ph, limit) || !mbar_wait(&done_bar[b], ph, limit)) {
         if (lane == 0) raise_error(T, (unsigned long long)ERR_STALL << 32);
         break;
@@ -1230,6 +1235,13 @@ hiccl_status_t hiccl_start(hiccl_comm_t c, void *stream) {
       const int ti = nt == 128 ? 1 : nt == 256 ? 2 : 3;
       const int per_sm = std::min(c->ctas_per_sm, d->occ[ti]);
       const unsigned long long grid = std::min<unsigned long long>(t.nitems, (unsigned long long)d->nsm * per_sm);
+      // the ticket arithmetic assumes the grid of the previous launches: a
+      // launch with another grid (changed options) starts from zeroed counters
+      if (d->last_grid && d->last_grid != (unsigned)grid) {
+        cudaError_t e = cudaMemsetAsync(d->counters, 0, d->counters_bytes, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "counter reset");
+      }
+      d->last_grid = (unsigned)grid;
       exec_launch(nt, (unsigned)grid, s, t);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_fail(c, e, "executor launch");

@@ -78,3 +78,45 @@ def test_chained_collectives_on_one_stream():
     want = S.def_allreduce([send[r] for r in range(P)], h)
     for r in range(P):
         assert np.array_equal(got[r].view(np.uint32), want[r].view(np.uint32)), r
+
+
+def test_grid_changes_between_starts():
+    """One communicator started back to back with its grid changing between
+    starts (CTAs per SM 2 -> 1 -> 2), then a CUDA graph captured with the
+    last grid and replayed between further starts: work items are numbered
+    from one ticket counter over all launches, which the library resets when
+    the grid changes, so every result equals the oracle's."""
+    import torch
+    from paper_2408_05962_gb300 import collectives as C
+    from paper_2408_05962_gb300 import hiccl as H
+    P, h, d = 16, [4, 4], 8195
+    b = C.Buffers("allreduce", P, d, torch.float32)
+    comm = H.Comm(P, "f32")
+    C.compose(comm, "allreduce", d, b.send_ptrs(), b.recv_ptrs())
+    comm.init(h, 2, 4)
+    prog = PR.allreduce(P, d)
+    graph = None
+    plan = [(2, False), (1, False), (1, False), (2, False), (2, True), (2, False), (2, True), (2, True)]
+    for it, (per_sm, replay) in enumerate(plan):
+        mem0 = fill(prog, 700 + it)
+        b.send.copy_(torch.from_numpy(np.stack([mem0[("send", r)] for r in range(P)])))
+        b.recv.fill_(-1.0)
+        torch.cuda.synchronize()
+        comm.set_option(H.OPT_CTAS_PER_SM, per_sm)
+        if replay:
+            if graph is None:
+                gs = torch.cuda.Stream()
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph, stream=gs):
+                    comm.start(gs)
+            graph.replay()
+            torch.cuda.synchronize()
+        else:
+            comm.start()
+            comm.wait()
+        ref = {k: v.copy() for k, v in mem0.items()}
+        S.run_program(prog, ref, h)
+        got = b.recv.cpu().numpy()
+        for r in range(P):
+            assert np.array_equal(got[r].view(np.uint32), ref[("recv", r)].view(np.uint32)), (it, r)
+    comm.destroy()
