@@ -849,6 +849,9 @@ def serve_trace(rate, duration, budget_gb, slots, max_batch, seed=0, shapes=0):
            "completed": len(done),
            "errors": len(srv.done) - len(done), "wall_s": wall, "achieved_req_per_s": len(done) / wall,
            "gbs": total / wall / 1e9, "launches": srv.launches, **st}
+    errs = sorted({r.error for r in srv.done if r.error})
+    if errs:
+        out["error_messages"] = errs[:3]
     for key in ("plan_cache_hits", "plan_cache_misses"):
         if hasattr(srv, key):
             out[key] = getattr(srv, key)

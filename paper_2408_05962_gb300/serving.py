@@ -319,27 +319,32 @@ class Server:
         return keep
 
     def _reserve_uploads(self):
-        """Count planned requests' tables and relays against the budget (in
-        order) and upload those that fit."""
-        while self.to_upload:
-            req = self.to_upload[0]
-            if self.max_batch > 1:                     # group members stay host plans
-                self.to_upload.popleft()
+        """Count planned requests' tables and relays against the budget and
+        upload those that fit (in order, passing over one that does not fit
+        yet).  When nothing that holds memory can move -- no launch running,
+        nothing uploading, ready or planning -- and no planned request fits,
+        the first is refused so that its buffers go to the others."""
+        if self.max_batch > 1:                         # group members stay host plans
+            while self.to_upload:
+                req = self.to_upload.popleft()
                 req.dev_bytes = 0
                 self.ready.append(req)
-                continue
-            if not self._make_room(req.dev_bytes):
-                if any(s["event"] is not None for s in self.slots) or self.uploading:
-                    return                             # memory frees as launches retire
-                # nothing else holds memory: the request alone exceeds the budget
-                self.to_upload.popleft()
-                req.error = "device footprint exceeds the budget"
-                self._finish(req, time.perf_counter())
-                continue
-            self.to_upload.popleft()
-            self.dev_bytes += req.dev_bytes
-            req.reserved = True
-            self.uploading.append((self.pool.submit(self._upload, req), req))
+            return
+        kept = deque()
+        while self.to_upload:
+            req = self.to_upload.popleft()
+            if self._make_room(req.dev_bytes):
+                self.dev_bytes += req.dev_bytes
+                req.reserved = True
+                self.uploading.append((self.pool.submit(self._upload, req), req))
+            else:
+                kept.append(req)
+        self.to_upload = kept
+        if kept and not (self.uploading or self.ready or self.planning or any(s["event"] for s in self.slots)):
+            req = self.to_upload.popleft()
+            req.error = (f"device footprint ({req.dev_bytes} bytes of tables and relays) does not fit the "
+                         f"budget next to the buffers of the waiting requests")
+            self._finish(req, time.perf_counter())
 
     def _launch(self):
         if self.device.type != "cuda":

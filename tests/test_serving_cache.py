@@ -113,3 +113,28 @@ def test_request_beyond_budget_is_refused():
         _step(srv)
     assert srv.waiting and srv.waiting[0] is r        # its buffers never fit: it waits, FIFO
     assert srv.plan_cache_misses == 0                  # retries of the waiting request count nothing
+
+
+def test_planned_request_waits_for_memory_held_by_others():
+    """A planned request whose tables do not fit next to buffers that other
+    admitted requests hold waits for them (it is not refused while they can
+    still move), and the requests behind it that fit are uploaded."""
+    srv = Server(64 << 20, slots=2, device="cpu")
+    srv.pool = _Pool()
+    a = Request(kind="allreduce", P=8, hierarchy=[2, 4], bytes_per_rank=8 * 1024 * 4, dtype="f32")
+    b = Request(kind="allgather", P=8, hierarchy=[2, 4], bytes_per_rank=8 * 1024 * 4, dtype="f32")
+    srv.submit(a)
+    srv.submit(b)
+    with srv.lock:
+        srv._admit()
+    srv.planning = srv._collect(srv.planning, srv.to_upload.append)
+    assert list(srv.to_upload) == [a, b]
+    srv.budget = srv.arena.used + b.dev_bytes            # room for b's tables only
+    srv._reserve_uploads()
+    assert [r for _, r in srv.uploading] == [b] and list(srv.to_upload) == [a] and not a.error
+    srv.uploading = srv._collect(srv.uploading, srv.ready.append)
+    srv._reserve_uploads()                               # b is ready and will free memory: a waits
+    assert list(srv.to_upload) == [a] and not a.error
+    srv._finish(srv.ready.popleft(), time.perf_counter())   # b done; its plan is kept idle
+    srv._reserve_uploads()                               # evicting b's idle plan makes room for a
+    assert [r for _, r in srv.uploading] == [a] and not a.error
