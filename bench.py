@@ -527,13 +527,15 @@ def _make_comm(H, P, dtype, args):
         comm.set_option(H.OPT_THREADS, args.threads)
     if args.ring > 1:
         comm.set_option(H.OPT_RING, args.ring)
+    if args.slot_items:
+        comm.set_option(H.OPT_SLOT_ITEMS, args.slot_items)
     return comm
 
 
 def _graph_of(comms, kinds, device):
-    """One CUDA graph holding one start of every communicator (a start under
-    capture records only the executor launch; each replay is a complete
-    execution)."""
+    """One CUDA graph holding, in order, one start of the communicator of
+    every name in ``kinds`` (names may repeat; a start under capture records
+    only the executor launch, and each replay is a complete execution)."""
     import torch
     gs = torch.cuda.Stream(device)
     graph = torch.cuda.CUDAGraph()
@@ -613,6 +615,17 @@ def measure_collectives(args, device, world, workload, dtype, xs=None, e2e=True)
         for i, kind in enumerate(kinds):
             per_kind[kind].append(evs[i].elapsed_time(evs[i + 1]))
 
+    # per-collective steady state: ten starts of one collective in one graph,
+    # replayed (consecutive launches overlap as in the step's graph)
+    per_kind_graph = {}
+    for kind in kinds:
+        g1 = _graph_of(comms, (kind,) * 10, device)
+        for _ in range(2):
+            g1.replay()
+        per_kind_graph[kind] = statistics.median(_time_blocks(g1.replay, 3, 0.0, stream)) / 30
+        del g1
+    torch.cuda.synchronize(device)
+
     graph = _graph_of(comms, kinds, device)
     for _ in range(warm):
         graph.replay()
@@ -643,7 +656,9 @@ def measure_collectives(args, device, world, workload, dtype, xs=None, e2e=True)
     coll = {}
     for kind in kinds:
         med = statistics.median(per_kind[kind])
+        gm = per_kind_graph[kind]
         coll[kind] = {"ms": med, "gbs": nbytes[kind] / med / 1e6, "frac": nbytes[kind] / med / 1e6 / peak,
+                      "graph_ms": gm, "graph_gbs": nbytes[kind] / gm / 1e6, "graph_frac": nbytes[kind] / gm / 1e6 / peak,
                       "dp_over_t_gbs": pbytes[kind] / med / 1e6, "schedule_bytes": nbytes[kind],
                       "min_bytes": mbytes[kind], "min_gbs": mbytes[kind] / med / 1e6,
                       "level_bytes": comms[kind].level_bytes(), "steps": comms[kind].plan_info()["steps"]}
@@ -908,7 +923,8 @@ def run_ours(args):
         cpu = cpu_baseline(args.cpu_budget)
 
     default_run = (args.workload == "seven" and not args.kinds and args.ring == 1 and not args.bytes_per_rank
-                   and not args.item_bytes and not args.ctas_per_sm and not args.threads and args.order is None)
+                   and not args.item_bytes and not args.ctas_per_sm and not args.threads and args.order is None
+                   and not args.slot_items)
     # DRAM bytes of an average executor launch of the default workload, from
     # the committed ncu capture (null for other workloads or options, or once
     # the executor sources have changed since the capture)
@@ -926,7 +942,9 @@ def run_ours(args):
                                    **({"collectives": args.kinds.split(",")} if args.kinds else {})}),
         "timing": {"method": "CUDA graph of one step (one start per collective), replayed; blocks of "
                              f"{args.steps} replays bracketed by CUDA events until >= {args.min_seconds:g} s; "
-                             "median block", "blocks": r["blocks"], "timed_s": r["timed_s"],
+                             "median block; per collective: 'ms' from eager starts bracketed by events, "
+                             "'graph_ms' from a graph of ten starts of that collective, replayed",
+                   "blocks": r["blocks"], "timed_s": r["timed_s"],
                    "block_ms": r["block_ms"], "eager": r["eager"]},
         "roofline": {"bound": "hbm", "achieved": r["value"] / world, "peak": peak, "unit": "GB/s",
                      "frac": r["frac"], "peak_source": r["peak_kind"],
@@ -1053,6 +1071,7 @@ def main(argv=None):
     ap.add_argument("--threads", type=int, default=0, help="executor threads per CTA (0: library default)")
     ap.add_argument("--order", type=int, default=None, help="work order: 0 pipeline slots, 1 stage depth")
     ap.add_argument("--ring", type=int, default=1, help="ring(n) of the hybrid ring+tree topology (1: tree)")
+    ap.add_argument("--slot-items", type=int, default=0, help="items a pipeline slot is spread over (0: library default)")
     ap.add_argument("--bytes-per-rank", type=int, default=0,
                     help="override the workload's per-rank bytes (profiling of a smaller case; 0: the workload's)")
     args = ap.parse_args(argv)
