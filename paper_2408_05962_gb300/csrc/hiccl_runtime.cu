@@ -306,7 +306,7 @@ __device__ __forceinline__ void warp_copy(const unsigned long long *ptrs, uint32
   const char *src = reinterpret_cast<const char *>(ptrs[0]) + lo;
   uint32_t done = 0;
   if (aligned) {
-    constexpr int U = 8;   // 4 KiB per pass
+    constexpr int U = 4;   // 2 KiB per pass
     const uint32_t nvec = n >> 4;
     for (uint32_t base = 0; base < nvec; base += 32 * U) {
       uint4 v[U];
