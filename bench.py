@@ -136,10 +136,11 @@ class cpus_of_node:
 
 
 def host_copy_rates(h_send, h_recv, bufs, kinds, stream, device):
-    """GB/s of one plain pass of the end-to-end leg's copies, alone: every
-    send buffer host -> device, then every receive buffer device -> host
-    (CUDA events on one stream).  The end-to-end figure cannot exceed what the
-    host link gives here; None where the measurement fails."""
+    """GB/s of one plain pass of the end-to-end leg's copies: every send
+    buffer host -> device alone, every receive buffer device -> host alone,
+    and both at once on two streams (bytes of both directions over the time
+    of both).  The end-to-end figure cannot exceed what the host link gives
+    here; None where the measurement fails."""
     import torch
     try:
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -155,9 +156,26 @@ def host_copy_rates(h_send, h_recv, bufs, kinds, stream, device):
         ev[2].synchronize()
         hb = sum(t.numel() * t.element_size() for t in h_send.values())
         db = sum(t.numel() * t.element_size() for t in h_recv.values())
-        return {"h2d_gbs": hb / (ev[0].elapsed_time(ev[1]) * 1e6), "d2h_gbs": db / (ev[1].elapsed_time(ev[2]) * 1e6)}
+        out = {"h2d_gbs": hb / (ev[0].elapsed_time(ev[1]) * 1e6), "d2h_gbs": db / (ev[1].elapsed_time(ev[2]) * 1e6)}
+        other = torch.cuda.Stream(device)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize(device)
+        e0.record(stream)
+        other.wait_event(e0)
+        with torch.cuda.stream(stream):
+            for k in kinds:
+                bufs[k].send.copy_(h_send[k], non_blocking=True)
+            e1.record(stream)
+        with torch.cuda.stream(other):
+            for k in kinds:
+                h_recv[k].copy_(bufs[k].recv, non_blocking=True)
+            e2.record(other)
+        torch.cuda.synchronize(device)
+        both = max(e0.elapsed_time(e1), e0.elapsed_time(e2))
+        out["both_directions_gbs"] = (hb + db) / (both * 1e6)
+        return out
     except Exception:   # a report field only: never fail the benchmark for it
-        return {"h2d_gbs": None, "d2h_gbs": None}
+        return {"h2d_gbs": None, "d2h_gbs": None, "both_directions_gbs": None}
 
 
 # ---------------------------------------------------------------------------
@@ -684,8 +702,12 @@ def _end_to_end(comms, bufs, kinds, tdt, step_bytes, args, device, stream):
     the NUMA node of the GPU's host link where sysfs names one: every step
     copies each send buffer host -> device, starts and waits on every
     collective, and copies each receive buffer device -> host.  The copies
-    overlap the collectives: H2D of collective k+1 and D2H of collective k-1
-    run on their own streams while collective k executes."""
+    overlap the collectives and each other: the uploads run on one stream and
+    the downloads on another, ordered only by events -- a collective starts
+    once its inputs are uploaded and the previous step's download of its
+    receive buffer is done, an upload waits for the previous step's
+    collective to have read the buffer -- so one step's downloads overlap the
+    next step's uploads (the host link runs both directions at once)."""
     import torch
     numa = host_node_of(device)
     with cpus_of_node(numa):
@@ -696,35 +718,46 @@ def _end_to_end(comms, bufs, kinds, tdt, step_bytes, args, device, stream):
             h_recv[k].zero_()
     h2d = sum(t.numel() * t.element_size() for t in h_send.values())
     d2h = sum(t.numel() * t.element_size() for t in h_recv.values())
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(args.steps, 5))
     s_in, s_out = torch.cuda.Stream(device), torch.cuda.Stream(device)
+    coll_done = {k: None for k in kinds}   # collective k of the previous step has read its inputs
+    d2h_done = {k: None for k in kinds}    # download of k's results of the previous step is done
     t_e2e = 0.0
     for it in range(e2e_steps + 1):      # the first pass is an untimed warm-up
         if it == 1:
             barrier(device)
             torch.cuda.synchronize(device)
             t_e2e = time.perf_counter()
-        ev_in = {k: torch.cuda.Event() for k in kinds}
-        ev_out = {k: torch.cuda.Event() for k in kinds}
+        ev_in = {}
         with torch.cuda.stream(s_in):
             for k in kinds:
+                if coll_done[k] is not None:
+                    s_in.wait_event(coll_done[k])
                 bufs[k].send.copy_(h_send[k], non_blocking=True)
+                ev_in[k] = torch.cuda.Event()
                 ev_in[k].record(s_in)
         for k in kinds:
             stream.wait_event(ev_in[k])
+            if d2h_done[k] is not None:
+                stream.wait_event(d2h_done[k])
             comms[k].start(stream)
-            ev_out[k].record(stream)
-            s_out.wait_event(ev_out[k])
+            coll_done[k] = torch.cuda.Event()
+            coll_done[k].record(stream)
+            s_out.wait_event(coll_done[k])
             with torch.cuda.stream(s_out):
                 h_recv[k].copy_(bufs[k].recv, non_blocking=True)
+                d2h_done[k] = torch.cuda.Event()
+                d2h_done[k].record(s_out)
         for k in kinds:
             comms[k].wait()
-        torch.cuda.synchronize(device)
+        if it == 0:
+            torch.cuda.synchronize(device)
+    torch.cuda.synchronize(device)
     e2e_s = time.perf_counter() - t_e2e
     eb, es = aggregate(step_bytes * e2e_steps, e2e_s, device)
     host_link = host_copy_rates(h_send, h_recv, bufs, kinds, s_in, device)
     return {"value": eb / es / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "host_numa_node": numa, **host_link}
+            "steps": e2e_steps, "host_numa_node": numa, **host_link}
 
 
 def measure_allreduce64(args, device, dtypes=("f32", "bf16", "fp8")):

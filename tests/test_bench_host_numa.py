@@ -77,4 +77,4 @@ def test_host_copy_rates_never_fail_the_bench():
     t = {"x": torch.zeros(4)}
     bufs = {"x": types.SimpleNamespace(send=torch.zeros(4), recv=torch.zeros(4))}
     out = bench.host_copy_rates(t, t, bufs, ["x"], None, "cpu")
-    assert out == {"h2d_gbs": None, "d2h_gbs": None}
+    assert out == {"h2d_gbs": None, "d2h_gbs": None, "both_directions_gbs": None}
