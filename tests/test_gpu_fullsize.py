@@ -115,3 +115,77 @@ def test_buffers_beyond_four_gib():
         comm.destroy()
         del b
         torch.cuda.empty_cache()
+
+
+def test_batch256_grouped_graph_full():
+    """Config 4 at full size, in the launch configuration the benchmark times:
+    the 256 collectives of the batch (All-gather / Reduce-scatter /
+    All-reduce, P in {8, 16, 32}, two-level hierarchies, 4 KiB .. 16 MiB per
+    rank, fp32 and bf16; synth.batch_mix seed 0), stripe, pipeline and
+    executor knobs autotuned per shape, run as one grouped launch replayed
+    from a CUDA graph.  Every receive buffer of every collective equals the
+    oracle's result for that collective alone, bit for bit."""
+    import math
+
+    import torch
+
+    from oracle import lowprec as LP
+    from paper_2408_05962_gb300 import collectives as C
+    from paper_2408_05962_gb300 import hiccl as H
+    from synth import batch_mix, rng
+
+    descs = batch_mix(256, seed=0)
+    stream = torch.cuda.current_stream()
+    comms, bufs, tuned = [], [], {}
+
+    def inputs(i, dsc, ls):
+        x = rng(7000 + i).uniform(-1.0, 1.0, size=(dsc["P"], ls)).astype(np.float32)
+        return x if dsc["dtype"] == "f32" else LP.f32_to_bf16(x)
+
+    for i, dsc in enumerate(descs):
+        P, h, dt = dsc["P"], dsc["hierarchy"], dsc["dtype"]
+        es = 4 if dt == "f32" else 2
+        d = dsc["bytes_per_rank"] // es // P
+        b = C.Buffers(dsc["kind"], P, d, torch.float32 if dt == "f32" else torch.int16)
+        b.send.view(torch.uint8).copy_(torch.from_numpy(inputs(i, dsc, b.ls).view(np.uint8)))
+        b.recv.view(torch.uint8).fill_(0xA5)
+        key = (dsc["kind"], P, tuple(h), dt, int(math.log2(dsc["bytes_per_rank"])))
+        comm = H.Comm(P, dt)
+        conf = tuned.get(key)
+        if conf:
+            comm.set_option(H.OPT_ORDER, conf["order"])
+            comm.set_option(H.OPT_ITEM_BYTES, conf["item_bytes"])
+        C.compose(comm, dsc["kind"], d, b.send_ptrs(), b.recv_ptrs())
+        if conf:
+            comm.init(h, conf["stripe"], conf["pipeline"])
+        else:
+            comm.init(h, h[-1], 4)
+            tuned[key] = comm.autotune(stream, tune_method=True)   # leaves the communicator on its best knobs
+        comms.append(comm)
+        bufs.append(b)
+    for b in bufs:                               # autotuning ran the collectives: start from sentinels again
+        b.recv.view(torch.uint8).fill_(0xA5)
+    grp = H.Comm.group(comms)
+    gs = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gs):
+        grp.start(gs)
+    graph.replay()
+    torch.cuda.synchronize()
+    for i, (dsc, b) in enumerate(zip(descs, bufs)):
+        P, h, dt = dsc["P"], dsc["hierarchy"], dsc["dtype"]
+        x = inputs(i, dsc, b.ls)
+        xs = [x[r] for r in range(P)]
+        fold_dt = None if dt == "f32" else dt
+        if dsc["kind"] == "allgather":
+            exp = S.def_allgather(xs)
+        elif dsc["kind"] == "reducescatter":
+            exp = S.def_reducescatter(xs, h, fold_dt)
+        else:
+            exp = S.def_allreduce(xs, h, fold_dt)
+        got = b.recv.view(torch.uint8).cpu().numpy()
+        for r in range(P):
+            assert np.array_equal(got[r], exp[r].view(np.uint8)), (i, dsc, r)
+    grp.destroy()
+    for c in comms:
+        c.destroy()

@@ -185,3 +185,94 @@ def test_slots_overlap_on_the_device():
     assert len(spans) == 2 and not any(r.error for r in srv.done)
     (a0, a1), (b0, b1) = spans.values()
     assert max(a0, b0) < min(a1, b1), spans       # the two intervals intersect
+
+
+def _expected_at(kind, P, d, root, xs_at, r, k, h, dtype):
+    """Expected value of receive element k of rank r, from the inputs:
+    xs_at(i, m) is element m of rank i's send buffer (Table 2)."""
+    if kind == "broadcast":
+        return xs_at(root, k)
+    if kind == "scatter":
+        return xs_at(root, r * d + k)
+    if kind == "gather":
+        return xs_at(k // d, k % d)
+    if kind == "allgather":
+        return xs_at(k // d, k % d)
+    if kind == "alltoall":
+        return xs_at(k // d, r * d + k % d)
+    m = r * d + k if kind == "reducescatter" else k
+    fold_dt = None if dtype == "f32" else dtype
+    return S.nested_fold({i: np.asarray([xs_at(i, m)]) for i in range(P)}, h, fold_dt)[0]
+
+
+@pytest.mark.parametrize("shapes", [0, 6])
+def test_served_full_size_sampled(shapes):
+    """Config 5 at full size: requests drawn from the serving distribution
+    (the seven collectives, P in {8, 16, 64}, 1 KiB .. 256 MiB per rank,
+    fp32 / bf16 / int32; with ``shapes``, drawn from that many recurring
+    shapes so memoized plans serve the repeats) under a 64 GB budget on eight
+    launch slots.  Every result is checked on sampled elements, each computed
+    by the oracle from the inputs read back from the device."""
+    import torch
+    from paper_2408_05962_gb300.serving import Request, Server
+    from synth import poisson_requests
+    descs = poisson_requests(2000.0, 0.02, seed=5, shapes=shapes)[:24]
+    TD = {"f32": torch.float32, "bf16": torch.bfloat16, "i32": torch.int32}
+    NV = {"f32": np.float32, "bf16": np.uint16, "i32": np.int32}
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(11)
+    checked = []
+
+    def rows(req, ptrs, n):
+        es = 2 if req.dtype == "bf16" else 4
+        off = [p - srv.arena.base for p in ptrs]
+        return [srv.arena.buf[o:o + n * es].view(TD[req.dtype]) for o in off]
+
+    def on_admit(req):
+        from paper_2408_05962_gb300.collectives import buffer_lengths
+        ls, lr = buffer_lengths(req.kind, req.P, req.d)
+        for t in rows(req, req.send_ptrs, ls):
+            if req.dtype == "i32":
+                t.copy_(torch.randint(-2**31, 2**31 - 1, t.shape, generator=gen, device="cuda", dtype=torch.int32))
+            else:
+                t.copy_(torch.empty(t.shape, device="cuda").uniform_(-1, 1, generator=gen))
+        for t in rows(req, req.recv_ptrs, lr):
+            t.view(torch.uint8).fill_(0x5A)
+        torch.cuda.synchronize()
+
+    def on_done(req):
+        from paper_2408_05962_gb300.collectives import buffer_lengths
+        ls, lr = buffer_lengths(req.kind, req.P, req.d)
+        g = np.random.Generator(np.random.PCG64(req.id))
+        send = rows(req, req.send_ptrs, ls)
+        recv = rows(req, req.recv_ptrs, lr)
+        targets = [req.root] if req.kind == "gather" else list(range(req.P))
+        cache = {}
+
+        def xs_at(i, m):
+            if (i, m) not in cache:
+                cache[(i, m)] = send[i][m:m + 1].cpu().view(
+                    torch.int16 if req.dtype == "bf16" else TD[req.dtype]).numpy().view(NV[req.dtype])[0]
+            return cache[(i, m)]
+        for r in targets:
+            for k in sorted(set(g.integers(0, lr, 6).tolist()) | {0, lr - 1}):
+                got = recv[r][k:k + 1].cpu().view(torch.int16 if req.dtype == "bf16" else TD[req.dtype]).numpy()
+                got = got.view(NV[req.dtype])[0]
+                exp = _expected_at(req.kind, req.P, req.d, req.root, xs_at, r, k, req.hierarchy, req.dtype)
+                a = np.asarray([got], dtype=NV[req.dtype]).view(np.uint8)
+                b = np.asarray([exp], dtype=NV[req.dtype]).view(np.uint8)
+                assert np.array_equal(a, b), (req.kind, req.P, req.bytes_per_rank, req.dtype, r, k)
+        checked.append(req.id)
+
+    srv = Server(64 << 30, slots=8, max_batch=1, planners=4, on_admit=on_admit, on_done=on_done)
+    for wave in (descs[:12], descs[12:]):      # the second wave finds the first wave's plans idle
+        for dsc in wave:
+            srv.submit(Request(kind=dsc["kind"], P=dsc["P"], hierarchy=dsc["hierarchy"],
+                               bytes_per_rank=dsc["bytes_per_rank"], dtype=dsc["dtype"]))
+        srv.drain()
+    srv.close()
+    assert not any(r.error for r in srv.done), [r.error for r in srv.done if r.error]
+    assert len(checked) == len(descs)
+    assert max(d["bytes_per_rank"] for d in descs) > (16 << 20)      # the large end of the range is served
+    if shapes:
+        assert srv.plan_cache_hits > 0
