@@ -19,8 +19,9 @@ payload) arrive at any time.  The server
 * launches planned requests on whichever of its ``slots`` CUDA streams is
   free -- each request alone (``group_max`` 1), or up to ``group_max``
   waiting requests together as one grouped persistent launch
-  (``hiccl_group``); requests that arrive while others run take the next free
-  slot, and launches on different slots overlap on the device;
+  (``hiccl_group``, whose combined table is built on the planner threads);
+  requests that arrive while others run take the next free slot, and
+  launches on different slots overlap on the device;
 * retires a launch when its event completes, recording each request's
   latency (completion observed minus arrival).
 
@@ -186,6 +187,8 @@ class Server:
         self.to_upload: deque = deque()   # planned, waiting for device memory
         self.uploading: list = []         # (future, request)
         self.ready: deque = deque()       # on the device, not launched
+        self.grouping: list = []          # (future, batch): combined tables being built
+        self.grouped: deque = deque()     # (group, device bytes, batch): built, waiting for a slot
         self.done: list = []
         self.on_admit, self.on_done = on_admit, on_done
         self.lock = threading.Lock()
@@ -346,34 +349,65 @@ class Server:
                          f"budget next to the buffers of the waiting requests")
             self._finish(req, time.perf_counter())
 
+    @staticmethod
+    def _build_group(batch):
+        """Combined table of a batch (pool thread): plan union and upload."""
+        grp = H.Comm.group([r.comm for r in batch])
+        info = grp.plan_info()
+        return grp, info["table_bytes"] + info["scratch_bytes"]
+
+    def _start_on(self, sl, grp, batch, gb):
+        """Launch ``grp`` on slot ``sl``; ``gb``: device bytes of a combined
+        table (counted since it was built), released when the launch retires."""
+        import torch
+        sl["group_bytes"] = gb
+        now = time.perf_counter()
+        for r in batch:
+            r.t_launch = now
+        grp.start(sl["stream"])
+        ev = torch.cuda.Event()
+        ev.record(sl["stream"])
+        sl["event"], sl["group"], sl["reqs"] = ev, grp, batch
+        self.launches += 1
+
+    def _collect_groups(self):
+        keep = []
+        for fut, batch in self.grouping:
+            if not fut.done():
+                keep.append((fut, batch))
+                continue
+            err = fut.exception()
+            if err is not None:
+                for r in batch:
+                    r.error = str(err)
+                    self._finish(r, time.perf_counter())
+            else:
+                grp, gb = fut.result()
+                self.dev_bytes += gb           # the combined table is on the device from now on
+                self.grouped.append((grp, gb, batch))
+        self.grouping = keep
+
     def _launch(self):
         if self.device.type != "cuda":
             return
         for sl in self.slots:
-            if not self.ready:
-                return
             if sl["event"] is not None:
                 continue
+            if self.max_batch == 1:
+                if not self.ready:
+                    break
+                req = self.ready.popleft()
+                self._start_on(sl, req.comm, [req], 0)
+            elif self.grouped:
+                grp, gb, batch = self.grouped.popleft()
+                self._start_on(sl, grp, batch, gb)
+        # grouped launches: combined tables are built on the planner threads,
+        # at most one per slot ahead of the launches
+        while self.max_batch > 1 and self.ready and len(self.grouping) + len(self.grouped) < len(self.slots):
             batch = []
             while self.ready and len(batch) < self.max_batch:
                 batch.append(self.ready.popleft())
-            if len(batch) == 1 and self.max_batch == 1:
-                grp, gb = batch[0].comm, 0
-            else:
-                grp = H.Comm.group([r.comm for r in batch])
-                info = grp.plan_info()
-                gb = info["table_bytes"] + info["scratch_bytes"]
-            self.dev_bytes += gb
-            sl["group_bytes"] = gb
-            now = time.perf_counter()
-            for r in batch:
-                r.t_launch = now
-            grp.start(sl["stream"])
-            import torch
-            ev = torch.cuda.Event()
-            ev.record(sl["stream"])
-            sl["event"], sl["group"], sl["reqs"] = ev, grp, batch
-            self.launches += 1
+            self.grouping.append((self.pool.submit(self._build_group, batch), batch))
 
     def _retire(self):
         for sl in self.slots:
@@ -423,12 +457,13 @@ class Server:
         self.planning = self._collect(self.planning, self.to_upload.append)
         self._reserve_uploads()
         self.uploading = self._collect(self.uploading, self.ready.append)
+        self._collect_groups()
         self._launch()
         time.sleep(0)
 
     def busy(self) -> bool:
         return bool(self.waiting or self.planning or self.to_upload or self.uploading or self.ready
-                    or any(s["event"] for s in self.slots))
+                    or self.grouping or self.grouped or any(s["event"] for s in self.slots))
 
     def drain(self, timeout_s: float = 600.0):
         t0 = time.perf_counter()
