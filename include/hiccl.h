@@ -304,7 +304,7 @@ typedef enum {
   HICCL_OPT_ORDER = 3,        /* work order: 0 pipeline slots, 1 stage depth (default)    */
   HICCL_OPT_THREADS = 4,      /* threads per executor CTA: 128, 256 (default), 512       */
   HICCL_OPT_TRACE = 5,        /* 1: record per-item timestamps (hiccl_get_trace); default 0 */
-  HICCL_OPT_SLOT_ITEMS = 6,   /* items a pipeline slot is spread over (default 768)       */
+  HICCL_OPT_SLOT_ITEMS = 6,   /* items a pipeline slot is spread over (0, default: grid)  */
   HICCL_OPT_RING = 7          /* ring(n) of Sec. 4.4: n nodes chained (default 1, tree)    */
 } hiccl_option_t;
 
@@ -314,7 +314,11 @@ typedef enum {
  * change must be captured again);
  * ITEM_BYTES, ORDER, SLOT_ITEMS and RING must be set before hiccl_init /
  * hiccl_plan, TRACE before hiccl_init.  A work item holds at most
- * max(4096, min(ITEM_BYTES, bytes of its slot / SLOT_ITEMS)) bytes of steps.
+ * max(4096, min(ITEM_BYTES, S / D)) bytes of steps of one pipeline slot of S
+ * bytes: with SLOT_ITEMS = 0 (default) D is the executor's grid (its CTAs on
+ * the device current at planning; 304 without one) for S under 8 MiB, so
+ * that a short slot runs as one round of items over every CTA, and 768 for
+ * larger slots; SLOT_ITEMS = k > 0 sets D = k for every slot.
  * RING = n (Sec. 4.4, hybrid ring+tree): the n nodes of P/n ranks, which must
  * be the groups of one hierarchy level (n = f_0 * ... * f_{l-1}; checked at
  * planning, HICCL_ERR_INVALID otherwise), are chained starting at the root's

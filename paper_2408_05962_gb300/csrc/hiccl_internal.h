@@ -29,6 +29,14 @@ constexpr uint32_t FP8_BLOCK_ELEMS = 128;
 constexpr uint32_t FP8_BLOCK_BYTES = 144;   // 128 e4m3 codes, binary32 scale, 12 zero bytes
 HICCL_HD inline uint32_t seg_bytes_of(uint32_t dtype) { return dtype == 3u ? 28u * FP8_BLOCK_BYTES : SEG_BYTES; }
 constexpr uint32_t MAX_ENTRIES_PER_ITEM = 64;
+// executor CTAs assumed when a plan is made without a device to query: a
+// 152-SM GB300 at two CTAs per SM
+constexpr unsigned long long DEFAULT_GRID = 304;
+// work-item sizing (measured on the seven collectives of 4 MiB per rank at
+// P = 64): pipeline slots under SMALL_SLOT_BYTES are spread over the grid,
+// larger ones over LARGE_SLOT_ITEMS items
+constexpr unsigned long long SMALL_SLOT_BYTES = 8ull << 20;
+constexpr unsigned long long LARGE_SLOT_ITEMS = 768;
 constexpr uint32_t MAX_FANIN = 1024;    // reduce inputs / copy destinations per step
 constexpr uint32_t TMA_MAX_FANIN = 8;   // reduce inputs folded in shared memory
 
@@ -228,7 +236,7 @@ struct hiccl_comm {
   int threads = 256;
   unsigned long long item_bytes = 49152;   // set per payload at creation
   int order = 1;
-  unsigned long long slot_items = 768;
+  unsigned long long slot_items = 0;   // 0: whole rounds over the executor grid
   int trace = 0;
   int ring = 1;                       // ring(n) of Sec. 4.4; 1 = tree only
   hiccl::Plan plan;
@@ -265,4 +273,8 @@ hiccl_status_t replan(hiccl_comm *c, const std::vector<int> &hierarchy, int stri
 // runtime entry points (hiccl_runtime.cu)
 hiccl_status_t dev_upload(hiccl_comm *c);
 void dev_release(hiccl_comm *c);
+// CTAs of an executor launch of c on the calling thread's current device
+// (SMs x resident CTAs per SM for c's THREADS and CTAS_PER_SM); 0 when no
+// device can be queried
+unsigned long long exec_grid(const hiccl_comm &c);
 }  // namespace hiccl

@@ -1155,15 +1155,22 @@ static hiccl_status_t build_plan(hiccl_comm *c, const int *hierarchy, int nlevel
 
   // work items: consecutive steps of one slot (so no item depends on itself)
   // and one data-path class, cut into runs of at most `cap` segment bytes and
-  // MAX_ENTRIES_PER_ITEM steps.  A slot with little data gets small items, so
-  // that it still spreads over about slot_items CTAs: the early levels of a
-  // tree are short but lie on the critical path.
+  // MAX_ENTRIES_PER_ITEM steps.  A slot of S bytes is spread over about D
+  // items (cap = S / D in whole segments, at most ITEM_BYTES): by default a
+  // slot under SMALL_SLOT_BYTES over exactly the executor's grid, G CTAs, so
+  // that a short slot -- the early levels of a tree, short but on the
+  // critical path -- runs as one round of items on every CTA, and a larger
+  // slot over LARGE_SLOT_ITEMS; SLOT_ITEMS > 0 sets D for every slot.
   const unsigned long long SEGB = seg_bytes_of((uint32_t)c->dtype);
   plan.seg = SEGB;
+  unsigned long long G = c->slot_items ? 0 : exec_grid(*c);
+  if (!c->slot_items && !G) G = DEFAULT_GRID;
   std::vector<unsigned long long> slot_bytes(N ? plan.steps.back().slot + 1 : 0, 0);
   for (const HStep &st : plan.steps) slot_bytes[st.slot] += st.nbytes;
   auto slot_cap = [&](unsigned long long sl) {
-    unsigned long long v = (slot_bytes[sl] + c->slot_items - 1) / c->slot_items;
+    const unsigned long long D = c->slot_items ? c->slot_items
+                                 : slot_bytes[sl] < SMALL_SLOT_BYTES ? G : LARGE_SLOT_ITEMS;
+    unsigned long long v = (slot_bytes[sl] + D - 1) / D;
     v = (v + SEGB - 1) / SEGB * SEGB;
     return std::min<unsigned long long>(std::max<unsigned long long>(v, SEGB),
                                         std::max<unsigned long long>(SEGB, c->item_bytes));

@@ -1058,6 +1058,21 @@ static cudaError_t device_res(int dev, DeviceRes **out) {
   return r.status;
 }
 
+static int threads_index(int nt) { return nt == 128 ? 1 : nt == 256 ? 2 : 3; }
+
+unsigned long long exec_grid(const hiccl_comm &c) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  DeviceRes *res = nullptr;
+  if (device_res(dev, &res) != cudaSuccess) return 0;
+  const int occ = res->occ[threads_index(c.threads)];
+  if (res->nsm < 1 || occ < 1) return 0;
+  return (unsigned long long)res->nsm * (unsigned long long)std::min(c.ctas_per_sm, occ);
+}
+
 constexpr int ERR_SLOTS = 1 << 16;
 static std::mutex g_err_mu;
 static unsigned long long *g_err_host = nullptr, *g_err_dev = nullptr;
@@ -1232,8 +1247,7 @@ hiccl_status_t hiccl_start(hiccl_comm_t c, void *stream) {
     t.timeout_ns = c->timeout_ns;
     if (t.nitems > 0) {
       const int nt = c->threads;
-      const int ti = nt == 128 ? 1 : nt == 256 ? 2 : 3;
-      const int per_sm = std::min(c->ctas_per_sm, d->occ[ti]);
+      const int per_sm = std::min(c->ctas_per_sm, d->occ[threads_index(nt)]);
       const unsigned long long grid = std::min<unsigned long long>(t.nitems, (unsigned long long)d->nsm * per_sm);
       // the ticket arithmetic assumes the grid of the previous launches: a
       // launch with another grid (changed options) starts from zeroed counters
