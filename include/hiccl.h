@@ -316,7 +316,7 @@ typedef enum {
  * hiccl_plan, TRACE before hiccl_init.  A work item holds at most
  * max(4096, min(ITEM_BYTES, S / D)) bytes of steps of one pipeline slot of S
  * bytes: with SLOT_ITEMS = 0 (default) D is the executor's grid (its CTAs on
- * the device current at planning; 304 without one) for S under 8 MiB, so
+ * the device current at planning; 304 without one) for S under 12 MiB, so
  * that a short slot runs as one round of items over every CTA, and 768 for
  * larger slots; SLOT_ITEMS = k > 0 sets D = k for every slot.
  * RING = n (Sec. 4.4, hybrid ring+tree): the n nodes of P/n ranks, which must

@@ -35,7 +35,7 @@ constexpr unsigned long long DEFAULT_GRID = 304;
 // work-item sizing (measured on the seven collectives of 4 MiB per rank at
 // P = 64): pipeline slots under SMALL_SLOT_BYTES are spread over the grid,
 // larger ones over LARGE_SLOT_ITEMS items
-constexpr unsigned long long SMALL_SLOT_BYTES = 8ull << 20;
+constexpr unsigned long long SMALL_SLOT_BYTES = 12ull << 20;
 constexpr unsigned long long LARGE_SLOT_ITEMS = 768;
 constexpr uint32_t MAX_FANIN = 1024;    // reduce inputs / copy destinations per step
 constexpr uint32_t TMA_MAX_FANIN = 8;   // reduce inputs folded in shared memory
