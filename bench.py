@@ -9,7 +9,8 @@ starts of a step are captured once in a CUDA graph; the timed region is a
 series of blocks of K graph replays (at least one second in all) and the
 median block gives the step time (Sec. 6.2 reports the median of its
 measured rounds).  The same steps through start / wait on the host are
-reported beside it ("eager").
+reported beside it ("eager"), and the seven collectives as one grouped
+communicator, one launch per step ("grouped_step").
 
 Metric: device-memory GB/s of the schedule (each copy reads its bytes once
 and writes them once per destination; an f-input reduce reads f times and
@@ -644,6 +645,21 @@ def measure_collectives(args, device, world, workload, dtype, xs=None, e2e=True)
         del g1
     torch.cuda.synchronize(device)
 
+    # the same collectives as one grouped communicator (hiccl_group): one
+    # persistent launch per step whose tickets interleave the seven by depth
+    grouped = None
+    if len(kinds) > 1:
+        gcomm = H.Comm.group([comms[k] for k in kinds])
+        gg = _graph_of({"group": gcomm}, ("group",) * 10, device)
+        for _ in range(2):
+            gg.replay()
+        gms = statistics.median(_time_blocks(gg.replay, 3, 0.0, stream)) / 30
+        grouped = {"ms_per_step": gms, "gbs": step_bytes / gms / 1e6, "launches_per_step": 1,
+                   "method": "graph of ten starts of the grouped communicator, replayed; median of 3 blocks of 3"}
+        del gg
+        gcomm.destroy()
+        torch.cuda.synchronize(device)
+
     graph = _graph_of(comms, kinds, device)
     for _ in range(warm):
         graph.replay()
@@ -689,7 +705,7 @@ def measure_collectives(args, device, world, workload, dtype, xs=None, e2e=True)
            "launches": len(kinds) * args.steps * len(blocks), "step_bytes": step_bytes,
            "eager": {"value": step_bytes * args.steps / (statistics.median(eager_blocks) / 1e3) / 1e9,
                      "ms_per_step": statistics.median(eager_blocks) / args.steps},
-           "collectives": coll, "e2e": e2e_line, "accuracy": accuracy}
+           "collectives": coll, "e2e": e2e_line, "accuracy": accuracy, "grouped": grouped}
     for c in comms.values():
         c.destroy()
     del bufs, graph
@@ -988,6 +1004,10 @@ def run_ours(args):
     }
     if r["accuracy"]:
         line["accuracy"] = r["accuracy"]
+    if r["grouped"]:
+        g = dict(r["grouped"])
+        g["frac"] = g["gbs"] / world / peak
+        line["grouped_step"] = g
     if extras:
         line["allreduce64"] = extras["allreduce64"]
         line["batch256"] = extras["batch256"]
