@@ -313,12 +313,14 @@ typedef enum {
  * dependency counters; a CUDA graph that recorded a start before such a
  * change must be captured again);
  * ITEM_BYTES, ORDER, SLOT_ITEMS and RING must be set before hiccl_init /
- * hiccl_plan, TRACE before hiccl_init.  A work item holds at most
- * max(4096, min(ITEM_BYTES, S / D)) bytes of steps of one pipeline slot of S
- * bytes: with SLOT_ITEMS = 0 (default) D is the executor's grid (its CTAs on
- * the device current at planning; 304 without one) for S under 12 MiB, so
- * that a short slot runs as one round of items over every CTA, and 768 for
- * larger slots; SLOT_ITEMS = k > 0 sets D = k for every slot.
+ * hiccl_plan, TRACE before hiccl_init.  The steps of one pipeline slot of S
+ * bytes are cut into work items of `cap` bytes, cap = S / D rounded up to a
+ * multiple of 4096 and kept within [4096, ITEM_BYTES] (an item closes at the
+ * first segment boundary at or past cap, so it holds less than cap + 4096
+ * bytes): with SLOT_ITEMS = 0 (default) D is the executor's grid (its CTAs
+ * on the device current at planning; 304 without one) for S under 12 MiB,
+ * so that a short slot runs as one round of items over every CTA, and 768
+ * for larger slots; SLOT_ITEMS = k > 0 sets D = k for every slot.
  * RING = n (Sec. 4.4, hybrid ring+tree): the n nodes of P/n ranks, which must
  * be the groups of one hierarchy level (n = f_0 * ... * f_{l-1}; checked at
  * planning, HICCL_ERR_INVALID otherwise), are chained starting at the root's

@@ -325,3 +325,62 @@ def test_group_plan_errors():
     assert e.value.status == H.ERR_UNSUPPORTED
     g = H.Comm.group_plan([ca])
     assert g.plan_info()["steps"] == ca.plan_info()["steps"]
+
+
+def _items_by_slot(comm):
+    """{slot: [bytes of each item]} of a planned communicator's image."""
+    steps = comm.steps()
+    recs, items = comm.image()
+    out = {}
+    for it in _decode(recs, items):
+        slot = steps[it["ent"][0][0]]["slot"]
+        out.setdefault(slot, []).append(sum(r[3] for r in it["runs"]))
+    return out, steps
+
+
+@pytest.mark.parametrize("name,slot_items", [("scatter", 0), ("scatter", 768), ("allreduce", 0), ("broadcast", 0)])
+def test_item_sizing(name, slot_items):
+    """Items follow the documented sizing: a slot of S bytes is cut at cap =
+    S / D rounded up to 4 KiB, within [4 KiB, ITEM_BYTES]; without a device
+    D is 304 for S under 12 MiB (one round over a 152-SM GB300's grid) and
+    768 above, unless SLOT_ITEMS sets it."""
+    P, d = 64, (4 << 20) // 4 // 64
+    prog = PR.BUILDERS[name](P, d)
+    fake = FakeAddresses(prog)
+    comm = register(prog, fake.addr)
+    if slot_items:
+        comm.set_option(H.OPT_SLOT_ITEMS, slot_items)
+    comm.plan([4, 4, 4], 4, 8)
+    by_slot, steps = _items_by_slot(comm)
+    slot_bytes = {}
+    for st in steps:
+        slot_bytes[st["slot"]] = slot_bytes.get(st["slot"], 0) + st["nbytes"]
+    seg, item_max = 4096, 49152
+    for slot, sizes in by_slot.items():
+        S = slot_bytes[slot]
+        D = slot_items or (304 if S < (12 << 20) else 768)
+        per_item = -(-S // D)                                   # ceil(S / D)
+        cap = min(max(-(-per_item // seg) * seg, seg), item_max)
+        assert sum(sizes) == S
+        assert max(sizes) < cap + seg
+        if not slot_items and S < (12 << 20):
+            assert len(sizes) <= 304 + 2           # one round (a class change may close one more)
+    comm.destroy()
+
+
+def test_small_slots_take_fewer_items_than_768():
+    """A Scatter's 4 MiB relay stage: one round over the grid (at most 304
+    items) by default, about 512 items when spread over 768."""
+    P, d = 64, (4 << 20) // 4 // 64
+    prog = PR.scatter(P, d)
+    fake = FakeAddresses(prog)
+    counts = []
+    for si in (0, 768):
+        comm = register(prog, fake.addr)
+        if si:
+            comm.set_option(H.OPT_SLOT_ITEMS, si)
+        comm.plan([4, 4, 4], 4, 8)
+        by_slot, _ = _items_by_slot(comm)
+        counts.append(len(by_slot[0]))
+        comm.destroy()
+    assert counts[0] <= 304 < counts[1]
