@@ -29,6 +29,7 @@ Under torchrun each rank runs an independent replica on its own GPU
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import math
@@ -884,15 +885,30 @@ def measure_batch(args, device, steps):
     return out
 
 
-def serve_trace(rate, duration, budget_gb, slots, max_batch, seed=0, shapes=0):
+def serve_trace(rate, duration, budget_gb, slots, max_batch, seed=0, shapes=0, **server_kw):
     """Serve one Poisson arrival trace (synth.poisson_requests; ``shapes`` > 0:
     arrivals drawn from that many recurring request shapes) with
     serving.Server; returns its latency and throughput summary."""
-    from paper_2408_05962_gb300.serving import Request, Server, latency_stats
+    from paper_2408_05962_gb300.serving import Request, Server, latency_stats, phase_stats
     from synth import poisson_requests
 
     descs = poisson_requests(rate, duration, seed=seed, shapes=shapes)
-    srv = Server(budget_gb << 30, slots=slots, max_batch=max_batch, planners=8)
+    srv = Server(budget_gb << 30, slots=slots, max_batch=max_batch, planners=8, **server_kw)
+    # the objects made before serving (this process's earlier measurements,
+    # torch's own) are moved out of the collector's reach, so that a full
+    # collection during the trace scans only what serving allocates; the
+    # collector's pauses are recorded
+    pauses, t_gc = [], [0.0]
+
+    def on_gc(phase, info):
+        if phase == "start":
+            t_gc[0] = time.perf_counter()
+        else:
+            pauses.append((info.get("generation", -1), time.perf_counter() - t_gc[0]))
+
+    gc.collect()
+    gc.freeze()
+    gc.callbacks.append(on_gc)
     t0 = time.perf_counter()
     k = 0
     while k < len(descs) or srv.busy():
@@ -905,7 +921,9 @@ def serve_trace(rate, duration, budget_gb, slots, max_batch, seed=0, shapes=0):
             k += 1
         srv.poll()
     wall = time.perf_counter() - t0
+    gc.callbacks.remove(on_gc)
     srv.close()
+    gc.unfreeze()
     done = [r for r in srv.done if not r.error]
     st = latency_stats(done)
     total = sum(r.hbm_bytes for r in done)
@@ -913,6 +931,12 @@ def serve_trace(rate, duration, budget_gb, slots, max_batch, seed=0, shapes=0):
            "completed": len(done),
            "errors": len(srv.done) - len(done), "wall_s": wall, "achieved_req_per_s": len(done) / wall,
            "gbs": total / wall / 1e9, "launches": srv.launches, **st}
+    out["phases_p50_p99_ms"] = phase_stats(done)
+    out["passed_waiting_head"] = srv.bypassed
+    out["plans_evicted"] = srv.evicted
+    out["longest_poll_round_ms"] = srv.max_round_s * 1e3
+    out["gc_pauses"] = {"count": len(pauses), "longest_ms": max((p for _, p in pauses), default=0.0) * 1e3,
+                        "full_collections": sum(1 for g, _ in pauses if g == 2)}
     errs = sorted({r.error for r in srv.done if r.error})
     if errs:
         out["error_messages"] = errs[:3]

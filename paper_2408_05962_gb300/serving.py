@@ -4,8 +4,14 @@ Requests (a collective kind, P virtual ranks, hierarchy, per-rank size,
 payload) arrive at any time.  The server
 
 * admits a request when its buffers fit in the device-memory budget (one
-  device arena, first-fit; FIFO, so a large request is never starved by later
-  small ones), keeping buffers and step tables on the device;
+  device arena, first-fit), keeping buffers and step tables on the device.
+  Admission is in arrival order, with one exception: while the request at
+  the head waits for memory, small requests behind it (buffers of at most
+  ``bypass_frac`` of the budget each, together at most ``bypass_cap_frac``)
+  may pass it, but only as long as the head could not fit even if every
+  request that passed it were gone -- so the head waits at most for those
+  short requests to drain, and a large request is never starved by later
+  small ones;
 * memoizes plans (Sec. 5.2: a schedule is optimized once and reused): a
   finished request leaves its communicator -- step table, counters, relay
   buffers -- and its arena buffers resident, keyed by the request's shape; a
@@ -26,8 +32,10 @@ payload) arrive at any time.  The server
   latency (completion observed minus arrival).
 
 Planning uses stripe 1 and pipeline 1 for every request: on one GPU every
-level is HBM.  The polling loop yields the interpreter lock once per round,
-so the planner threads run as soon as their native calls return.
+level is HBM.  The polling loop yields the interpreter lock once per round
+and sleeps ``idle_s`` after a round that changed nothing, so the planner
+threads (whose Python parts need the lock between native calls) are not held
+up by a spinning loop.
 """
 from __future__ import annotations
 
@@ -152,7 +160,9 @@ class Request:
     dev_bytes: int = 0           # table, counters and relays of its communicator
     cached: bool = False         # served from a memoized plan
     reserved: bool = False       # dev_bytes counted against the budget
+    bypass_bytes: int = 0        # device bytes held while admitted past a waiting head
     t_admit: float = 0.0
+    t_ready: float = 0.0         # planned and uploaded (or memoized): waiting for a slot
     t_launch: float = 0.0
     t_done: float = 0.0
     error: str = ""
@@ -167,10 +177,14 @@ class Server:
     included (a grouped launch's combined table is counted while it runs).
     ``cache_entries`` caps the memoized plans (0 disables them);
     ``comm_options`` ({hiccl option: value}) is applied to every request's
-    communicator before planning."""
+    communicator before planning.  ``bypass_frac`` = 0 makes admission
+    strictly first in, first out; ``bypass_scan`` bounds how far behind a
+    waiting head admission looks.  ``idle_s`` = 0 makes the loop spin."""
 
     def __init__(self, budget_bytes: int, slots: int = 8, max_batch: int = 1, planners: int = 4,
-                 device="cuda", on_admit=None, on_done=None, cache_entries: int = 4096, comm_options=None):
+                 device="cuda", on_admit=None, on_done=None, cache_entries: int = 256, comm_options=None,
+                 bypass_frac: float = 1 / 64, bypass_cap_frac: float = 1 / 8, bypass_scan: int = 64,
+                 idle_s: float = 50e-6):
         import torch
         self.device = torch.device(device)
         self.budget = budget_bytes
@@ -182,6 +196,7 @@ class Server:
                        "reqs": [], "group_bytes": 0} for _ in range(slots)]
         self.max_batch = max_batch
         self.pool = ThreadPoolExecutor(max_workers=planners)
+        self.reaper = ThreadPoolExecutor(max_workers=1)   # destroys evicted communicators
         self.waiting: deque = deque()     # submitted, not admitted
         self.planning: list = []          # (future, request): host planning
         self.to_upload: deque = deque()   # planned, waiting for device memory
@@ -199,6 +214,14 @@ class Server:
         self.cache = PlanCache(cache_entries if max_batch == 1 else 0)
         self.dev_bytes = 0                # tables, counters, relays of live communicators
         self.comm_options = dict(comm_options or {})
+        self.bypass_max = int(budget_bytes * bypass_frac)
+        self.bypass_cap = int(budget_bytes * bypass_cap_frac)
+        self.bypass_scan = bypass_scan
+        self.bypass_held = 0              # device bytes of live requests admitted past a waiting head
+        self.bypassed = 0                 # requests admitted past a waiting head
+        self.idle_s = idle_s
+        self.evicted = 0                  # memoized plans evicted for memory
+        self.max_round_s = 0.0            # longest poll round (host stalls)
 
     @property
     def plan_cache_hits(self):
@@ -233,10 +256,15 @@ class Server:
         return (req.kind, req.P, tuple(req.hierarchy), req.d, req.dtype, req.root)
 
     def _release_entry(self, e):
-        """Free a memoized entry: its communicator and its arena region."""
-        e["comm"].destroy()
+        """Free a memoized entry: its arena region and its communicator.  The
+        entry is idle (no launch uses it), so its region is reusable at once;
+        the communicator is destroyed on the reaper thread (its device memory
+        is freed in stream order there), so that evicting many plans for one
+        large request does not stall the polling loop."""
+        self.evicted += 1
         self.dev_bytes -= e["dev_bytes"]
         self.arena.free(*e["region"])
+        self.reaper.submit(e["comm"].destroy)
 
     def _fits(self, extra: int) -> bool:
         return self.arena.used + self.dev_bytes + extra <= self.budget
@@ -252,34 +280,58 @@ class Server:
         return True
 
     def _admit(self):
-        while self.waiting:
-            req = self.waiting[0]
+        """Admit waiting requests in order while their buffers fit (memoized
+        shapes take their resident plan).  When the head does not fit, small
+        requests behind it may pass it under the rule in the module notes."""
+        k = 0
+        head_need = None               # buffer bytes of the head, while it waits for memory
+        while k < len(self.waiting):
+            req = self.waiting[k]
             sb, rb = self._layout(req)
-            if self.max_batch == 1:
+            need = req.P * (sb + rb)
+            passing = head_need is not None
+            if passing:
+                if k >= self.bypass_scan or self._fits(head_need - self.bypass_held):
+                    return             # the head would fit once the requests that passed it drain
+                if need > self.bypass_max or self.bypass_held + need > self.bypass_cap:
+                    k += 1
+                    continue
+            if self.max_batch == 1 and not passing:   # (the head's attempt left no idle plan to take)
                 e = self.cache.take(self._shape(req))
                 if e is not None:                      # memoized: nothing to plan, upload or allocate
                     self.cache.hits += 1
-                    self.waiting.popleft()
+                    del self.waiting[k]
                     req.comm, req.region = e["comm"], e["region"]
                     req.send_ptrs, req.recv_ptrs = e["send_ptrs"], e["recv_ptrs"]
                     req.hbm_bytes, req.dev_bytes, req.cached = e["hbm_bytes"], e["dev_bytes"], True
                     req.reserved = True
-                    req.t_admit = time.perf_counter()
+                    req.t_admit = req.t_ready = time.perf_counter()
                     if self.on_admit:
                         self.on_admit(req)
                     self.ready.append(req)
                     continue
-            need = req.P * (sb + rb)
-            got = self.arena.alloc(need) if self._make_room(need) else None
-            while got is None and len(self.cache):     # fragmentation: free idle regions until it fits
-                self._release_entry(self.cache.evict_lru())
-                got = self.arena.alloc(need)
+            if passing:
+                # nothing is evicted for a request that passes the head (the
+                # head's own attempt already freed what could be freed)
+                got = self.arena.alloc(need) if self._fits(need) else None
+            else:
+                got = self.arena.alloc(need) if self._make_room(need) else None
+                while got is None and len(self.cache):     # fragmentation: free idle regions until it fits
+                    self._release_entry(self.cache.evict_lru())
+                    got = self.arena.alloc(need)
             if got is None:
-                return                     # FIFO: wait until memory frees
-            self.waiting.popleft()
+                if not passing:
+                    if self.bypass_max <= 0:
+                        return                 # strictly in order: wait until memory frees
+                    head_need = need
+                k += 1
+                continue
+            del self.waiting[k]
             self.cache.misses += 1
             off, n = got
             req.region = (off, n)
+            if passing:
+                self._hold_bypass(req, n)
             base = self.arena.base + off
             req.send_ptrs = [base + r * sb for r in range(req.P)]
             req.recv_ptrs = [base + req.P * sb + r * rb for r in range(req.P)]
@@ -287,6 +339,11 @@ class Server:
             if self.on_admit:
                 self.on_admit(req)
             self.planning.append((self.pool.submit(self._plan, req, self.comm_options), req))
+
+    def _hold_bypass(self, req: Request, nbytes: int):
+        req.bypass_bytes = nbytes
+        self.bypass_held += nbytes
+        self.bypassed += 1
 
     @staticmethod
     def _plan(req: Request, options: dict):
@@ -306,6 +363,10 @@ class Server:
     def _upload(req: Request):
         """Upload of a host plan (pool thread; the plan is not factorized again)."""
         req.comm.init(req.hierarchy, 1, 1)
+
+    def _on_uploaded(self, req: Request):
+        req.t_ready = time.perf_counter()
+        self.ready.append(req)
 
     def _collect(self, pending, on_ok):
         keep = []
@@ -331,6 +392,7 @@ class Server:
             while self.to_upload:
                 req = self.to_upload.popleft()
                 req.dev_bytes = 0
+                req.t_ready = time.perf_counter()
                 self.ready.append(req)
             return
         kept = deque()
@@ -339,6 +401,9 @@ class Server:
             if self._make_room(req.dev_bytes):
                 self.dev_bytes += req.dev_bytes
                 req.reserved = True
+                if req.bypass_bytes:
+                    req.bypass_bytes += req.dev_bytes
+                    self.bypass_held += req.dev_bytes
                 self.uploading.append((self.pool.submit(self._upload, req), req))
             else:
                 kept.append(req)
@@ -426,6 +491,8 @@ class Server:
 
     def _finish(self, req: Request, now: float):
         req.t_done = now
+        self.bypass_held -= req.bypass_bytes
+        req.bypass_bytes = 0
         if self.on_done:
             self.on_done(req)
         if req.comm is not None and req.reserved and not req.error and self.cache.max_entries > 0:
@@ -450,16 +517,23 @@ class Server:
         """One round of progress: retire finished launches, admit waiting
         requests (memoized plans directly, the others to the planners), upload
         planned ones that fit, launch ready ones on free slots; then yield the
-        interpreter lock to the planner threads."""
+        interpreter lock to the planner threads (for ``idle_s`` after a round
+        that changed nothing)."""
+        t0 = time.perf_counter()
+        before = (len(self.done), len(self.waiting), len(self.planning), len(self.uploading), len(self.ready),
+                  len(self.grouping), self.launches)
         self._retire()
         with self.lock:
             self._admit()
         self.planning = self._collect(self.planning, self.to_upload.append)
         self._reserve_uploads()
-        self.uploading = self._collect(self.uploading, self.ready.append)
+        self.uploading = self._collect(self.uploading, self._on_uploaded)
         self._collect_groups()
         self._launch()
-        time.sleep(0)
+        after = (len(self.done), len(self.waiting), len(self.planning), len(self.uploading), len(self.ready),
+                 len(self.grouping), self.launches)
+        self.max_round_s = max(self.max_round_s, time.perf_counter() - t0)
+        time.sleep(self.idle_s if after == before else 0)
 
     def busy(self) -> bool:
         return bool(self.waiting or self.planning or self.to_upload or self.uploading or self.ready
@@ -478,6 +552,7 @@ class Server:
         self.pool.shutdown()
         while len(self.cache):
             self._release_entry(self.cache.evict_lru())
+        self.reaper.shutdown()
 
 
 def latency_stats(done: list) -> dict:
@@ -488,3 +563,19 @@ def latency_stats(done: list) -> dict:
     def pct(q):
         return lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))]
     return {"n": len(lat), "p50_ms": pct(0.5) * 1e3, "p99_ms": pct(0.99) * 1e3, "max_ms": lat[-1] * 1e3}
+
+
+def phase_stats(done: list) -> dict:
+    """Where served requests spent their time, as p50 / p99 in ms of each
+    phase: waiting for admission (memory), planning and upload, waiting for
+    a launch slot, and from launch to observed completion."""
+    ok = [r for r in done if not r.error and r.t_launch]
+    if not ok:
+        return {}
+    phases = {"admit_wait": lambda r: r.t_admit - r.t_arrival, "plan_upload": lambda r: r.t_ready - r.t_admit,
+              "slot_wait": lambda r: r.t_launch - r.t_ready, "run": lambda r: r.t_done - r.t_launch}
+    out = {}
+    for name, f in phases.items():
+        v = sorted(f(r) for r in ok)
+        out[name] = [round(v[int(q * (len(v) - 1) + 0.5)] * 1e3, 3) for q in (0.5, 0.99)]
+    return out

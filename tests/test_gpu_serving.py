@@ -60,7 +60,7 @@ def _expected(req, seed):
     return sends, {r: mem[("recv", r)].copy() for r in range(req.P)}
 
 
-def _serve(reqs, budget, slots=2, max_batch=6, burst=6, gap_s=0.001):
+def _serve(reqs, budget, slots=2, max_batch=6, burst=6, gap_s=0.001, **server_kw):
     import torch
     from paper_2408_05962_gb300.serving import Server
     es = {"f32": 4, "i32": 4, "bf16": 2}
@@ -90,7 +90,8 @@ def _serve(reqs, budget, slots=2, max_batch=6, burst=6, gap_s=0.001):
             out[r] = srv.arena.buf[off:off + recvs[r].nbytes].cpu().numpy()
         results[index[id(req)]] = out
 
-    srv = Server(budget, slots=slots, max_batch=max_batch, planners=4, on_admit=on_admit, on_done=on_done)
+    srv = Server(budget, slots=slots, max_batch=max_batch, planners=4, on_admit=on_admit, on_done=on_done,
+                 **server_kw)
     for k in range(0, len(reqs), burst):      # bursts of arrivals interleaved with progress
         for req in reqs[k:k + burst]:
             srv.submit(req)
@@ -126,13 +127,29 @@ def test_concurrent_slots_results_equal_alone():
 def test_tight_budget_admits_in_order():
     reqs = _requests(10, seed=6)
     big = max(r.P * 2 * r.bytes_per_rank for r in reqs)
-    srv, expected, results, index = _serve(reqs, budget=((big + 255) // 256) * 256 + 4096, slots=2, max_batch=4)
+    srv, expected, results, index = _serve(reqs, budget=((big + 255) // 256) * 256 + 4096, slots=2, max_batch=4,
+                                           bypass_frac=0)
     assert len(srv.done) == len(reqs)
     admits = [r.t_admit for r in sorted(srv.done, key=lambda r: r.id)]
     assert admits == sorted(admits)               # FIFO admission
     for k, req in enumerate(reqs):
         for r in range(req.P):
             assert np.array_equal(results[k][r], expected[k][r].view(np.uint8))
+
+
+def test_tight_budget_small_requests_pass_the_waiting_head():
+    """The same tight budget, launched one request per slot, with small
+    requests allowed to pass a head that waits for memory: every result is
+    still the one it has alone."""
+    reqs = _requests(16, seed=6)
+    big = max(r.P * 2 * r.bytes_per_rank for r in reqs)
+    budget = 2 * ((big + 255) // 256) * 256 + (1 << 20)     # room for the largest request's tables too
+    srv, expected, results, index = _serve(reqs, budget=budget, slots=4, max_batch=1, bypass_frac=1 / 8,
+                                           bypass_cap_frac=1 / 4)
+    assert len(srv.done) == len(reqs) and not any(r.error for r in srv.done) and srv.bypass_held == 0
+    for k, req in enumerate(reqs):
+        for r in range(req.P):
+            assert np.array_equal(results[k][r], expected[k][r].view(np.uint8)), (req.kind, req.dtype, req.P, r)
 
 
 def test_memoized_plans_equal_fresh(monkeypatch):
