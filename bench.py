@@ -5,12 +5,15 @@ Broadcast, Scatter, Gather, All-gather, Reduce-scatter, All-reduce (Listing
 2) and All-to-all -- over P = 64 virtual ranks with hierarchy {4,4,4}, 4 MiB
 of fp32 per rank (uniform[-1, 1], seed 0), stripe 4, pipeline 8; each
 collective is one start of its own persistent communicator.  The seven
-starts of a step are captured once in a CUDA graph; the timed region is a
-series of blocks of K graph replays (at least one second in all) and the
-median block gives the step time (Sec. 6.2 reports the median of its
-measured rounds).  The same steps through start / wait on the host are
-reported beside it ("eager"), and the seven collectives as one grouped
-communicator, one launch per step ("grouped_step").
+starts of a step are captured once in a CUDA graph, each on its own stream
+forked from the step's stream (independent collectives started back to back
+on separate streams, so that one launch's last work items run beside the
+next one's first); the timed region is a series of blocks of K graph
+replays (at least one second in all) and the median block gives the step
+time (Sec. 6.2 reports the median of its measured rounds).  Beside it: the
+same step with the starts in order on one stream ("serial_step"), the same
+steps through start / wait on the host ("eager"), and the seven collectives
+as one grouped communicator, one launch per step ("grouped_step").
 
 Metric: device-memory GB/s of the schedule (each copy reads its bytes once
 and writes them once per destination; an f-input reduce reads f times and
@@ -552,16 +555,29 @@ def _make_comm(H, P, dtype, args):
     return comm
 
 
-def _graph_of(comms, kinds, device):
-    """One CUDA graph holding, in order, one start of the communicator of
-    every name in ``kinds`` (names may repeat; a start under capture records
-    only the executor launch, and each replay is a complete execution)."""
+def _graph_of(comms, kinds, device, concurrent=False):
+    """One CUDA graph holding one start of the communicator of every name in
+    ``kinds`` (names may repeat; a start under capture records only the
+    executor launch, and each replay is a complete execution): in order on
+    one stream, or (``concurrent``) each on its own stream forked from the
+    graph's stream and joined back, as independent collectives started back
+    to back on separate streams run -- the launches then overlap on the
+    device (one's last work items beside the next one's first) instead of
+    each waiting for the previous grid to complete."""
     import torch
     gs = torch.cuda.Stream(device)
     graph = torch.cuda.CUDAGraph()
+    side = [torch.cuda.Stream(device) for _ in kinds] if concurrent else []
     with torch.cuda.graph(graph, stream=gs):
-        for kind in kinds:
-            comms[kind].start(gs)
+        if concurrent:
+            for s, kind in zip(side, kinds):
+                s.wait_stream(gs)
+                comms[kind].start(s)
+            for s in side:
+                gs.wait_stream(s)
+        else:
+            for kind in kinds:
+                comms[kind].start(gs)
     return graph
 
 
@@ -661,7 +677,23 @@ def measure_collectives(args, device, world, workload, dtype, xs=None, e2e=True)
         gcomm.destroy()
         torch.cuda.synchronize(device)
 
-    graph = _graph_of(comms, kinds, device)
+    # the same step with the seven starts in order on one stream, each launch
+    # waiting for the previous grid (programmatic dependent launch overlaps
+    # only their launch latency)
+    serial = None
+    if len(kinds) > 1:
+        gser = _graph_of(comms, kinds, device)
+        for _ in range(warm):
+            gser.replay()
+        sblocks = _time_blocks(gser.replay, args.steps, 0.25, stream)
+        sms = statistics.median(sblocks) / args.steps
+        serial = {"ms_per_step": sms, "gbs": step_bytes / sms / 1e6, "launches_per_step": len(kinds),
+                  "method": f"graph of one step with the starts in order on one stream; blocks of {args.steps} "
+                            "replays until >= 0.25 s, median block"}
+        del gser
+        torch.cuda.synchronize(device)
+
+    graph = _graph_of(comms, kinds, device, concurrent=len(kinds) > 1)
     for _ in range(warm):
         graph.replay()
     torch.cuda.synchronize(device)
@@ -706,7 +738,7 @@ def measure_collectives(args, device, world, workload, dtype, xs=None, e2e=True)
            "launches": len(kinds) * args.steps * len(blocks), "step_bytes": step_bytes,
            "eager": {"value": step_bytes * args.steps / (statistics.median(eager_blocks) / 1e3) / 1e9,
                      "ms_per_step": statistics.median(eager_blocks) / args.steps},
-           "collectives": coll, "e2e": e2e_line, "accuracy": accuracy, "grouped": grouped}
+           "collectives": coll, "e2e": e2e_line, "accuracy": accuracy, "grouped": grouped, "serial": serial}
     for c in comms.values():
         c.destroy()
     del bufs, graph
@@ -1013,9 +1045,12 @@ def run_ours(args):
                                   {**({"ring": args.ring} if args.ring > 1 else {}),
                                    **({"bytes_per_rank": args.bytes_per_rank} if args.bytes_per_rank else {}),
                                    **({"collectives": args.kinds.split(",")} if args.kinds else {})}),
-        "timing": {"method": "CUDA graph of one step (one start per collective), replayed; blocks of "
-                             f"{args.steps} replays bracketed by CUDA events until >= {args.min_seconds:g} s; "
-                             "median block; per collective: 'ms' from eager starts bracketed by events, "
+        "timing": {"method": "CUDA graph of one step (one start per collective"
+                             + (", each on its own stream forked from the step's stream and joined back"
+                                if len(r["collectives"]) > 1 else "")
+                             + f"), replayed; blocks of {args.steps} replays bracketed by CUDA events until >= "
+                             f"{args.min_seconds:g} s; median block; 'eager': the starts in order on one stream "
+                             "through start / wait; per collective: 'ms' from eager starts bracketed by events, "
                              "'graph_ms' from a graph of ten starts of that collective, replayed",
                    "blocks": r["blocks"], "timed_s": r["timed_s"],
                    "block_ms": r["block_ms"], "eager": r["eager"]},
@@ -1032,6 +1067,10 @@ def run_ours(args):
         g = dict(r["grouped"])
         g["frac"] = g["gbs"] / world / peak
         line["grouped_step"] = g
+    if r["serial"]:
+        g = dict(r["serial"])
+        g["frac"] = g["gbs"] / world / peak
+        line["serial_step"] = g
     if extras:
         line["allreduce64"] = extras["allreduce64"]
         line["batch256"] = extras["batch256"]
