@@ -33,9 +33,9 @@ payload) arrive at any time.  The server
 
 Planning uses stripe 1 and pipeline 1 for every request: on one GPU every
 level is HBM.  The polling loop yields the interpreter lock once per round
-and sleeps ``idle_s`` after a round that changed nothing, so the planner
-threads (whose Python parts need the lock between native calls) are not held
-up by a spinning loop.
+(and, with ``idle_s`` > 0, sleeps that long after a round that changed
+nothing), so the planner threads, whose Python parts need the lock between
+native calls, run as soon as their native calls return.
 """
 from __future__ import annotations
 
@@ -179,12 +179,13 @@ class Server:
     ``comm_options`` ({hiccl option: value}) is applied to every request's
     communicator before planning.  ``bypass_frac`` = 0 makes admission
     strictly first in, first out; ``bypass_scan`` bounds how far behind a
-    waiting head admission looks.  ``idle_s`` = 0 makes the loop spin."""
+    waiting head admission looks.  ``idle_s`` > 0 makes the loop sleep after
+    a round that changed nothing (0: it only yields)."""
 
     def __init__(self, budget_bytes: int, slots: int = 8, max_batch: int = 1, planners: int = 4,
                  device="cuda", on_admit=None, on_done=None, cache_entries: int = 256, comm_options=None,
                  bypass_frac: float = 1 / 64, bypass_cap_frac: float = 1 / 8, bypass_scan: int = 64,
-                 idle_s: float = 50e-6):
+                 idle_s: float = 0.0):
         import torch
         self.device = torch.device(device)
         self.budget = budget_bytes
