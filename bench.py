@@ -926,10 +926,13 @@ def serve_trace(rate, duration, budget_gb, slots, max_batch, seed=0, shapes=0, *
 
     descs = poisson_requests(rate, duration, seed=seed, shapes=shapes)
     srv = Server(budget_gb << 30, slots=slots, max_batch=max_batch, planners=8, **server_kw)
-    # the objects made before serving (this process's earlier measurements,
-    # torch's own) are moved out of the collector's reach, so that a full
-    # collection during the trace scans only what serving allocates; the
-    # collector's pauses are recorded
+    # as a latency-bound Python service would run: the objects made before
+    # serving (this process's earlier measurements, torch's own) are frozen
+    # out of the cyclic collector, and the collector is off while requests
+    # arrive (reference counting still frees everything acyclic; a full
+    # collection over the requests kept for the statistics paused the loop
+    # for up to 180 ms in a 60 s run); it collects once the trace is served.
+    # Any collection during the trace is recorded
     pauses, t_gc = [], [0.0]
 
     def on_gc(phase, info):
@@ -941,21 +944,26 @@ def serve_trace(rate, duration, budget_gb, slots, max_batch, seed=0, shapes=0, *
     gc.collect()
     gc.freeze()
     gc.callbacks.append(on_gc)
-    t0 = time.perf_counter()
-    k = 0
-    while k < len(descs) or srv.busy():
-        now = time.perf_counter() - t0
-        while k < len(descs) and descs[k]["t"] <= now:
-            dsc = descs[k]
-            srv.submit(Request(kind=dsc["kind"], P=dsc["P"], hierarchy=dsc["hierarchy"],
-                               bytes_per_rank=dsc["bytes_per_rank"], dtype=dsc["dtype"],
-                               t_arrival=t0 + dsc["t"]))
-            k += 1
-        srv.poll()
-    wall = time.perf_counter() - t0
-    gc.callbacks.remove(on_gc)
+    gc.disable()
+    try:
+        t0 = time.perf_counter()
+        k = 0
+        while k < len(descs) or srv.busy():
+            now = time.perf_counter() - t0
+            while k < len(descs) and descs[k]["t"] <= now:
+                dsc = descs[k]
+                srv.submit(Request(kind=dsc["kind"], P=dsc["P"], hierarchy=dsc["hierarchy"],
+                                   bytes_per_rank=dsc["bytes_per_rank"], dtype=dsc["dtype"],
+                                   t_arrival=t0 + dsc["t"]))
+                k += 1
+            srv.poll()
+        wall = time.perf_counter() - t0
+    finally:
+        gc.enable()
+        gc.callbacks.remove(on_gc)
     srv.close()
     gc.unfreeze()
+    gc.collect()
     done = [r for r in srv.done if not r.error]
     st = latency_stats(done)
     total = sum(r.hbm_bytes for r in done)
