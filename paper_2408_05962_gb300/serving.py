@@ -17,7 +17,9 @@ payload) arrive at any time.  The server
   buffers -- and its arena buffers resident, keyed by the request's shape; a
   later request of the same shape takes them over with no factorization, no
   upload and no allocation.  Idle entries are evicted, least recently used
-  first, when the budget needs their memory;
+  first, when the budget needs their memory -- and only when evicting them
+  makes room: a request that waits for memory held by running requests
+  leaves the idle plans in place;
 * plans the other admitted requests on a pool of host threads (the native
   factorizer), counts each plan's device footprint (table, counters, relay
   buffers) against the budget together with the buffers, then uploads it on
@@ -96,14 +98,17 @@ class PlanCache:
     communicator, arena region, buffer pointers, footprint); ``take`` hands an
     idle entry of a shape to a new request (the oldest of that shape), ``put``
     returns one after use, ``evict_lru`` removes the least recently used idle
-    entry of any shape.  Every operation is O(1).  ``hits`` and ``misses``
-    count admitted requests (the server updates them)."""
+    entry of any shape.  Every operation is O(1).  ``nbytes`` is the device
+    memory the idle entries hold (each entry's weight as ``put`` was given
+    it).  ``hits`` and ``misses`` count admitted requests (the server updates
+    them)."""
 
     def __init__(self, max_entries: int = 4096):
         self.max_entries = max_entries
         self.by_shape = {}             # shape -> deque of serials, oldest first
-        self.lru = OrderedDict()       # serial -> (shape, entry), oldest first
+        self.lru = OrderedDict()       # serial -> (shape, entry, nbytes), oldest first
         self.serial = 0
+        self.nbytes = 0
         self.hits = 0
         self.misses = 0
 
@@ -114,16 +119,18 @@ class PlanCache:
         q = self.by_shape.get(shape)
         if not q:
             return None
-        entry = self.lru.pop(q.popleft())[1]
+        _, entry, nb = self.lru.pop(q.popleft())
+        self.nbytes -= nb
         if not q:
             del self.by_shape[shape]
         return entry
 
-    def put(self, shape, entry):
+    def put(self, shape, entry, nbytes: int = 0):
         """Store an idle entry; returns the entries pushed out by the size cap."""
         self.serial += 1
         self.by_shape.setdefault(shape, deque()).append(self.serial)
-        self.lru[self.serial] = (shape, entry)
+        self.lru[self.serial] = (shape, entry, nbytes)
+        self.nbytes += nbytes
         out = []
         while len(self.lru) > self.max_entries:
             out.append(self.evict_lru())
@@ -132,7 +139,8 @@ class PlanCache:
     def evict_lru(self):
         if not self.lru:
             return None
-        serial, (shape, entry) = self.lru.popitem(last=False)
+        serial, (shape, entry, nb) = self.lru.popitem(last=False)
+        self.nbytes -= nb
         q = self.by_shape[shape]
         q.popleft()                    # serials grow, so the oldest overall is the oldest of its shape
         if not q:
@@ -272,7 +280,13 @@ class Server:
 
     def _make_room(self, need: int) -> bool:
         """Evict idle memoized plans (least recently used first) until
-        ``need`` more bytes fit in the budget."""
+        ``need`` more bytes fit in the budget; evicts nothing when even
+        every idle plan gone would not make room (memory held by running
+        requests must free first, and the idle plans stay reusable)."""
+        if self._fits(need):
+            return True
+        if not self._fits(need - self.cache.nbytes):
+            return False
         while not self._fits(need):
             e = self.cache.evict_lru()
             if e is None:
@@ -292,12 +306,12 @@ class Server:
             need = req.P * (sb + rb)
             passing = head_need is not None
             if passing:
-                if k >= self.bypass_scan or self._fits(head_need - self.bypass_held):
+                if k >= self.bypass_scan or self._fits(head_need - self.bypass_held - self.cache.nbytes):
                     return             # the head would fit once the requests that passed it drain
                 if need > self.bypass_max or self.bypass_held + need > self.bypass_cap:
                     k += 1
                     continue
-            if self.max_batch == 1 and not passing:   # (the head's attempt left no idle plan to take)
+            if self.max_batch == 1:
                 e = self.cache.take(self._shape(req))
                 if e is not None:                      # memoized: nothing to plan, upload or allocate
                     self.cache.hits += 1
@@ -306,6 +320,8 @@ class Server:
                     req.send_ptrs, req.recv_ptrs = e["send_ptrs"], e["recv_ptrs"]
                     req.hbm_bytes, req.dev_bytes, req.cached = e["hbm_bytes"], e["dev_bytes"], True
                     req.reserved = True
+                    if passing:                        # its resident memory is now held past the head
+                        self._hold_bypass(req, e["region"][1] + e["dev_bytes"])
                     req.t_admit = req.t_ready = time.perf_counter()
                     if self.on_admit:
                         self.on_admit(req)
@@ -316,8 +332,9 @@ class Server:
                 # head's own attempt already freed what could be freed)
                 got = self.arena.alloc(need) if self._fits(need) else None
             else:
-                got = self.arena.alloc(need) if self._make_room(need) else None
-                while got is None and len(self.cache):     # fragmentation: free idle regions until it fits
+                room = self._make_room(need)
+                got = self.arena.alloc(need) if room else None
+                while room and got is None and len(self.cache):   # fragmentation: free idle regions until it fits
                     self._release_entry(self.cache.evict_lru())
                     got = self.arena.alloc(need)
             if got is None:
@@ -500,7 +517,7 @@ class Server:
             # memoize: the communicator and its buffers stay resident
             e = {"comm": req.comm, "region": req.region, "send_ptrs": req.send_ptrs, "recv_ptrs": req.recv_ptrs,
                  "hbm_bytes": req.hbm_bytes, "dev_bytes": req.dev_bytes}
-            for old in self.cache.put(self._shape(req), e):
+            for old in self.cache.put(self._shape(req), e, req.region[1] + req.dev_bytes):
                 self._release_entry(old)
         else:
             if req.comm is not None:

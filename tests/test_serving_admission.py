@@ -119,3 +119,30 @@ def test_evicted_plans_are_destroyed_off_the_polling_loop(monkeypatch):
         srv._finish(r, time.perf_counter())
     srv.reaper.shutdown()                             # wait for the reaper thread
     assert srv.evicted == 3 and len(destroyed) == 3 and len(srv.cache) == 2
+
+
+def test_idle_plans_stay_when_evicting_them_would_not_make_room():
+    srv = _server(1024, bypass_frac=1 / 16, bypass_cap_frac=1 / 8)
+    small = _ag(60)
+    srv.submit(small)
+    assert _advance(srv) == [small]
+    srv._finish(small, time.perf_counter())           # idle, memoized: about 60 MiB
+    assert len(srv.cache) == 1 and srv.cache.nbytes > 60 * MiB - (1 << 20)
+    hold = _ag(640)
+    srv.submit(hold)
+    assert _advance(srv) == [hold]                    # running
+    head = _ag(512)
+    srv.submit(head)
+    assert _advance(srv) == [] and list(srv.waiting) == [head]
+    assert len(srv.cache) == 1 and srv.evicted == 0   # 640 + 512 > 1024 even without it: kept
+    again = _ag(60)                                   # the same shape passes the head on its resident plan
+    srv.submit(again)
+    assert _advance(srv) == [again] and again.cached and again.send_ptrs == small.send_ptrs
+    assert srv.bypass_held > 0 and srv.cache.nbytes == 0
+    srv._finish(again, time.perf_counter())
+    assert srv.bypass_held == 0 and len(srv.cache) == 1
+    srv._finish(hold, time.perf_counter())            # now evicting the idle plans makes room for the head
+    assert _advance(srv) == [head] and srv.evicted >= 1
+    srv._finish(head, time.perf_counter())
+    srv.close()
+    assert srv.device_bytes() == 0 and srv.cache.nbytes == 0
