@@ -34,14 +34,8 @@ def _run(kind, P, d, h, s, m, x):
     return out
 
 
-@pytest.mark.parametrize("kind", ["broadcast", "scatter", "gather", "allgather", "reducescatter",
-                                  "allreduce", "alltoall"])
-def test_seven_collectives_full_size(kind):
-    P, h = 64, [4, 4, 4]
-    d = (4 << 20) // 4 // P
-    x = uniform_ranks(P, d * P, seed=1)
-    y = _run(kind, P, d, h, 4, 8, x)
-    xs = [x[r] for r in range(P)]
+def _expected_seven(kind, xs, d, h):
+    P = len(xs)
     if kind == "broadcast":
         exp = S.def_broadcast(xs, 0)
     elif kind == "scatter":
@@ -57,11 +51,66 @@ def test_seven_collectives_full_size(kind):
         exp = S.def_allreduce(xs, h)
     else:
         exp = S.def_alltoall(xs)
-    for r in range(P):
+    return exp
+
+
+def _check(kind, y, exp):
+    for r in range(len(exp)):
         if exp[r] is None:
-            assert np.all(y[r] == -3.0)
+            assert np.all(y[r] == -3.0), (kind, r)
         else:
             assert np.array_equal(y[r].view(np.uint32), exp[r].view(np.uint32)), (kind, r)
+
+
+SEVEN = ["broadcast", "scatter", "gather", "allgather", "reducescatter", "allreduce", "alltoall"]
+
+
+@pytest.mark.parametrize("kind", SEVEN)
+def test_seven_collectives_full_size(kind):
+    P, h = 64, [4, 4, 4]
+    d = (4 << 20) // 4 // P
+    x = uniform_ranks(P, d * P, seed=1)
+    y = _run(kind, P, d, h, 4, 8, x)
+    _check(kind, y, _expected_seven(kind, [x[r] for r in range(P)], d, h))
+
+
+def test_seven_collectives_concurrent_graph_full_size():
+    """The benchmark's step as it is timed: the seven communicators' starts
+    captured in one CUDA graph, each on its own stream forked from the
+    graph's stream (their launches overlap on the device), replayed twice;
+    after each replay every receive buffer of every collective equals the
+    oracle's in full."""
+    import torch
+
+    import bench
+    from paper_2408_05962_gb300 import collectives as C
+    from paper_2408_05962_gb300 import hiccl as H
+    P, h = 64, [4, 4, 4]
+    d = (4 << 20) // 4 // P
+    x = uniform_ranks(P, d * P, seed=4)
+    xs = [x[r] for r in range(P)]
+    dev = torch.device("cuda", 0)
+    comms, bufs = {}, {}
+    for kind in SEVEN:
+        b = C.Buffers(kind, P, d, torch.float32, dev)
+        b.send.copy_(torch.from_numpy(x[:, :b.ls]))
+        comm = H.Comm(P, "f32")
+        C.compose(comm, kind, d, b.send_ptrs(), b.recv_ptrs())
+        comm.init(h, 4, 8)
+        comms[kind], bufs[kind] = comm, b
+    graph = bench._graph_of(comms, SEVEN, dev, concurrent=True)
+    exp = {kind: _expected_seven(kind, xs, d, h) for kind in SEVEN}
+    for _ in range(2):
+        for kind in SEVEN:
+            bufs[kind].recv.fill_(-3.0)
+        torch.cuda.synchronize(dev)
+        graph.replay()
+        torch.cuda.synchronize(dev)
+        for kind in SEVEN:
+            _check(kind, bufs[kind].recv.cpu().numpy(), exp[kind])
+    del graph
+    for c in comms.values():
+        c.destroy()
 
 
 def test_allreduce_64mib_full():
